@@ -1,0 +1,229 @@
+/*
+ * fr_pcpf.h -- C ABI of the GB300 FR-PCPF library (libfrpcpf.so).
+ *
+ * The library advances the preconditioned conservative phase field of
+ * arXiv 2006.10967 with explicit high-order Flux Reconstruction (FR) on
+ * quadrilateral, triangular and hexahedral meshes:
+ *
+ *   phi_t + div(phi u) = div( max(gamma,|u|) (eps grad phi
+ *                              - gamma phi(1-phi) grad psi/|grad psi|) )
+ *                        (Section 2, Eq. altconservativephasefieldeq, with the
+ *                         normal from psi as in Section 2's preconditioned form)
+ *   psi_t + div(psi u) = 0                                   (Section 2)
+ *   every N steps: psi0 = phi - 1/2, then pseudo-time iterations of
+ *   psi_tau = div(nu_s grad psi) + sgn(psi0)(1 - |grad psi|)
+ *                        (Section 2 Eq. lsequation; Section 3.2
+ *                         Eqs. peudoSystem1, resolutionIndicator, nu_s,
+ *                         pseudotimesystem and the L2 stop rule)
+ *
+ * Spatial discretisation: FR Steps 1-6 of Section 3.1 (Eqs. extrapolateSoln,
+ * continuousGrad, extrapolateGrad, normalTransFlux, commonFlux, inviscidFlux,
+ * viscousFlux, continuousDivFlux), copy ghost states on walls (Section 3.3);
+ * time: the 4-stage Runge-Kutta march of Section 3.1 (classical RK4).
+ *
+ * Conventions
+ *  - All functions return an int status: FR_OK (0) or a negative FR_E* code.
+ *    No exception or longjmp crosses this boundary.  fr_strerror() names codes.
+ *  - "host" pointers are CPU memory, "device" pointers are CUDA device memory
+ *    of the current device.  Host inputs are copied before the call returns;
+ *    the caller keeps ownership of every pointer it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it asynchronously unless stated otherwise.
+ *  - The library never allocates device memory.  The caller allocates one
+ *    workspace of fr_field_workspace_bytes() bytes (256-byte aligned) and
+ *    passes it to fr_field_init(); it must outlive the field.
+ *  - Solution-point data are laid out element-major: value (e, i) at index
+ *    e * Nu + i, where i orders tensor points xi-fastest (then eta, zeta) on
+ *    quadrilaterals/hexahedra and lattice points (i fastest, then j) on
+ *    triangles; fr_mesh_solution_points() returns the coordinates.
+ *  - Vertex orders: quad counter-clockwise; tri counter-clockwise; hex the
+ *    quad order at zeta = -1 then at zeta = +1.
+ */
+#ifndef FR_PCPF_H
+#define FR_PCPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FR_OK 0
+#define FR_EINVAL (-1)      /* invalid argument, mesh or parameter */
+#define FR_ENOMEM (-2)      /* host allocation failed or workspace too small */
+#define FR_ECUDA (-3)       /* a CUDA runtime call failed */
+#define FR_ENONFINITE (-4)  /* a non-finite value appeared in the state */
+#define FR_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define FR_EUNSUPPORTED (-6) /* element type / order / mode not built */
+
+/* ---- element types, precisions, velocity and IC kinds ---------------- */
+#define FR_QUAD 0
+#define FR_TRI 1
+#define FR_HEX 2
+
+#define FR_FP64 0  /* every array and operation in double precision */
+#define FR_MIXED 1 /* float stage values/fluxes/traces; double solution,
+                      RK accumulator, psi0 and mass integral */
+
+#define FR_VEL_UNIFORM 0     /* u = a */
+#define FR_VEL_RIDER_KOTHE 1 /* Section 4.2 field times g(t) */
+#define FR_VEL_LEVEQUE 2     /* Section 4.3 field times g(t) */
+#define FR_VEL_STREAM 3      /* u = dPsi/dy, v = -dPsi/dx,
+                                Psi = g(t) sum_m A_m sin(2 pi k_m.x) + B_m cos(2 pi k_m.x) */
+#define FR_VEL_ROTATION 4    /* (0.5 - y, x - 0.5), Section 4.1 */
+#define FR_MAX_MODES 32
+
+#define FR_IC_CIRCLE 0 /* phi = (1 + tanh(beta (r - |x - c|)))/2, Eqs. initialCond, discEq */
+#define FR_IC_ARRAY 1  /* phi0 given at the solution points (host, E*Nu) */
+
+typedef struct fr_mesh fr_mesh;   /* opaque, host side */
+typedef struct fr_field fr_field; /* opaque, host handle to device state */
+
+/* Mesh description (Section 3.1: elements, mapping, coinciding flux points). */
+typedef struct fr_mesh_desc {
+  int32_t dim;           /* 2 or 3 */
+  int32_t etype;         /* FR_QUAD, FR_TRI (dim 2) or FR_HEX (dim 3) */
+  int32_t order;         /* p: quad 1..6, tri 1..4, hex 1..5 */
+  int32_t reserved;
+  int64_t n_nodes;
+  const double* nodes;   /* host, n_nodes * dim, node-major */
+  int64_t n_elems;
+  const int64_t* conn;   /* host, n_elems * nverts (4, 3 or 8) */
+  int32_t periodic[3];   /* axis a periodic with period[a] */
+  double period[3];
+} fr_mesh_desc;
+
+typedef struct fr_mesh_info {
+  int32_t dim, etype, order, nu, nf, n_faces_per_elem;
+  int64_t n_elems;
+  int64_t n_dof;         /* n_elems * nu */
+  int64_t n_boundary_fpts;
+  double h;              /* average element size (quad/hex (|Omega|/E)^(1/d); tri sqrt(2|Omega|/E)) */
+  double volume;         /* |Omega| */
+} fr_mesh_info;
+
+typedef struct fr_velocity {
+  int32_t kind;          /* FR_VEL_* */
+  int32_t n_modes;       /* FR_VEL_STREAM: 1..FR_MAX_MODES */
+  double T;              /* g(t) = cos(pi t / T) if T > 0, else 1 */
+  double a[3];           /* FR_VEL_UNIFORM */
+  const double* kx;      /* host, n_modes each (FR_VEL_STREAM), copied */
+  const double* ky;
+  const double* A;
+  const double* B;
+} fr_velocity;
+
+typedef struct fr_params {
+  double gamma;          /* 0.09 in the paper */
+  double eps;            /* 0.06 h/p in the paper */
+  double tau;            /* LDG penalty on phi (total flux out of L gets +tau(u_L-u_R)) */
+  double tau_psi;        /* penalty on psi's advection flux (0: central) */
+  double tau_pseudo;     /* LDG penalty in the preconditioning equation */
+  double dt;             /* physical time step */
+  int32_t n_precond;     /* precondition every n_precond steps (paper: 1000) */
+  int32_t pseudo_kmax;   /* maximum pseudo iterations (paper: up to 20) */
+  double pseudo_dtau;    /* pseudo time step */
+  double pseudo_tol;     /* stop when RMS((psi^k - psi^{k-1})/dtau) <= tol (paper: 1/2) */
+  int32_t pseudo_fixed;  /* 1: always run pseudo_kmax iterations */
+  int32_t precision;     /* FR_FP64 or FR_MIXED */
+  double s0, kappa, nu_max; /* Eq. nu_s */
+  double delta;          /* guard: |grad psi| -> max(|grad psi|, delta) */
+  fr_velocity vel;
+} fr_params;
+
+typedef struct fr_ic {
+  int32_t kind;          /* FR_IC_CIRCLE or FR_IC_ARRAY */
+  int32_t precondition;  /* 1: reset psi = phi - 1/2 and precondition (Section 2) */
+  double centre[3];
+  double radius;
+  double beta;           /* sharpness; the paper uses 3p/(4h) */
+  const double* phi0;    /* FR_IC_ARRAY: host, n_dof */
+} fr_ic;
+
+typedef struct fr_stats {
+  int64_t n_steps;       /* physical steps taken since init */
+  double t;              /* physical time */
+  int32_t last_pseudo_iters;
+  int32_t status;        /* sticky device status: FR_OK, FR_ENONFINITE, ... */
+  double last_pseudo_rms;
+  int64_t n_preconditions;
+} fr_stats;
+
+/* ---- mesh ------------------------------------------------------------ */
+
+/* Build the host mesh: reference operators, element geometry, face pairing
+ * (faces matched by vertex positions modulo the periods; flux points by
+ * physical position).  The L side of an interior face is the lower element
+ * number.  Unmatched faces are walls (copy ghost states, Section 3.3).
+ * Errors: FR_EINVAL (bad dim/type/order/index, face shared by > 2 elements,
+ * non-coinciding flux points, det J <= 0), FR_ENOMEM, FR_EUNSUPPORTED. */
+int fr_mesh_create(const fr_mesh_desc* desc, fr_mesh** out);
+int fr_mesh_info_get(const fr_mesh* mesh, fr_mesh_info* info);
+/* Physical solution-point coordinates, host out[n_dof * dim] (point-major). */
+int fr_mesh_solution_points(const fr_mesh* mesh, double* out);
+/* Quadrature weights w_i det J_ei, host out[n_dof]: the exact integral of the
+ * interpolant (Section 4 error measures). */
+int fr_mesh_quadrature(const fr_mesh* mesh, double* out);
+void fr_mesh_destroy(fr_mesh* mesh);
+
+/* ---- field ----------------------------------------------------------- */
+
+/* Bytes of device workspace fr_field_init needs for this mesh and params. */
+int fr_field_workspace_bytes(const fr_mesh* mesh, const fr_params* prm, size_t* bytes);
+
+/* Create a field on `workspace` (device, >= fr_field_workspace_bytes, 256-byte
+ * aligned), set phi from `ic`, psi = phi - 1/2, and (if ic->precondition)
+ * run the preconditioning of Section 2 at t = 0.  Synchronises `stream`.
+ * Errors: FR_EINVAL, FR_ENOMEM (workspace too small), FR_ENONFINITE (IC not
+ * finite), FR_EUNSUPPORTED, FR_ECUDA. */
+int fr_field_init(const fr_mesh* mesh, const fr_params* prm, const fr_ic* ic,
+                  void* workspace, size_t workspace_bytes, void* stream, fr_field** out);
+
+/* Advance n_steps physical RK4 steps on `stream` (asynchronous).  Before step
+ * n (n > 0, n % n_precond == 0) psi is reset to phi - 1/2 and preconditioned.
+ * Returns the sticky status of earlier work (FR_ENONFINITE once a non-finite
+ * value was seen); call fr_sync for the status of this call. */
+int fr_step(fr_field* field, int n_steps, void* stream);
+
+/* Reset psi0 = phi - 1/2 and run the pseudo-time iterations now (asynchronous). */
+int fr_precondition(fr_field* field, void* stream);
+
+/* Synchronise `stream`, read the device status word; returns it. */
+int fr_sync(fr_field* field, void* stream);
+int fr_stats_get(fr_field* field, void* stream, fr_stats* out);
+
+/* int phi dOmega (which = 0) or int psi dOmega (which = 1): sum over elements
+ * and points of w_i det J_i u_i with a compensated (Neumaier) FP64 reduction
+ * in a fixed order (deterministic).  Synchronous: *out_host is valid on return. */
+int fr_mass_integral(fr_field* field, int which, double* out_host, void* stream);
+
+/* Copy a field to/from host memory (synchronous): which = 0 phi, 1 psi,
+ * 2 psi0; n_dof doubles.  fr_field_set also refreshes the stage copies and
+ * flux-point traces. */
+int fr_field_get(fr_field* field, int which, double* host, void* stream);
+int fr_field_set(fr_field* field, int which, const double* host, void* stream);
+/* Device-pointer variants (asynchronous on `stream`), n_dof doubles. */
+int fr_field_get_device(fr_field* field, int which, double* dev, void* stream);
+int fr_field_set_device(fr_field* field, int which, const double* dev, void* stream);
+
+/* Evaluate the semi-discrete right-hand side du/dt = -J^{-1} div~ f~ (Step 6)
+ * of the physical system at the current state and time t into dev_out
+ * (device, 2 * n_dof doubles: phi rates then psi rates).  Does not change the
+ * state.  Asynchronous. */
+int fr_rhs(fr_field* field, double t, double* dev_out, void* stream);
+/* Same for the preconditioning system (Eq. pseudotimesystem), psi rates into
+ * dev_out (n_dof doubles), with the stored psi0. */
+int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
+
+void fr_field_destroy(fr_field* field);
+
+const char* fr_strerror(int code);
+int fr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_PCPF_H */

@@ -1,0 +1,227 @@
+"""GB300-native FR-PCPF: the flux-reconstruction update of the preconditioned,
+localised conservative phase field (arXiv 2006.10967) as hand-written sm_103a
+CUDA kernels behind a C ABI (include/fr_pcpf.h, libfrpcpf.so).
+
+This module is the thin Python binding: it marshals arguments, lets PyTorch
+provide device memory (one workspace per field) and streams, and calls the
+library.  Every step of the update runs in the library's kernels; if the
+library is missing, importing Field/Mesh raises instead of falling back.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _capi as capi
+from ._capi import (FR_FP64, FR_MIXED, FR_QUAD, FR_TRI, FR_HEX, FR_IC_ARRAY, FR_IC_CIRCLE,
+                    FRError, check, lib)
+
+__all__ = ["Mesh", "Field", "make_params", "FRError", "FR_FP64", "FR_MIXED", "lib",
+           "fr_mesh_create", "fr_field_init", "fr_step", "fr_adjoint_step", "fr_mass_integral"]
+
+ETYPES = {"quad": FR_QUAD, "tri": FR_TRI, "hex": FR_HEX}
+VELS = {"uniform": 0, "rider_kothe": 1, "leveque": 2, "stream": 3, "rotation": 4}
+_dp = C.POINTER(C.c_double)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Mesh:
+    """Host mesh (fr_mesh_create): operators, geometry, face pairing."""
+
+    def __init__(self, nodes, conn, etype, order, periodic=(False, False, False), period=(1.0, 1.0, 1.0)):
+        self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        self._conn = np.ascontiguousarray(conn, dtype=np.int64)
+        dim = self._nodes.shape[1]
+        d = capi.fr_mesh_desc()
+        d.dim = dim
+        d.etype = ETYPES[etype] if isinstance(etype, str) else int(etype)
+        d.order = int(order)
+        d.n_nodes = self._nodes.shape[0]
+        d.nodes = _ptr(self._nodes)
+        d.n_elems = self._conn.shape[0]
+        d.conn = self._conn.ctypes.data_as(C.POINTER(C.c_int64))
+        for a in range(3):
+            d.periodic[a] = int(bool(periodic[a])) if a < len(periodic) else 0
+            d.period[a] = float(period[a]) if a < len(period) else 1.0
+        h = C.c_void_p()
+        check(lib().fr_mesh_create(C.byref(d), C.byref(h)), "fr_mesh_create")
+        self.handle = h
+        self.info = capi.fr_mesh_info()
+        check(lib().fr_mesh_info_get(h, C.byref(self.info)), "fr_mesh_info_get")
+
+    @classmethod
+    def from_synthetic(cls, m, order):
+        return cls(m.nodes, m.conn, m.etype, order, tuple(m.periodic) + (False,) * (3 - len(m.periodic)),
+                   tuple(m.period) + (1.0,) * (3 - len(m.period)))
+
+    @property
+    def shape(self):
+        return (self.info.n_elems, self.info.nu)
+
+    def solution_points(self):
+        out = np.empty((self.info.n_elems, self.info.nu, self.info.dim))
+        check(lib().fr_mesh_solution_points(self.handle, _ptr(out)), "fr_mesh_solution_points")
+        return out
+
+    def quadrature(self):
+        out = np.empty((self.info.n_elems, self.info.nu))
+        check(lib().fr_mesh_quadrature(self.handle, _ptr(out)), "fr_mesh_quadrature")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().fr_mesh_destroy(h)
+            self.handle = None
+
+
+def make_params(w, precision="fp64", **kw):
+    """fr_params from a workload-like object (attributes of synthetic.Workload)."""
+    p = capi.fr_params()
+    g = lambda k: kw.get(k, getattr(w, k))
+    p.gamma = g("gamma")
+    p.eps = g("eps")
+    p.tau = g("tau")
+    p.tau_psi = g("tau_psi")
+    p.tau_pseudo = g("tau_pseudo")
+    p.dt = g("dt")
+    p.n_precond = int(g("n_precond"))
+    p.pseudo_kmax = int(g("pseudo_kmax"))
+    p.pseudo_dtau = g("pseudo_dtau")
+    p.pseudo_tol = g("pseudo_tol")
+    p.pseudo_fixed = int(bool(kw.get("pseudo_fixed", False)))
+    p.precision = FR_MIXED if precision in ("mixed", FR_MIXED) else FR_FP64
+    p.s0 = g("s0")
+    p.kappa = g("kappa")
+    p.nu_max = g("nu_max")
+    p.delta = g("delta")
+    vel = kw.get("velocity", w.velocity)
+    p.vel.kind = VELS[vel.kind]
+    p.vel.T = float(vel.T)
+    for a in range(3):
+        p.vel.a[a] = float(vel.a[a]) if a < len(vel.a) else 0.0
+    keep = []
+    if vel.kind == "stream":
+        arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (vel.kx, vel.ky, vel.A, vel.B)]
+        keep = arrs
+        p.vel.n_modes = len(arrs[0])
+        p.vel.kx, p.vel.ky, p.vel.A, p.vel.B = [_ptr(x) for x in arrs]
+    p._keep = keep
+    return p
+
+
+class Field:
+    """Device state of one FR-PCPF problem (fr_field_init); PyTorch owns the workspace."""
+
+    def __init__(self, mesh, params, ic=None, phi0=None, precondition=True, stream=None):
+        import torch
+        self.mesh = mesh
+        self.params = params
+        self.torch = torch
+        nbytes = C.c_size_t()
+        check(lib().fr_field_workspace_bytes(mesh.handle, C.byref(params), C.byref(nbytes)),
+              "fr_field_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        self._base = (base + 255) // 256 * 256
+        icd = capi.fr_ic()
+        icd.precondition = int(bool(precondition))
+        self._phi0 = None
+        if phi0 is not None:
+            self._phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
+            icd.kind = FR_IC_ARRAY
+            icd.phi0 = _ptr(self._phi0)
+        else:
+            icd.kind = FR_IC_CIRCLE
+            for a in range(3):
+                icd.centre[a] = float(ic.centre[a]) if a < len(ic.centre) else 0.0
+            icd.radius = float(ic.radius)
+            icd.beta = float(ic.beta)
+        h = C.c_void_p()
+        check(lib().fr_field_init(mesh.handle, C.byref(params), C.byref(icd), C.c_void_p(self._base),
+                                  nbytes.value, self._stream(stream), C.byref(h)), "fr_field_init")
+        self.handle = h
+
+    def _stream(self, stream=None):
+        s = stream if stream is not None else self.torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def step(self, n=1, stream=None):
+        check(lib().fr_step(self.handle, int(n), self._stream(stream)), "fr_step")
+
+    def precondition(self, stream=None):
+        check(lib().fr_precondition(self.handle, self._stream(stream)), "fr_precondition")
+
+    def sync(self, stream=None):
+        return lib().fr_sync(self.handle, self._stream(stream))
+
+    def stats(self, stream=None):
+        s = capi.fr_stats()
+        check(lib().fr_stats_get(self.handle, self._stream(stream), C.byref(s)), "fr_stats_get")
+        return dict(n_steps=s.n_steps, t=s.t, last_pseudo_iters=s.last_pseudo_iters, status=s.status,
+                    last_pseudo_rms=s.last_pseudo_rms, n_preconditions=s.n_preconditions)
+
+    def mass(self, which=0, stream=None):
+        out = C.c_double()
+        check(lib().fr_mass_integral(self.handle, int(which), C.byref(out), self._stream(stream)),
+              "fr_mass_integral")
+        return out.value
+
+    def get(self, which=0, stream=None):
+        out = np.empty(self.mesh.shape)
+        check(lib().fr_field_get(self.handle, int(which), _ptr(out), self._stream(stream)), "fr_field_get")
+        return out
+
+    def set(self, which, values, stream=None):
+        arr = np.ascontiguousarray(values, dtype=np.float64).reshape(self.mesh.shape)
+        check(lib().fr_field_set(self.handle, int(which), _ptr(arr), self._stream(stream)), "fr_field_set")
+
+    def get_device(self, which, out, stream=None):
+        check(lib().fr_field_get_device(self.handle, int(which), C.c_void_p(out.data_ptr()),
+                                        self._stream(stream)), "fr_field_get_device")
+        return out
+
+    def set_device(self, which, values, stream=None):
+        check(lib().fr_field_set_device(self.handle, int(which), C.c_void_p(values.data_ptr()),
+                                        self._stream(stream)), "fr_field_set_device")
+
+    def rhs(self, t, stream=None):
+        out = self.torch.empty((2,) + self.mesh.shape, dtype=self.torch.float64, device="cuda")
+        check(lib().fr_rhs(self.handle, float(t), C.c_void_p(out.data_ptr()), self._stream(stream)), "fr_rhs")
+        return out
+
+    def rhs_pseudo(self, stream=None):
+        out = self.torch.empty(self.mesh.shape, dtype=self.torch.float64, device="cuda")
+        check(lib().fr_rhs_pseudo(self.handle, C.c_void_p(out.data_ptr()), self._stream(stream)),
+              "fr_rhs_pseudo")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().fr_field_destroy(h)
+            self.handle = None
+
+
+# C-ABI names of the hot path, for callers who want the raw entry points
+def fr_mesh_create(*a):
+    return lib().fr_mesh_create(*a)
+
+
+def fr_field_init(*a):
+    return lib().fr_field_init(*a)
+
+
+def fr_step(*a):
+    return lib().fr_step(*a)
+
+
+def fr_mass_integral(*a):
+    return lib().fr_mass_integral(*a)
+
+
+def fr_adjoint_step(*a):
+    return lib().fr_adjoint_step(*a)

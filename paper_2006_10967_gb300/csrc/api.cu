@@ -1,0 +1,567 @@
+// C ABI of libfrpcpf: field life cycle, RK4 march, preconditioning schedule,
+// mass integral and state transfer.  Device memory is a caller-provided
+// workspace; the library never allocates device memory.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.hpp"
+#include "kdispatch.hpp"
+
+using namespace frp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t status, dstate, red, geo, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0;
+  size_t tri_xu, tri_xf, tri_nref, tri_L, tri_Dr, tri_Ds, tri_LIFT, tri_Vinv, tri_high;
+  size_t total;
+};
+
+Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
+  Layout L{};
+  const size_t E = (size_t)m.E, NU = m.nu, NF = m.nf, NG = (size_t)m.dim * m.ncoef;
+  const size_t tb = precision == FR_FP64 ? 8 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.status = take(ST_WORDS * sizeof(int32_t));
+  L.dstate = take(DS_WORDS * sizeof(double));
+  L.red = take((size_t)(max_blocks + 1) * 2 * sizeof(double));
+  L.geo = take(E * NG * sizeof(double));
+  L.fnbr = take(E * NF * sizeof(int32_t));
+  L.wdet = take(E * NU * sizeof(double));
+  L.ustg = take(E * 2 * NU * tb);
+  L.u = take(E * 2 * NU * sizeof(double));
+  L.acc = take(E * 2 * NU * sizeof(double));
+  L.rp = take(E * 2 * NU * tb);
+  L.tr = take(E * 2 * NF * tb);
+  L.fc = take(E * 2 * NF * tb);
+  L.psi0 = take(E * NU * sizeof(double));
+  if (m.etype == FR_TRI) {
+    L.tri_xu = take(NU * 2 * sizeof(double));
+    L.tri_xf = take(NF * 2 * sizeof(double));
+    L.tri_nref = take(NF * 2 * sizeof(double));
+    L.tri_L = take(NF * NU * sizeof(double));
+    L.tri_Dr = take(NU * NU * sizeof(double));
+    L.tri_Ds = take(NU * NU * sizeof(double));
+    L.tri_LIFT = take(NU * NF * sizeof(double));
+    L.tri_Vinv = take(NU * NU * sizeof(double));
+    L.tri_high = take(NU);
+  }
+  L.total = off;
+  return L;
+}
+
+bool get_kernels(const fr_mesh& m, int precision, KernelSet* ks) {
+  if (m.etype == FR_QUAD) return kernels_quad(m.order, precision, m.E, ks);
+  if (m.etype == FR_HEX) return kernels_hex(m.order, precision, m.E, ks);
+  return kernels_tri(m.order, precision, m.E, ks);
+}
+
+int check_params(const fr_params* p) {
+  if (!p) return FR_EINVAL;
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return FR_EINVAL;
+  if (p->n_precond < 1 || p->pseudo_kmax < 0) return FR_EINVAL;
+  if (p->pseudo_kmax > 0 && !(p->pseudo_dtau > 0.0)) return FR_EINVAL;
+  if (p->precision != FR_FP64 && p->precision != FR_MIXED) return FR_EINVAL;
+  if (!(p->gamma >= 0.0) || !(p->eps >= 0.0) || !(p->delta > 0.0) || !(p->kappa > 0.0)) return FR_EINVAL;
+  if (!(p->nu_max >= 0.0) || !std::isfinite(p->tau) || !std::isfinite(p->tau_psi)) return FR_EINVAL;
+  const fr_velocity& v = p->vel;
+  if (v.kind < 0 || v.kind > 4) return FR_EINVAL;
+  if (v.kind == FR_VEL_STREAM) {
+    if (v.n_modes < 1 || v.n_modes > FR_MAX_MODES) return FR_EINVAL;
+    if (!v.kx || !v.ky || !v.A || !v.B) return FR_EINVAL;
+  }
+  return FR_OK;
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return FR_ECUDA;    \
+  } while (0)
+
+// ---- small kernels ---------------------------------------------------------
+template <typename T>
+__global__ void k_reset_psi(KArgs A, int64_t NU) {
+  const int64_t n = A.E * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / NU, i = g % NU;
+    const double p0 = A.u[(e * 2 + 0) * NU + i] - 0.5;
+    A.psi0[g] = p0;
+    A.u[(e * 2 + 1) * NU + i] = p0;
+    reinterpret_cast<T*>(A.ustg)[(e * 2 + 1) * NU + i] = (T)p0;
+  }
+}
+
+template <typename T>
+__global__ void k_to_stage(KArgs A, int64_t NU) {
+  const int64_t n = A.E * 2 * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    reinterpret_cast<T*>(A.ustg)[g] = (T)A.u[g];
+}
+
+// Neumaier two-term accumulation
+__device__ __forceinline__ void neu_add(double& s, double& c, double x) {
+  const double t = s + x;
+  c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+// Compensated, fixed-order integral of field `fld` with weights wdet.
+__global__ void k_mass(KArgs A, int64_t NU, int fld) {
+  __shared__ double ss[kThreads], sc[kThreads];
+  __shared__ bool last;
+  const int64_t n = A.E * NU;
+  double s = 0.0, c = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / NU, i = g % NU;
+    neu_add(s, c, A.wdet[g] * A.u[(e * 2 + fld) * NU + i]);
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bs = 0.0, bc = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      neu_add(bs, bc, ss[t]);
+      bc += sc[t];
+    }
+    A.red[2 * blockIdx.x] = bs;
+    A.red[2 * blockIdx.x + 1] = bc;
+    __threadfence();
+    last = atomicAdd(&A.status[ST_COUNTER], 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double ts = 0.0, tc = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      neu_add(ts, tc, ((volatile double*)A.red)[2 * b]);
+      tc += ((volatile double*)A.red)[2 * b + 1];
+    }
+    A.dstate[DS_MASS] = ts + tc;
+    A.status[ST_COUNTER] = 0;
+  }
+}
+
+}  // namespace
+
+struct fr_field {
+  int dim = 0, etype = 0, order = 0, nu = 0, nf = 0, precision = 0;
+  int64_t E = 0;
+  KArgs args{};
+  KernelSet ks{};
+  fr_params prm{};
+  int64_t nstep = 0;
+  int64_t n_precond_done = 0;
+  int sticky = FR_OK;
+  int mass_grid = 1;
+};
+
+namespace {
+
+void launch_elementwise_grid(int64_t n, int* grid) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  *grid = (int)g;
+}
+
+int stage_and_traces(fr_field* f, cudaStream_t s) {
+  int grid;
+  launch_elementwise_grid(f->E * 2 * f->nu, &grid);
+  if (f->precision == FR_FP64) k_to_stage<double><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  else k_to_stage<float><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  KArgs a = f->args;
+  a.stage = 0;
+  f->ks.ka[0](a, s);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+int run_precondition(fr_field* f, cudaStream_t s) {
+  CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
+  int grid;
+  launch_elementwise_grid(f->E * f->nu, &grid);
+  if (f->precision == FR_FP64) k_reset_psi<double><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  else k_reset_psi<float><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  KArgs a = f->args;
+  a.stage = 0;
+  a.dt = f->prm.pseudo_dtau;
+  a.use_dev_time = 0;
+  f->ks.ka[1](a, s);
+  for (int k = 0; k < f->prm.pseudo_kmax; ++k)
+    for (int st = 1; st <= 4; ++st) {
+      a.stage = st;
+      f->ks.kb[1](a, s);
+      f->ks.ka[1](a, s);
+    }
+  CK(cudaGetLastError());
+  f->n_precond_done++;
+  return FR_OK;
+}
+
+int run_step(fr_field* f, cudaStream_t s) {
+  if (f->nstep > 0 && f->nstep % f->prm.n_precond == 0) {
+    const int rc = run_precondition(f, s);
+    if (rc) return rc;
+  }
+  KArgs a = f->args;
+  a.use_dev_time = 1;
+  a.dt = f->prm.dt;
+  for (int st = 1; st <= 4; ++st) {
+    a.stage = st;
+    f->ks.kb[0](a, s);
+    f->ks.ka[0](a, s);
+  }
+  CK(cudaGetLastError());
+  f->nstep++;
+  return FR_OK;
+}
+
+int read_status(fr_field* f, cudaStream_t s) {
+  int32_t st[ST_WORDS];
+  CK(cudaMemcpyAsync(st, f->args.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[ST_STATUS] != 0 && f->sticky == FR_OK) f->sticky = st[ST_STATUS];
+  return f->sticky;
+}
+
+}  // namespace
+
+extern "C" int fr_field_workspace_bytes(const fr_mesh* m, const fr_params* prm, size_t* bytes) {
+  if (!m || !bytes) return FR_EINVAL;
+  int rc = check_params(prm);
+  if (rc) return rc;
+  KernelSet ks;
+  if (!get_kernels(*m, prm->precision, &ks)) return FR_EUNSUPPORTED;
+  int mg;
+  launch_elementwise_grid(m->E * m->nu, &mg);
+  const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
+  *bytes = make_layout(*m, prm->precision, mb).total;
+  return FR_OK;
+}
+
+extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic* ic, void* ws,
+                             size_t ws_bytes, void* stream, fr_field** out) {
+  if (!m || !ic || !out) return FR_EINVAL;
+  *out = nullptr;
+  int rc = check_params(prm);
+  if (rc) return rc;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return FR_EINVAL;
+  KernelSet ks;
+  if (!get_kernels(*m, prm->precision, &ks)) return FR_EUNSUPPORTED;
+  int mg;
+  launch_elementwise_grid(m->E * m->nu, &mg);
+  const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
+  const Layout L = make_layout(*m, prm->precision, mb);
+  if (ws_bytes < L.total) return FR_ENOMEM;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  // initial phi at the solution points
+  const int64_t ndof = m->E * m->nu;
+  std::vector<double> phi(ndof);
+  if (ic->kind == FR_IC_CIRCLE) {
+    for (int64_t g = 0; g < ndof; ++g) {
+      double r2 = 0.0;
+      for (int c = 0; c < m->dim; ++c) {
+        const double d = m->xu[g * m->dim + c] - ic->centre[c];
+        r2 += d * d;
+      }
+      phi[g] = 0.5 * (1.0 + std::tanh(ic->beta * (ic->radius - std::sqrt(r2))));
+    }
+  } else if (ic->kind == FR_IC_ARRAY) {
+    if (!ic->phi0) return FR_EINVAL;
+    std::memcpy(phi.data(), ic->phi0, ndof * sizeof(double));
+  } else {
+    return FR_EINVAL;
+  }
+  for (int64_t g = 0; g < ndof; ++g)
+    if (!std::isfinite(phi[g])) return FR_ENONFINITE;
+
+  fr_field* f = new (std::nothrow) fr_field();
+  if (!f) return FR_ENOMEM;
+  f->dim = m->dim;
+  f->etype = m->etype;
+  f->order = m->order;
+  f->nu = m->nu;
+  f->nf = m->nf;
+  f->E = m->E;
+  f->precision = prm->precision;
+  f->prm = *prm;
+  f->ks = ks;
+  launch_elementwise_grid(ndof, &f->mass_grid);
+
+  char* b = reinterpret_cast<char*>(ws);
+  KArgs& A = f->args;
+  A.E = m->E;
+  A.status = reinterpret_cast<int32_t*>(b + L.status);
+  A.dstate = reinterpret_cast<double*>(b + L.dstate);
+  A.red = reinterpret_cast<double*>(b + L.red);
+  A.geo = reinterpret_cast<const double*>(b + L.geo);
+  A.fnbr = reinterpret_cast<const int32_t*>(b + L.fnbr);
+  A.wdet = reinterpret_cast<const double*>(b + L.wdet);
+  A.ustg = b + L.ustg;
+  A.u = reinterpret_cast<double*>(b + L.u);
+  A.acc = reinterpret_cast<double*>(b + L.acc);
+  A.rp = b + L.rp;
+  A.tr = b + L.tr;
+  A.fc = b + L.fc;
+  A.psi0 = reinterpret_cast<double*>(b + L.psi0);
+  A.out = nullptr;
+  A.stage = 0;
+  A.use_dev_time = 0;
+  A.t = 0.0;
+  A.dt = prm->dt;
+  A.prm.gamma = prm->gamma;
+  A.prm.eps = prm->eps;
+  A.prm.tau = prm->tau;
+  A.prm.tau_psi = prm->tau_psi;
+  A.prm.tau_pseudo = prm->tau_pseudo;
+  A.prm.delta = prm->delta;
+  A.prm.s0 = prm->s0;
+  A.prm.kappa = prm->kappa;
+  A.prm.nu_max = prm->nu_max;
+  A.prm.pseudo_tol = prm->pseudo_tol;
+  A.prm.pseudo_fixed = prm->pseudo_fixed;
+  std::memset(&A.vel, 0, sizeof(A.vel));
+  A.vel.kind = prm->vel.kind;
+  A.vel.T = prm->vel.T;
+  for (int c = 0; c < 3; ++c) A.vel.a[c] = prm->vel.a[c];
+  if (prm->vel.kind == FR_VEL_STREAM) {
+    A.vel.n_modes = prm->vel.n_modes;
+    for (int k = 0; k < prm->vel.n_modes; ++k) {
+      A.vel.kx[k] = prm->vel.kx[k];
+      A.vel.ky[k] = prm->vel.ky[k];
+      A.vel.A[k] = prm->vel.A[k];
+      A.vel.B[k] = prm->vel.B[k];
+    }
+  }
+  std::memset(&A.ops, 0, sizeof(A.ops));
+  if (m->etype != FR_TRI) {
+    const Tensor1D& t = m->t1;
+    for (int i = 0; i < t.n; ++i) {
+      A.ops.x[i] = t.x[i];
+      A.ops.lend[0][i] = t.lend[0][i];
+      A.ops.lend[1][i] = t.lend[1][i];
+      A.ops.gLd[i] = t.gLd[i];
+      A.ops.gRd[i] = t.gRd[i];
+      for (int j = 0; j < t.n; ++j) {
+        A.ops.D[i][j] = t.D[i][j];
+        A.ops.Vinv[i][j] = t.Vinv[i][j];
+      }
+    }
+  }
+
+  int err = FR_OK;
+  auto up = [&](size_t off, const void* src, size_t bytes) {
+    if (err == FR_OK && cudaMemcpyAsync(b + off, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      err = FR_ECUDA;
+  };
+  up(L.geo, m->geo.data(), m->geo.size() * sizeof(double));
+  up(L.fnbr, m->fnbr.data(), m->fnbr.size() * sizeof(int32_t));
+  up(L.wdet, m->wdet.data(), m->wdet.size() * sizeof(double));
+  if (m->etype == FR_TRI) {
+    const TriRef& t = m->tri;
+    up(L.tri_xu, t.xu.data(), t.xu.size() * 8);
+    up(L.tri_xf, t.xf.data(), t.xf.size() * 8);
+    up(L.tri_nref, t.nref.data(), t.nref.size() * 8);
+    up(L.tri_L, t.L.data(), t.L.size() * 8);
+    up(L.tri_Dr, t.Dr.data(), t.Dr.size() * 8);
+    up(L.tri_Ds, t.Ds.data(), t.Ds.size() * 8);
+    up(L.tri_LIFT, t.LIFT.data(), t.LIFT.size() * 8);
+    up(L.tri_Vinv, t.Vinv.data(), t.Vinv.size() * 8);
+    up(L.tri_high, t.high.data(), t.high.size());
+    A.tri.xu = reinterpret_cast<const double*>(b + L.tri_xu);
+    A.tri.xf = reinterpret_cast<const double*>(b + L.tri_xf);
+    A.tri.nref = reinterpret_cast<const double*>(b + L.tri_nref);
+    A.tri.L = reinterpret_cast<const double*>(b + L.tri_L);
+    A.tri.Dr = reinterpret_cast<const double*>(b + L.tri_Dr);
+    A.tri.Ds = reinterpret_cast<const double*>(b + L.tri_Ds);
+    A.tri.LIFT = reinterpret_cast<const double*>(b + L.tri_LIFT);
+    A.tri.Vinv = reinterpret_cast<const double*>(b + L.tri_Vinv);
+    A.tri.high = reinterpret_cast<const uint8_t*>(b + L.tri_high);
+  }
+  // u = [phi, phi - 1/2] element-major
+  std::vector<double> u0(m->E * 2 * m->nu);
+  for (int64_t e = 0; e < m->E; ++e)
+    for (int i = 0; i < m->nu; ++i) {
+      u0[(e * 2 + 0) * m->nu + i] = phi[e * m->nu + i];
+      u0[(e * 2 + 1) * m->nu + i] = phi[e * m->nu + i] - 0.5;
+    }
+  up(L.u, u0.data(), u0.size() * sizeof(double));
+  std::vector<double> p0(ndof);
+  for (int64_t g = 0; g < ndof; ++g) p0[g] = phi[g] - 0.5;
+  up(L.psi0, p0.data(), p0.size() * sizeof(double));
+  if (err == FR_OK && cudaMemsetAsync(b + L.status, 0, ST_WORDS * sizeof(int32_t), s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && cudaMemsetAsync(b + L.dstate, 0, DS_WORDS * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && cudaMemsetAsync(b + L.acc, 0, m->E * 2 * m->nu * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && cudaMemsetAsync(b + L.fc, 0, L.psi0 - L.fc, s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK) err = stage_and_traces(f, s);
+  if (err == FR_OK && ic->precondition) err = run_precondition(f, s);
+  if (err == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && cudaGetLastError() != cudaSuccess) err = FR_ECUDA;
+  if (err != FR_OK) {
+    delete f;
+    return err;
+  }
+  err = read_status(f, s);
+  *out = f;
+  return err;
+}
+
+extern "C" int fr_step(fr_field* f, int n_steps, void* stream) {
+  if (!f || n_steps < 0) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int n = 0; n < n_steps; ++n) {
+    const int rc = run_step(f, s);
+    if (rc) return rc;
+  }
+  return f->sticky;
+}
+
+extern "C" int fr_precondition(fr_field* f, void* stream) {
+  if (!f) return FR_EINVAL;
+  return run_precondition(f, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fr_sync(fr_field* f, void* stream) {
+  if (!f) return FR_EINVAL;
+  return read_status(f, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fr_stats_get(fr_field* f, void* stream, fr_stats* out) {
+  if (!f || !out) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t st[ST_WORDS];
+  double ds[DS_WORDS];
+  CK(cudaMemcpyAsync(st, f->args.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ds, f->args.dstate, sizeof(ds), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[ST_STATUS] != 0 && f->sticky == FR_OK) f->sticky = st[ST_STATUS];
+  out->n_steps = f->nstep;
+  out->t = ds[DS_TIME];
+  out->last_pseudo_iters = st[ST_PSEUDO_ITERS];
+  out->status = f->sticky;
+  out->last_pseudo_rms = ds[DS_PSEUDO_RMS];
+  out->n_preconditions = f->n_precond_done;
+  return FR_OK;
+}
+
+extern "C" int fr_mass_integral(fr_field* f, int which, double* out_host, void* stream) {
+  if (!f || !out_host || which < 0 || which > 1) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  k_mass<<<f->mass_grid, kThreads, 0, s>>>(f->args, f->nu, which);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out_host, f->args.dstate + DS_MASS, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+namespace {
+int copy_field(fr_field* f, int which, void* dst, const void* src, bool to_state, cudaMemcpyKind kind,
+               cudaStream_t s) {
+  const size_t NU = f->nu, E = f->E;
+  if (which == 2) {
+    if (to_state) CK(cudaMemcpyAsync(f->args.psi0, src, E * NU * 8, kind, s));
+    else CK(cudaMemcpyAsync(dst, f->args.psi0, E * NU * 8, kind, s));
+    return FR_OK;
+  }
+  if (to_state)
+    CK(cudaMemcpy2DAsync(f->args.u + which * NU, 2 * NU * 8, src, NU * 8, NU * 8, E, kind, s));
+  else
+    CK(cudaMemcpy2DAsync(dst, NU * 8, f->args.u + which * NU, 2 * NU * 8, NU * 8, E, kind, s));
+  return FR_OK;
+}
+}  // namespace
+
+extern "C" int fr_field_get(fr_field* f, int which, double* host, void* stream) {
+  if (!f || !host || which < 0 || which > 2) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = copy_field(f, which, host, nullptr, false, cudaMemcpyDeviceToHost, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+extern "C" int fr_field_set(fr_field* f, int which, const double* host, void* stream) {
+  if (!f || !host || which < 0 || which > 2) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = copy_field(f, which, nullptr, host, true, cudaMemcpyHostToDevice, s);
+  if (rc) return rc;
+  if (which < 2) rc = stage_and_traces(f, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+extern "C" int fr_field_get_device(fr_field* f, int which, double* dev, void* stream) {
+  if (!f || !dev || which < 0 || which > 2) return FR_EINVAL;
+  return copy_field(f, which, dev, nullptr, false, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fr_field_set_device(fr_field* f, int which, const double* dev, void* stream) {
+  if (!f || !dev || which < 0 || which > 2) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = copy_field(f, which, nullptr, dev, true, cudaMemcpyDeviceToDevice, s);
+  if (rc) return rc;
+  return which < 2 ? stage_and_traces(f, s) : FR_OK;
+}
+
+extern "C" int fr_rhs(fr_field* f, double t, double* dev_out, void* stream) {
+  if (!f || !dev_out) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KArgs a = f->args;
+  a.use_dev_time = 0;
+  a.t = t;
+  a.stage = 1;
+  a.dt = f->prm.dt;
+  f->ks.kb[0](a, s);
+  a.stage = -1;
+  a.out = dev_out;
+  f->ks.ka[0](a, s);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+extern "C" int fr_rhs_pseudo(fr_field* f, double* dev_out, void* stream) {
+  if (!f || !dev_out) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, sizeof(int32_t), s));
+  KArgs a = f->args;
+  a.use_dev_time = 0;
+  a.stage = 1;
+  a.dt = f->prm.pseudo_dtau;
+  f->ks.kb[1](a, s);
+  a.stage = -1;
+  a.out = dev_out;
+  f->ks.ka[1](a, s);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+extern "C" void fr_field_destroy(fr_field* f) { delete f; }
+
+extern "C" const char* fr_strerror(int code) {
+  switch (code) {
+    case FR_OK: return "ok";
+    case FR_EINVAL: return "invalid argument";
+    case FR_ENOMEM: return "out of memory or workspace too small";
+    case FR_ECUDA: return "CUDA runtime error";
+    case FR_ENONFINITE: return "non-finite value in the state";
+    case FR_ETIMEOUT: return "bounded device wait timed out";
+    case FR_EUNSUPPORTED: return "element type, order or mode not supported";
+    default: return "unknown error";
+  }
+}
+
+extern "C" int fr_version(void) { return 100; }

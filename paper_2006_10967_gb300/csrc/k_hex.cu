@@ -1,0 +1,17 @@
+// Hexahedron kernel instantiations (p = 1..5, fp64 and mixed).
+#include "k_tensor_inst.cuh"
+
+namespace frp {
+bool kernels_hex(int order, int precision, int64_t E, KernelSet* ks) {
+#define FRP_H(P)                                                        \
+  case P:                                                               \
+    if (precision == 0) fill_tensor<3, P + 1, double>(E, ks);           \
+    else fill_tensor<3, P + 1, float>(E, ks);                           \
+    return true;
+  switch (order) {
+    FRP_H(1) FRP_H(2) FRP_H(3) FRP_H(4) FRP_H(5)
+    default: return false;
+  }
+#undef FRP_H
+}
+}  // namespace frp

@@ -1,0 +1,44 @@
+// Instantiation helpers for the tensor kernels (included by k_quad.cu, k_hex.cu).
+#pragma once
+#include "kdispatch.hpp"
+#include "ktensor.cuh"
+
+namespace frp {
+
+template <int DIM, int N, typename T, int MODE>
+void launch_kb_tensor(const KArgs& A, cudaStream_t s) {
+  using LY = KBLayout<DIM, N, T, MODE>;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+    init = true;
+  }
+  launch_kernel(kb_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s);
+}
+
+template <int DIM, int N, typename T, int MODE>
+void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
+  using LY = KALayout<DIM, N, T, MODE>;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+    init = true;
+  }
+  launch_kernel(ka_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s);
+}
+
+template <int DIM, int N, typename T>
+void fill_tensor(int64_t E, KernelSet* ks) {
+  ks->kb[0] = launch_kb_tensor<DIM, N, T, 0>;
+  ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;
+  ks->ka[0] = launch_ka_tensor<DIM, N, T, 0>;
+  ks->ka[1] = launch_ka_tensor<DIM, N, T, 1>;
+  const int et_min = KBLayout<DIM, N, T, 0>::ET < KALayout<DIM, N, T, 0>::ET ? KBLayout<DIM, N, T, 0>::ET
+                                                                              : KALayout<DIM, N, T, 0>::ET;
+  const int et_min1 = KBLayout<DIM, N, T, 1>::ET < KALayout<DIM, N, T, 1>::ET ? KBLayout<DIM, N, T, 1>::ET
+                                                                               : KALayout<DIM, N, T, 1>::ET;
+  const int et = et_min < et_min1 ? et_min : et_min1;
+  ks->max_blocks = (int)((E + et - 1) / et);
+}
+
+}  // namespace frp

@@ -1,0 +1,435 @@
+// FR kernels for straight-sided triangles (affine map, constant J per
+// element) with dense reference operators: the same Steps 1-6 and kernel
+// split as ktensor.cuh, with the line applies replaced by small dense
+// matrix-vector products staged in shared memory.
+#pragma once
+#include "kcommon.cuh"
+
+namespace frp {
+
+template <int P>
+struct TriS {
+  static constexpr int N = P + 1;
+  static constexpr int NU = N * (N + 1) / 2;
+  static constexpr int NF = 3 * N;
+  static constexpr int NG = 6;
+};
+
+template <int P, typename T>
+struct TriOpsS {
+  static constexpr int NU = TriS<P>::NU, NF = TriS<P>::NF;
+  T L[NF][NU], Dr[NU][NU], Ds[NU][NU], LIFT[NU][NF], Vinv[NU][NU];
+  T xf[NF][2], nref[NF][2];
+  unsigned char high[NU];
+};
+
+template <int P, typename T>
+__device__ __forceinline__ void load_tri_ops(const TriOps& o, TriOpsS<P, T>& s) {
+  constexpr int NU = TriS<P>::NU, NF = TriS<P>::NF;
+  for (int t = threadIdx.x; t < NF * NU; t += blockDim.x) {
+    s.L[t / NU][t % NU] = (T)o.L[t];
+    s.LIFT[t / NF][t % NF] = (T)o.LIFT[t];
+  }
+  for (int t = threadIdx.x; t < NU * NU; t += blockDim.x) {
+    s.Dr[t / NU][t % NU] = (T)o.Dr[t];
+    s.Ds[t / NU][t % NU] = (T)o.Ds[t];
+    s.Vinv[t / NU][t % NU] = (T)o.Vinv[t];
+  }
+  for (int t = threadIdx.x; t < NF * 2; t += blockDim.x) {
+    s.xf[t / 2][t % 2] = (T)o.xf[t];
+    s.nref[t / 2][t % 2] = (T)o.nref[t];
+  }
+  for (int t = threadIdx.x; t < NU; t += blockDim.x) s.high[t] = o.high[t];
+}
+
+// per-element metric of the affine map: S = det J J^{-1}, det J
+template <typename T>
+struct TriMet {
+  T S[2][2];
+  T dj;
+};
+
+template <typename T>
+__device__ __forceinline__ void tri_metric(const T* g, TriMet<T>& m) {
+  T J[3][3], Sm[3][3];
+  const T xi[2] = {0, 0};
+  jacobian<ET_TRI, T>(g, xi, J);
+  m.dj = adjugate<2, T>(J, Sm);
+  m.S[0][0] = Sm[0][0];
+  m.S[0][1] = Sm[0][1];
+  m.S[1][0] = Sm[1][0];
+  m.S[1][1] = Sm[1][1];
+}
+
+template <int P, typename T, int MODE>
+struct KBTriLayout {
+  using S = TriS<P>;
+  static constexpr int NFLD = MODE == 0 ? 2 : 1;
+  static constexpr int PER_EL_T = NFLD * S::NU + 3 * NFLD * S::NF + NFLD * 2 * S::NU + S::NG + 5 + 1;
+  static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + S::NF;
+  static constexpr int ETr = 32768 / BYTES_EL;
+  static constexpr int ET = ETr < 1 ? 1 : (ETr > 64 ? 64 : ETr);
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
+};
+
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
+  using S = TriS<P>;
+  using LY = KBTriLayout<P, T, MODE>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET, N = S::N;
+  constexpr int F0 = MODE == 0 ? 0 : 1;
+  if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TriOpsS<P, T>& op = *reinterpret_cast<TriOpsS<P, T>*>(smem_raw);
+  T* base = reinterpret_cast<T*>(smem_raw + ((sizeof(TriOpsS<P, T>) + 15) & ~size_t(15)));
+  T* us = base;                         // [ET][NFLD][NU]
+  T* uf = us + ET * NFLD * NU;          // [ET][NFLD][NF]
+  T* uo = uf + ET * NFLD * NF;
+  T* cor = uo + ET * NFLD * NF;
+  T* q = cor + ET * NFLD * NF;          // [ET][NFLD][2][NU]
+  T* gs = q + ET * NFLD * 2 * NU;       // [ET][NG]
+  T* met = gs + ET * NG;                // [ET][5]: S00 S01 S10 S11 dj
+  T* nus = met + ET * 5;                // [ET]
+  unsigned char* lm = reinterpret_cast<unsigned char*>(nus + ET);
+
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)min((int64_t)ET, A.E - e0);
+  const T* ustg = reinterpret_cast<const T*>(A.ustg);
+  const T* tr = reinterpret_cast<const T*>(A.tr);
+  T* fc = reinterpret_cast<T*>(A.fc);
+  T* rp = reinterpret_cast<T*>(A.rp);
+  const int tid = threadIdx.x;
+  const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
+
+  load_tri_ops<P, T>(A.tri, op);
+  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+    us[idx] = ustg[((e0 + el) * 2 + F0 + fld) * NU + i];
+  }
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  __syncthreads();
+  for (int el = tid; el < ne; el += blockDim.x) {
+    TriMet<T> m;
+    tri_metric(gs + el * NG, m);
+    met[el * 5 + 0] = m.S[0][0];
+    met[el * 5 + 1] = m.S[0][1];
+    met[el * 5 + 2] = m.S[1][0];
+    met[el * 5 + 3] = m.S[1][1];
+    met[el * 5 + 4] = m.dj;
+  }
+  // ---- Step 1 and partner traces
+  for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+    const int el = idx / NF, k = idx % NF;
+    const int32_t w = A.fnbr[(e0 + el) * NF + k];
+    const int isL = w & 1;
+    const int64_t pg = (int64_t)(w >> 1), pe = pg / NF, pk = pg % NF;
+    lm[el * NF + k] = (unsigned char)isL;
+#pragma unroll
+    for (int fld = 0; fld < NFLD; ++fld) {
+      const T* ul = us + (el * NFLD + fld) * NU;
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ul[j];
+      uf[(el * NFLD + fld) * NF + k] = acc;
+      uo[(el * NFLD + fld) * NF + k] = isL ? tr[(pe * 2 + F0 + fld) * NF + pk] : acc;
+    }
+  }
+  __syncthreads();
+  // ---- Step 3
+  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+    const int el = idx / NU, i = idx % NU;
+    const T* mt = met + el * 5;
+    const T rdj = (T)1 / mt[4];
+#pragma unroll
+    for (int fld = 0; fld < NFLD; ++fld) {
+      const T* ul = us + (el * NFLD + fld) * NU;
+      const T* fo = uo + (el * NFLD + fld) * NF;
+      const T* ff = uf + (el * NFLD + fld) * NF;
+      T q0 = 0, q1 = 0;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        q0 += op.Dr[i][j] * ul[j];
+        q1 += op.Ds[i][j] * ul[j];
+      }
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        const T jmp = lm[el * NF + k] ? fo[k] - ff[k] : (T)0;
+        const T lj = op.LIFT[i][k] * jmp;
+        q0 += lj * op.nref[k][0];
+        q1 += lj * op.nref[k][1];
+      }
+      // q_b = sum_a S[a][b] q~_a / det J
+      q[((el * NFLD + fld) * 2 + 0) * NU + i] = (mt[0] * q0 + mt[2] * q1) * rdj;
+      q[((el * NFLD + fld) * 2 + 1) * NU + i] = (mt[1] * q0 + mt[3] * q1) * rdj;
+    }
+  }
+  if (MODE == 1) {
+    for (int el = tid; el < ne; el += blockDim.x) {
+      const T* ul = us + el * NU;
+      double tot = 0.0, hi = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        T c = 0;
+        for (int j = 0; j < NU; ++j) c += op.Vinv[m][j] * ul[j];
+        const double v = (double)c * (double)c;
+        tot += v;
+        if (op.high[m]) hi += v;
+      }
+      double nu = 0.0;
+      if (tot > 0.0 && hi > 0.0) {
+        const double se = log10(hi / tot);
+        const double lo = A.prm.s0 - A.prm.kappa, up = A.prm.s0 + A.prm.kappa;
+        if (se < lo) nu = 0.0;
+        else if (se > up) nu = A.prm.nu_max;
+        else nu = 0.5 * A.prm.nu_max * (1.0 + sin(M_PI * (se - A.prm.s0) / (2.0 * A.prm.kappa)));
+      }
+      nus[el] = (T)nu;
+    }
+  }
+  __syncthreads();
+  // ---- Step 5 on L points
+  for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+    const int el = idx / NF, k = idx % NF;
+    if (!lm[el * NF + k]) {
+#pragma unroll
+      for (int fld = 0; fld < NFLD; ++fld) cor[(el * NFLD + fld) * NF + k] = 0;
+      continue;
+    }
+    const T* mt = met + el * 5;
+    T pn[2];
+    pn[0] = mt[0] * op.nref[k][0] + mt[2] * op.nref[k][1];
+    pn[1] = mt[1] * op.nref[k][0] + mt[3] * op.nref[k][1];
+    const T pm = sqrt_(pn[0] * pn[0] + pn[1] * pn[1]);
+    const T nh[2] = {pn[0] / pm, pn[1] / pm};
+    if (MODE == 0) {
+      T qf[2][2];
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const T* ql = q + ((el * 2 + fld) * 2 + c) * NU;
+          T acc = 0;
+#pragma unroll
+          for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
+          qf[fld][c] = acc;
+        }
+      T x[3], v[3];
+      map_point<ET_TRI, T>(gs + el * NG, op.xf[k], x);
+      velocity<2, T>(A.vel, x, tstage, v);
+      const T vn = v[0] * nh[0] + v[1] * nh[1];
+      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), (T)A.prm.gamma);
+      const T gm = fmax(sqrt_(qf[1][0] * qf[1][0] + qf[1][1] * qf[1][1]), (T)A.prm.delta);
+      const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
+      const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
+      const T sharp = (T)A.prm.gamma * pL * ((T)1 - pL) / gm;
+      T fvn = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * ((T)A.prm.eps * qf[0][c] - sharp * qf[1][c]);
+      const T Fp = (T)0.5 * (pL + pR) * vn - fvn + (T)A.prm.tau * (pL - pR);
+      const T Fs = (T)0.5 * (sL + sR) * vn + (T)A.prm.tau_psi * (sL - sR);
+      fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
+      fc[((e0 + el) * 2 + 1) * NF + k] = Fs;
+      cor[(el * 2 + 0) * NF + k] = pm * Fp;
+      cor[(el * 2 + 1) * NF + k] = pm * Fs;
+    } else {
+      T gn = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T* ql = q + (el * 2 + c) * NU;
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
+        gn += nh[c] * acc;
+      }
+      const T F = -nus[el] * gn + (T)A.prm.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
+      fc[((e0 + el) * 2 + 1) * NF + k] = F;
+      cor[el * NF + k] = pm * F;
+    }
+  }
+  __syncthreads();
+  // ---- Step 4
+  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+    const int el = idx / NU, i = idx % NU;
+    const T* mt = met + el * 5;
+    if (MODE == 0) {
+      T xi[2], x[3], v[3];
+      // solution point reference coordinates are those of the lattice
+      {
+        int c = 0, jj = 0, ii = 0;
+        for (int j = 0; j <= P; ++j)
+          for (int i2 = 0; i2 <= P - j; ++i2, ++c)
+            if (c == i) { jj = j; ii = i2; }
+        xi[0] = (T)(2.0 * (ii + 1) / (P + 3) - 1.0);
+        xi[1] = (T)(2.0 * (jj + 1) / (P + 3) - 1.0);
+      }
+      map_point<ET_TRI, T>(gs + el * NG, xi, x);
+      velocity<2, T>(A.vel, x, tstage, v);
+      const T qp0 = q[((el * 2 + 0) * 2 + 0) * NU + i], qp1 = q[((el * 2 + 0) * 2 + 1) * NU + i];
+      const T qs0 = q[((el * 2 + 1) * 2 + 0) * NU + i], qs1 = q[((el * 2 + 1) * 2 + 1) * NU + i];
+      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), (T)A.prm.gamma);
+      const T gm = fmax(sqrt_(qs0 * qs0 + qs1 * qs1), (T)A.prm.delta);
+      const T ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];
+      const T sharp = (T)A.prm.gamma * ph * ((T)1 - ph) / gm;
+      const T f00 = ph * v[0] - M * ((T)A.prm.eps * qp0 - sharp * qs0);
+      const T f01 = ph * v[1] - M * ((T)A.prm.eps * qp1 - sharp * qs1);
+      const T f10 = ps * v[0], f11 = ps * v[1];
+      q[((el * 2 + 0) * 2 + 0) * NU + i] = mt[0] * f00 + mt[1] * f01;
+      q[((el * 2 + 0) * 2 + 1) * NU + i] = mt[2] * f00 + mt[3] * f01;
+      q[((el * 2 + 1) * 2 + 0) * NU + i] = mt[0] * f10 + mt[1] * f11;
+      q[((el * 2 + 1) * 2 + 1) * NU + i] = mt[2] * f10 + mt[3] * f11;
+    } else {
+      const T qs0 = q[(el * 2 + 0) * NU + i], qs1 = q[(el * 2 + 1) * NU + i];
+      const T nu = nus[el];
+      q[(el * 2 + 0) * NU + i] = mt[0] * (-nu * qs0) + mt[1] * (-nu * qs1);
+      q[(el * 2 + 1) * NU + i] = mt[2] * (-nu * qs0) + mt[3] * (-nu * qs1);
+      const T qm = sqrt_(qs0 * qs0 + qs1 * qs1);
+      const T p0 = (T)A.psi0[(e0 + el) * NU + i];
+      us[el * NU + i] = tanh_(p0 / fmax(qm, (T)A.prm.delta)) * ((T)1 - qm) * mt[4];
+    }
+  }
+  __syncthreads();
+  // ---- normal discontinuous flux and jumps
+  for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
+    const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
+    const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
+    const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
+    T a0 = 0, a1 = 0;
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      a0 += op.L[k][j] * f0[j];
+      a1 += op.L[k][j] * f1[j];
+    }
+    cor[idx] = cor[idx] - (op.nref[k][0] * a0 + op.nref[k][1] * a1);
+  }
+  __syncthreads();
+  // ---- Step 6
+  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+    const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
+    const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
+    const T* cr = cor + (el * NFLD + fld) * NF;
+    T div = 0;
+#pragma unroll
+    for (int j = 0; j < NU; ++j) div += op.Dr[i][j] * f0[j] + op.Ds[i][j] * f1[j];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * cr[k];
+    if (MODE == 1) div -= us[el * NU + i];
+    rp[((e0 + el) * 2 + F0 + fld) * NU + i] = div;
+  }
+  (void)N;
+}
+
+template <int P, typename T, int MODE>
+struct KATriLayout {
+  using S = TriS<P>;
+  static constexpr int NFLD = MODE == 0 ? 2 : 1;
+  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1) * (int)sizeof(T);
+  static constexpr int ETr = 16384 / BYTES_EL;
+  static constexpr int ET = ETr < 1 ? 1 : (ETr > 128 ? 128 : ETr);
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
+};
+
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
+  using S = TriS<P>;
+  using LY = KATriLayout<P, T, MODE>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET;
+  constexpr int F0 = MODE == 0 ? 0 : 1;
+  if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sh[32];
+  TriOpsS<P, T>& op = *reinterpret_cast<TriOpsS<P, T>*>(smem_raw);
+  T* base = reinterpret_cast<T*>(smem_raw + ((sizeof(TriOpsS<P, T>) + 15) & ~size_t(15)));
+  T* ys = base;
+  T* cr = ys + ET * NFLD * NU;
+  T* gs = cr + ET * NFLD * NF;
+  T* djs = gs + ET * NG;
+
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)min((int64_t)ET, A.E - e0);
+  T* ustg = reinterpret_cast<T*>(A.ustg);
+  T* tr = reinterpret_cast<T*>(A.tr);
+  const T* fc = reinterpret_cast<const T*>(A.fc);
+  const T* rp = reinterpret_cast<const T*>(A.rp);
+  const int tid = threadIdx.x;
+  const int stage = A.stage;
+
+  load_tri_ops<P, T>(A.tri, op);
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+    const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
+    ys[idx] = stage == 0 ? ustg[g] : rp[g];
+  }
+  __syncthreads();
+  double sq = 0.0;
+  if (stage != 0) {
+    for (int el = tid; el < ne; el += blockDim.x) {
+      TriMet<T> m;
+      tri_metric(gs + el * NG, m);
+      djs[el] = m.dj;
+    }
+    for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+      const int el = idx / NF, k = idx % NF;
+      const int32_t w = A.fnbr[(e0 + el) * NF + k];
+      if (w & 1) {
+#pragma unroll
+        for (int fld = 0; fld < NFLD; ++fld) cr[(el * NFLD + fld) * NF + k] = 0;
+        continue;
+      }
+      const int64_t pg = (int64_t)(w >> 1), pe = pg / NF, pk = pg % NF;
+      TriMet<T> m;
+      tri_metric(gs + el * NG, m);
+      const T pn0 = m.S[0][0] * op.nref[k][0] + m.S[1][0] * op.nref[k][1];
+      const T pn1 = m.S[0][1] * op.nref[k][0] + m.S[1][1] * op.nref[k][1];
+      const T pm = sqrt_(pn0 * pn0 + pn1 * pn1);
+#pragma unroll
+      for (int fld = 0; fld < NFLD; ++fld)
+        cr[(el * NFLD + fld) * NF + k] = -pm * fc[(pe * 2 + F0 + fld) * NF + pk];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+      const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+      const T* c = cr + (el * NFLD + fld) * NF;
+      T div = ys[idx];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * c[k];
+      const double R = (double)(-div / djs[el]);
+      const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
+      if (stage < 0) {
+        A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = R;
+        continue;
+      }
+      double uu = A.u[g], aa = stage == 1 ? 0.0 : A.acc[g];
+      const double uold = uu;
+      const double y = rk_update(stage, A.dt, R, uu, aa);
+      if (stage < 4) A.acc[g] = aa;
+      else A.u[g] = uu;
+      if (MODE == 1 && stage == 4) {
+        const double d = (uu - uold) / A.dt;
+        sq += d * d;
+      }
+      if (!isfinite(y)) atomicExch(&A.status[ST_STATUS], -4);
+      const T yt = (T)y;
+      ustg[g] = yt;
+      ys[idx] = yt;
+    }
+    __syncthreads();
+  }
+  if (stage >= 0) {
+    for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
+      const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
+      const T* yl = ys + (el * NFLD + fld) * NU;
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) acc += op.L[k][j] * yl[j];
+      tr[((e0 + el) * 2 + F0 + fld) * NF + k] = acc;
+    }
+  }
+  if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)
+    A.dstate[DS_TIME] = A.dstate[DS_TIME] + A.dt;
+  if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
+}
+
+}  // namespace frp

@@ -1,0 +1,86 @@
+"""Host-side checks of the C-ABI library: it builds, loads, exports every
+declared entry point, and its mesh builder (points, quadrature, face pairing)
+agrees with the oracle's independent construction.  No GPU needed."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from libutil import ensure_built, header_functions
+
+
+@pytest.fixture(scope="module")
+def G():
+    ensure_built()
+    import paper_2006_10967_gb300 as G
+    return G
+
+
+def test_exports_every_declared_symbol(G):
+    L = G.lib()
+    names = header_functions()
+    assert "fr_step" in names and "fr_mesh_create" in names and "fr_mass_integral" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+MESHES = [
+    ("quad", lambda: S.quad_grid(5, jitter=0.12, seed=2, shuffle_seed=3, rotate_seed=4), 3),
+    ("quad", lambda: S.quad_grid(6, periodic=(False, False), jitter=0.1, seed=1, shuffle_seed=11, rotate_seed=12), 4),
+    ("tri", lambda: S.tri_delaunay(7, seed=2, shuffle_seed=13), 3),
+    ("tri", lambda: S.tri_split(4, shuffle_seed=1), 2),
+    ("hex", lambda: S.hex_grid(3, periodic=(True, False, True), jitter=0.1, seed=4, shuffle_seed=5), 2),
+    ("quad", lambda: S.quad_grid(1), 2),
+]
+
+
+@pytest.mark.parametrize("et,mk,p", MESHES)
+def test_mesh_geometry_matches_oracle(G, et, mk, p):
+    from oracle.mesh import build_geometry
+    m = mk()
+    M = G.Mesh.from_synthetic(m, p)
+    geo = build_geometry(m, p)
+    assert M.info.n_elems == m.n_elems
+    assert M.info.nu == geo.el.nu and M.info.nf == geo.el.nf
+    assert np.allclose(M.solution_points(), geo.xu, atol=1e-13)
+    assert np.allclose(M.quadrature(), geo.el.wq[None, :] * geo.detJu, atol=1e-14)
+    assert M.info.h == pytest.approx(geo.h, rel=1e-12)
+    assert M.info.n_boundary_fpts == int(geo.boundary.sum())
+
+
+def test_invalid_meshes_are_rejected(G):
+    m = S.quad_grid(3)
+    with pytest.raises(G.FRError) as e:
+        G.Mesh(m.nodes, np.where(m.conn == 5, 999, m.conn), "quad", 2)
+    assert e.value.code == -1
+    flipped = m.conn[:, ::-1].copy()            # clockwise elements: det J < 0
+    with pytest.raises(G.FRError):
+        G.Mesh(m.nodes, flipped, "quad", 2)
+    with pytest.raises(G.FRError) as e:
+        G.Mesh(m.nodes, m.conn, "quad", 9)      # order not built
+    assert e.value.code == -6
+    bad = m.nodes.copy()
+    bad[3, 0] = np.nan
+    with pytest.raises(G.FRError):
+        G.Mesh(bad, m.conn, "quad", 2)
+    # three elements on one face
+    conn = np.concatenate([m.conn, m.conn[:1]], 0)
+    with pytest.raises(G.FRError):
+        G.Mesh(m.nodes, conn, "quad", 2)
+
+
+def test_workspace_size_and_param_validation(G):
+    w = S.workload("c1")
+    M = G.Mesh.from_synthetic(w.mesh(), w.order)
+    p = G.make_params(w)
+    n = C.c_size_t()
+    assert G.lib().fr_field_workspace_bytes(M.handle, C.byref(p), C.byref(n)) == 0
+    assert n.value > 16 * 16 * 16 * 2 * 8 * 4
+    pm = G.make_params(w, precision="mixed")
+    n2 = C.c_size_t()
+    assert G.lib().fr_field_workspace_bytes(M.handle, C.byref(pm), C.byref(n2)) == 0
+    assert n2.value < n.value
+    p.dt = -1.0
+    assert G.lib().fr_field_workspace_bytes(M.handle, C.byref(p), C.byref(n)) == -1
+    assert G.lib().fr_strerror(-4) == b"non-finite value in the state"

@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances: FP64 path 1e-12 relative (max-norm of the difference over the
+max-norm of the oracle's value) per residual evaluation and per RK step; the
+mixed path 1e-4 relative per residual (float32 stage values and fluxes, unit
+round-off 6e-8, amplified by the FR operator norm ~ (p+1)^2 / h times the flux
+scale over the residual scale).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from libutil import ensure_built
+from oracle import Params, Solver
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_2006_10967_gb300 as G
+    return G
+
+
+def _workload(mesh_fn, p, vel, circle, h, **kw):
+    w = S.Workload("t", mesh_fn, p, vel, circle, t_end=1.0, h=h)
+    w.eps = 0.06 * h / p
+    w.nu_max = 0.15 * h / p
+    w.pseudo_dtau = 0.1 * h / (p + 1)
+    w.dt = 0.1 * h / ((p + 1) * 1.0)
+    for k, v in kw.items():
+        setattr(w, k, v)
+    return w
+
+
+def _pair(G, w, precision="fp64", precondition=False, fixed=True, **okw):
+    mesh = w.mesh()
+    prm = Params.from_workload(w, pseudo_fixed=fixed, **okw)
+    sol = Solver(mesh, w.order, prm, w.velocity)
+    sol.initialize(w.circle, precondition=precondition)
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    P = G.make_params(w, precision, pseudo_fixed=fixed, **okw)
+    F = G.Field(M, P, ic=w.circle, precondition=precondition)
+    return sol, F
+
+
+def _perturb(sol, F):
+    """A generic psi (smooth but not aligned with phi) on both sides."""
+    x = sol.xu
+    pert = 0.05 * torch.sin(5.0 * x[..., 0] + 1.0) * torch.cos(3.0 * x[..., 1])
+    psi = sol.phi - 0.5 + pert
+    sol.psi = psi
+    F.set(1, psi.numpy())
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    "quad_periodic_jitter_p3": lambda: _workload(
+        lambda: S.quad_grid(6, jitter=0.12, seed=3, shuffle_seed=4, rotate_seed=5), 3,
+        S.Velocity("rider_kothe", T=8.0), S.Circle((0.45, 0.55), 0.25, 3 * 3 / (4 / 6)), 1 / 6),
+    "quad_walls_jitter_p4": lambda: _workload(
+        lambda: S.quad_grid(7, 5, periodic=(False, False), jitter=0.1, seed=1, shuffle_seed=11, rotate_seed=12), 4,
+        S.Velocity("rider_kothe", T=8.0), S.Circle((0.5, 0.6), 0.25, 3 * 4 / (4 / 6)), 1 / 6),
+    "quad_stream_p5": lambda: _workload(
+        lambda: S.quad_grid(5, jitter=0.05, seed=8), 5,
+        S.Velocity("stream", T=4.0, **dict(zip(("kx", "ky", "A", "B"), S.stream_coefficients(16, seed=4)))),
+        S.Circle((0.5, 0.5), 0.2, 3 * 5 / (4 / 5)), 1 / 5),
+    "tri_delaunay_p3": lambda: _workload(
+        lambda: S.tri_delaunay(9, seed=2, shuffle_seed=13), 3,
+        S.Velocity("rider_kothe", T=8.0), S.Circle((0.5, 0.6), 0.25, 3 * 3 / (4 / 8)), 1 / 8),
+    "tri_split_periodic_p2": lambda: _workload(
+        lambda: S.tri_split(5, shuffle_seed=1), 2,
+        S.Velocity("rotation"), S.Circle((0.5, 0.6), 0.25, 3 * 2 / (4 / 5)), 1 / 5),
+    "hex_walls_p3": lambda: _workload(
+        lambda: S.hex_grid(3, shuffle_seed=2), 3,
+        S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 3 / (4 / 3)), 1 / 3),
+    "hex_periodic_jitter_p2": lambda: _workload(
+        lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=4), 2,
+        S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 2 / (4 / 3)), 1 / 3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_parity_fp64(G, case):
+    w = CASES[case]()
+    sol, F = _pair(G, w)
+    assert _rel(F.get(0), sol.phi.numpy()) < 1e-14
+    _perturb(sol, F)
+    for t in (0.0, 0.7):
+        R = F.rhs(t).cpu().numpy()
+        Ro = sol.rhs(sol.phi, sol.psi, t)
+        assert _rel(R[0], Ro[0].numpy()) < TOL64, case
+        assert _rel(R[1], Ro[1].numpy()) < TOL64, case
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_pseudo_rhs_parity_fp64(G, case):
+    w = CASES[case]()
+    sol, F = _pair(G, w)
+    _perturb(sol, F)
+    # psi0 = phi - 1/2 on both sides (set at init); the state's psi is perturbed
+    R = F.rhs_pseudo().cpu().numpy()
+    Ro = sol.rhs_pseudo(sol.psi, sol.phi - 0.5).numpy()
+    assert _rel(R, Ro) < TOL64, case
+
+
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "tri_delaunay_p3", "hex_walls_p3"])
+def test_rk_steps_and_preconditioning_parity_fp64(G, case):
+    w = CASES[case]()
+    w.n_precond = 2
+    w.pseudo_kmax = 3
+    sol, F = _pair(G, w, precondition=True)
+    assert _rel(F.get(1), sol.psi.numpy()) < TOL64
+    # psi0 = phi - 1/2 from each side's own tanh of the initial condition
+    assert _rel(F.get(2), sol.psi0.numpy()) < 1e-13
+    for nsteps in (1, 4):
+        F.step(nsteps)
+        sol.step(nsteps)
+        assert _rel(F.get(0), sol.phi.numpy()) < TOL64, case
+        assert _rel(F.get(1), sol.psi.numpy()) < TOL64, case
+    st = F.stats()
+    assert st["n_steps"] == 5 and st["n_preconditions"] == 3
+    assert st["t"] == pytest.approx(sol.t, rel=1e-15)
+
+
+def test_pseudo_stop_rule_matches_oracle(G):
+    w = CASES["quad_periodic_jitter_p3"]()
+    w.pseudo_kmax = 20
+    w.pseudo_tol = 2.0
+    sol, F = _pair(G, w, precondition=True, fixed=False)
+    st = F.stats()
+    assert st["last_pseudo_iters"] == sol.pseudo_iters
+    assert st["last_pseudo_rms"] == pytest.approx(sol.pseudo_rms, rel=1e-10)
+    assert _rel(F.get(1), sol.psi.numpy()) < TOL64
+
+
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "tri_split_periodic_p2", "hex_periodic_jitter_p2"])
+def test_mass_integral_and_conservation(G, case):
+    w = CASES[case]()
+    sol, F = _pair(G, w)
+    m0 = F.mass(0)
+    assert m0 == pytest.approx(float(sol.integral(sol.phi)), rel=1e-14)
+    assert F.mass(1) == pytest.approx(float(sol.integral(sol.psi)), rel=1e-12, abs=1e-15)
+    F.step(10)
+    assert abs(F.mass(0) - m0) < 1e-13 * abs(m0)
+
+
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3"])
+def test_rhs_parity_mixed(G, case):
+    w = CASES[case]()
+    sol, F = _pair(G, w, precision="mixed")
+    _perturb(sol, F)
+    R = F.rhs(0.3).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.3)
+    assert _rel(R[0], Ro[0].numpy()) < TOL32, case
+    assert _rel(R[1], Ro[1].numpy()) < TOL32, case
+    Rp = F.rhs_pseudo().cpu().numpy()
+    assert _rel(Rp, sol.rhs_pseudo(sol.psi, sol.phi - 0.5).numpy()) < TOL32
+
+
+def test_mixed_steps_track_fp64(G):
+    w = CASES["quad_periodic_jitter_p3"]()
+    sol, F64 = _pair(G, w)
+    _, F32 = _pair(G, w, precision="mixed")
+    F64.step(20)
+    F32.step(20)
+    sol.step(20)
+    assert _rel(F64.get(0), sol.phi.numpy()) < TOL64
+    assert _rel(F32.get(0), sol.phi.numpy()) < 1e-5
+
+
+def test_full_size_c2q_rhs_parity(G):
+    """The benchmark's configuration (128^2 jittered quads, p = 4, Rider-Kothe)
+    at full size: every residual value against the oracle."""
+    w = S.workload("c2q")
+    sol, F = _pair(G, w)
+    for t in (0.0, 2.5):
+        R = F.rhs(t).cpu().numpy()
+        Ro = sol.rhs(sol.phi, sol.psi, t)
+        assert _rel(R[0], Ro[0].numpy()) < TOL64
+        assert _rel(R[1], Ro[1].numpy()) < TOL64
+
+
+def test_nonfinite_state_is_reported(G):
+    w = CASES["quad_periodic_jitter_p3"]()
+    sol, F = _pair(G, w)
+    phi = F.get(0)
+    phi[3, 2] = np.nan
+    F.set(0, phi)
+    F.step(1)
+    assert F.sync() == -4
