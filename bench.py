@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the FR-PCPF hot path: FR DOF-stage updates per second.
+
+Workload: 128 x 128 jittered, shuffled quads on [0,1]^2, p = 4 (409,600
+solution points), Rider-Kothe vortex with T = 8, disk r = 0.15 at (0.5, 0.75),
+the paper's parameters (gamma = 0.09, eps = 0.06 h/p, precondition every
+1000 steps with up to 20 pseudo iterations, s0 = -5).
+
+One benchmark step = one pass of the whole hot path: the psi reset and
+pseudo-time preconditioning, 1000 RK4 physical steps (4 FR residual + update
+stages each) and the compensated mass integral.  value = (solution points x
+4 stages x 1000 steps x K steps x ranks) / (max over ranks of the summed
+device time of the K steps).  The L2 cache is flushed (a 512 MiB write)
+before every timed step; within a step the working set (~30 MB) stays in L2.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (single RK4 steps), on the same metric.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FR DOF-stage updates/s"
+UNIT = "DOF-stage/s"
+STEPS_PER_BENCH_STEP = 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=25, help="oracle RK4 steps for cpu_baseline (0: skip)")
+    ap.add_argument("--mesh-n", type=int, default=128, help="elements per side (128 is the benchmark workload)")
+    ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def alg_flops_per_dof(dim, p):
+    """Algorithmic flops per solution point per RK stage of the residual kernel
+    (Steps 1-6, both fields, sum-factorised tensor operators; an FMA counts 2).
+    Velocity evaluation and metric terms are excluded (they depend on whether
+    they are stored or recomputed)."""
+    n = p + 1
+    nu = n ** dim
+    nf = 2 * dim * n ** (dim - 1)
+    r = nf / nu
+    f = 0.0
+    f += 2 * r * n * 2                       # Step 1 traces, 2 fields
+    f += 2 * dim * (n * 2 + 2 * 2)           # Step 3 reference gradient + two line corrections
+    f += 2 * dim * dim * 2                   # q = J^-T q~
+    f += 0.5 * r * 2 * dim * n * 2           # q^f at L flux points
+    f += 0.5 * r * (8 * dim + 14)            # Step 5 common flux (normal, speeds, fluxes, penalty)
+    f += 6 * dim + 10                        # Step 4 pointwise fluxes (|v|, |q_psi|, sharpening)
+    f += 2 * dim * dim * 2                   # f~ = det J J^-1 f
+    f += 2 * r * n * 2 + 2 * r               # discontinuous normal flux and jump
+    f += 2 * dim * (n * 2 + 2 * 2)           # Step 6 divergence + two line lifts
+    return f
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for fn in ("ktensor.cuh", "kcommon.cuh", "geom.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2006_10967_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if its kernel
+    source hash matches the current source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_sha") != source_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = json.load(open(path)) if os.path.exists(path) else {}
+    return d
+
+
+# ---------------------------------------------------------------------------
+def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False):
+    import torch
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    P = G.make_params(w, precision)
+    F = G.Field(M, P, ic=w.circle, precondition=True)
+    ndof = M.info.n_dof
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        F.step(STEPS_PER_BENCH_STEP)
+        F.mass(0)
+    torch.cuda.synchronize()
+    out = {"ndof": ndof}
+    clocks = Clocks(torch.cuda.current_device())
+    times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(K):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        F.step(STEPS_PER_BENCH_STEP)
+        F.mass(0)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    out["clocks"] = clocks.stop()
+    total_ms = max_over_ranks(sum(times), world)
+    out["ms_per_step"] = total_ms / K
+    out["value"] = world * K * STEPS_PER_BENCH_STEP * 4 * ndof / (total_ms * 1e-3)
+    out["status"] = F.sync()
+    if want_kernel:
+        flush.zero_()
+        F.profile(True)
+        F.step(STEPS_PER_BENCH_STEP)
+        prof = F.profile_read()
+        F.profile(False)
+        out["kernels"] = prof
+    if e2e:
+        # through the C ABI with host buffers: upload phi, psi (pinned), run, read phi back
+        L = G.lib()
+        phi = torch.from_numpy(F.get(0)).pin_memory()
+        psi = torch.from_numpy(F.get(1)).pin_memory()
+        res = torch.empty_like(phi).pin_memory()
+        sp = C.c_void_p(stream.cuda_stream)
+        dp = C.POINTER(C.c_double)
+        ptr = lambda t: C.cast(C.c_void_p(t.data_ptr()), dp)
+        m = C.c_double()
+        times = []
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.check(L.fr_field_set(F.handle, 0, ptr(phi), sp), "fr_field_set")
+            G.check(L.fr_field_set(F.handle, 1, ptr(psi), sp), "fr_field_set")
+            G.check(L.fr_step(F.handle, STEPS_PER_BENCH_STEP, sp), "fr_step")
+            G.check(L.fr_mass_integral(F.handle, 0, C.byref(m), sp), "fr_mass_integral")
+            G.check(L.fr_field_get(F.handle, 0, ptr(res), sp), "fr_field_get")
+            times.append(time.perf_counter() - t0)
+        tot = max_over_ranks(sum(times), world)
+        out["e2e"] = {"value": world * K * STEPS_PER_BENCH_STEP * 4 * ndof / tot, "unit": UNIT,
+                      "h2d_bytes_per_step": 2 * ndof * 8, "d2h_bytes_per_step": ndof * 8 + 8}
+    return out, F
+
+
+def cpu_baseline(S, w, mesh, nsteps):
+    import torch
+    from oracle import Params, Solver
+    sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
+    sol.initialize(w.circle, precondition=False)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        sol.rk4_step()
+    dt = time.perf_counter() - t0
+    ndof = sol.E * sol.Nu
+    return {"value": ndof * 4 * nsteps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{nsteps} RK4 step(s) (4 residual stages) of the full 128^2 p=4 workload, "
+                      f"FP64 torch-CPU oracle, {dt:.1f} s"}
+
+
+def accuracy(G, S, w, mesh):
+    """Run both precisions to t = T and report E_L1 / E_m against the initial disk
+    (the Rider-Kothe flow returns it at t = T)."""
+    import numpy as np
+    res = {}
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    xu = M.solution_points()
+    c = np.array(w.circle.centre)
+    phi_e = 0.5 * (1 + np.tanh(w.circle.beta * (w.circle.radius - np.sqrt(((xu - c) ** 2).sum(-1)))))
+    wq = M.quadrature()
+    for prec in ("fp64", "mixed"):
+        F = G.Field(M, G.make_params(w, prec), ic=w.circle, precondition=True)
+        m0 = F.mass(0)
+        t0 = time.perf_counter()
+        F.step(w.n_steps)
+        F.sync()
+        el = time.perf_counter() - t0
+        phi = F.get(0)
+        res[prec] = {"E_L1": float((wq * np.abs(phi - phi_e)).sum()),
+                     "E_m": float((F.mass(0) - m0) / (wq * phi_e).sum()),
+                     "steps": w.n_steps, "wall_s": el}
+    res["ratio_L1_mixed_over_fp64"] = res["mixed"]["E_L1"] / res["fp64"]["E_L1"]
+    return res
+
+
+def main():
+    args = parse()
+    rank, world = dist_init()
+    import synthetic as S
+    w = S.workload("c2q", n=args.mesh_n)
+    mesh = w.mesh()
+    workload_cfg = {"workload": f"rider_kothe_quad{args.mesh_n}_jitter_p4", "elements": mesh.n_elems, "order": w.order,
+                    "solution_points": mesh.n_elems * (w.order + 1) ** 2, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
+                    "stages_per_rk_step": 4, "precondition_every": w.n_precond, "pseudo_kmax": w.pseudo_kmax,
+                    "l2": "flushed before each timed step (512 MiB write); working set L2-resident within a step",
+                    "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import torch
+        from oracle import Params, Solver
+        sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
+        sol.initialize(w.circle, precondition=False)
+        for _ in range(args.warmup):
+            sol.rk4_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sol.rk4_step()
+        dt = time.perf_counter() - t0
+        ndof = sol.E * sol.Nu
+        val = ndof * 4 * args.steps / dt
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(workload_cfg, reference_step="one RK4 step of the oracle"),
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                                 "sample": f"{args.steps} RK4 steps of the full workload after {args.warmup} warm-up"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10967_gb300 as G
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    main_out, F = run_path(G, S, w, mesh, args.precision, args.steps, max(args.warmup, 3), world, rank, flush,
+                           want_kernel=True, e2e=True)
+    fp64_out = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        fp64_out, _ = run_path(G, S, w, mesh, "fp64", args.fp64_steps, 1, world, rank, flush, want_kernel=True)
+
+    # roofline of the dominant kernel
+    kern = main_out["kernels"]
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, nl = kern[dom]
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    if args.precision == "mixed":
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 lanes x FMA x clock
+        peak_note = "FP32: 152 SM x 128 lanes x 2 flop x max SM clock"
+    else:
+        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12     # FP64: 2 DFMA/clk/SM
+        peak_note = "FP64: 152 SM x 2 DFMA x 2 flop x max SM clock"
+    ndof = main_out["ndof"]
+    flops_launch = alg_flops_per_dof(2, w.order) * ndof
+    achieved = flops_launch / (ms / nl * 1e-3) / 1e12 if dom == "kb_phys" else None
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": load_traffic(f"kb_phys_quad_p4_{args.precision}"),
+            "peak_source": peak_note + " (derived, nominal units and clocks)",
+            "avg_launch_us": ms / nl * 1e3,
+            "share_of_step": ms / sum(v[0] for v in kern.values()),
+            "alg_flops_per_launch": flops_launch}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_steps > 0:
+        cpu = cpu_baseline(S, w, mesh, args.cpu_steps)
+
+    line = {"metric": METRIC, "value": main_out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": main_out["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": dict(workload_cfg, precision=args.precision),
+            "clocks": main_out["clocks"], "e2e": main_out["e2e"],
+            "gpu_launches": int(sum(v[1] for v in kern.values())) * args.steps + 3 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "status": main_out["status"]}
+    if fp64_out is not None:
+        line["fp64"] = {"value": fp64_out["value"], "ms_per_step": fp64_out["ms_per_step"],
+                        "kb_phys_avg_us": fp64_out["kernels"]["kb_phys"][0] / fp64_out["kernels"]["kb_phys"][1] * 1e3}
+        line["speedup_mixed_over_fp64"] = main_out["value"] / fp64_out["value"]
+    if args.accuracy:
+        line["accuracy"] = accuracy(G, S, w, mesh)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -217,6 +217,16 @@ int fr_rhs(fr_field* field, double t, double* dev_out, void* stream);
  * dev_out (n_dof doubles), with the stored psi0. */
 int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
 
+/* Per-kernel timing (not part of the method): with enable != 0 every FR
+ * kernel launch of fr_step / fr_precondition is bracketed by CUDA events on
+ * its stream.  fr_profile_read synchronises `stream` and returns, for the
+ * four kernel classes {residual+flux (physical), lift+RK+traces (physical),
+ * residual+flux (preconditioning), lift+RK+traces (preconditioning)}, the
+ * summed device milliseconds and the launch counts since the last read
+ * (host arrays of 4). */
+int fr_profile(fr_field* field, int enable);
+int fr_profile_read(fr_field* field, void* stream, double* total_ms, int64_t* launches);
+
 void fr_field_destroy(fr_field* field);
 
 const char* fr_strerror(int code);

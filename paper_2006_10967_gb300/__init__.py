@@ -199,6 +199,16 @@ class Field:
               "fr_rhs_pseudo")
         return out
 
+    def profile(self, enable=True):
+        check(lib().fr_profile(self.handle, int(bool(enable))), "fr_profile")
+
+    def profile_read(self, stream=None):
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        check(lib().fr_profile_read(self.handle, self._stream(stream), ms, n), "fr_profile_read")
+        names = ("kb_phys", "ka_phys", "kb_pseudo", "ka_pseudo")
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

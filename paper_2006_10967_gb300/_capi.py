@@ -78,6 +78,8 @@ _SIGS = {
     "fr_field_set_device": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "fr_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "fr_rhs_pseudo": (C.c_int, [_vp, _vp, _vp]),
+    "fr_profile": (C.c_int, [_vp, C.c_int]),
+    "fr_profile_read": (C.c_int, [_vp, _vp, _dp, C.POINTER(C.c_int64)]),
     "fr_field_destroy": (None, [_vp]),
     "fr_strerror": (C.c_char_p, [C.c_int]),
     "fr_version": (C.c_int, []),

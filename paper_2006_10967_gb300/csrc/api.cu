@@ -165,6 +165,9 @@ struct fr_field {
   int64_t n_precond_done = 0;
   int sticky = FR_OK;
   int mass_grid = 1;
+  // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
+  int profiling = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];
 };
 
 namespace {
@@ -174,6 +177,22 @@ void launch_elementwise_grid(int64_t n, int* grid) {
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
   *grid = (int)g;
+}
+
+// Launch one FR kernel; with profiling on, bracket it by CUDA events.
+// cls: 0 kb physical, 1 ka physical, 2 kb preconditioning, 3 ka preconditioning
+void timed(fr_field* f, int cls, LaunchFn fn, const KArgs& a, cudaStream_t s) {
+  if (!f->profiling) {
+    fn(a, s);
+    return;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  fn(a, s);
+  cudaEventRecord(e1, s);
+  f->prof[cls].emplace_back(e0, e1);
 }
 
 int stage_and_traces(fr_field* f, cudaStream_t s) {
@@ -202,8 +221,8 @@ int run_precondition(fr_field* f, cudaStream_t s) {
   for (int k = 0; k < f->prm.pseudo_kmax; ++k)
     for (int st = 1; st <= 4; ++st) {
       a.stage = st;
-      f->ks.kb[1](a, s);
-      f->ks.ka[1](a, s);
+      timed(f, 2, f->ks.kb[1], a, s);
+      timed(f, 3, f->ks.ka[1], a, s);
     }
   CK(cudaGetLastError());
   f->n_precond_done++;
@@ -220,8 +239,8 @@ int run_step(fr_field* f, cudaStream_t s) {
   a.dt = f->prm.dt;
   for (int st = 1; st <= 4; ++st) {
     a.stage = st;
-    f->ks.kb[0](a, s);
-    f->ks.ka[0](a, s);
+    timed(f, 0, f->ks.kb[0], a, s);
+    timed(f, 1, f->ks.ka[0], a, s);
   }
   CK(cudaGetLastError());
   f->nstep++;
@@ -549,7 +568,40 @@ extern "C" int fr_rhs_pseudo(fr_field* f, double* dev_out, void* stream) {
   return FR_OK;
 }
 
-extern "C" void fr_field_destroy(fr_field* f) { delete f; }
+extern "C" int fr_profile(fr_field* f, int enable) {
+  if (!f) return FR_EINVAL;
+  f->profiling = enable ? 1 : 0;
+  return FR_OK;
+}
+
+extern "C" int fr_profile_read(fr_field* f, void* stream, double* total_ms, int64_t* launches) {
+  if (!f || !total_ms || !launches) return FR_EINVAL;
+  CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  for (int c = 0; c < 4; ++c) {
+    double tot = 0.0;
+    for (auto& pr : f->prof[c]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess) return FR_ECUDA;
+      tot += ms;
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    total_ms[c] = tot;
+    launches[c] = (int64_t)f->prof[c].size();
+    f->prof[c].clear();
+  }
+  return FR_OK;
+}
+
+extern "C" void fr_field_destroy(fr_field* f) {
+  if (!f) return;
+  for (int c = 0; c < 4; ++c)
+    for (auto& pr : f->prof[c]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  delete f;
+}
 
 extern "C" const char* fr_strerror(int code) {
   switch (code) {
