@@ -199,6 +199,33 @@ int fr_stats_get(fr_field* field, void* stream, fr_stats* out);
  * in a fixed order (deterministic).  Synchronous: *out_host is valid on return. */
 int fr_mass_integral(fr_field* field, int which, double* out_host, void* stream);
 
+/* Allocation-free weighted integral.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code running
+ * inside another framework's memory pool (a cudaMalloc would bypass its
+ * accounting and can fragment its arena), latency-critical loops that cannot
+ * afford the implicit device synchronisation of cudaMalloc/cudaFree, and
+ * callers that hold their data on the device without an fr_field workspace.
+ *
+ * Computes sum_i w[i] * u[i] over n doubles (dev_u, dev_w: device arrays,
+ * caller-owned) with the compensated, fixed-order reduction of
+ * fr_mass_integral and writes it to *out_host (synchronous on `stream`).
+ * Pass u = one field from fr_field_get_device and w = fr_mesh_quadrature
+ * copied to the device to get fr_mass_integral's value.
+ *
+ * Scratch: a static device array of FR_NOALLOC_MAX_BLOCKS (sum, compensation)
+ * pairs plus two words (~256 KB), held by every GPU that loads the library
+ * until the process exits.  n > FR_NOALLOC_MAX_VALUES returns FR_EINVAL.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * resets its counter before use, so calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define FR_NOALLOC_MAX_BLOCKS 16384
+#define FR_NOALLOC_MAX_VALUES ((int64_t)FR_NOALLOC_MAX_BLOCKS * 256 * 8)
+int fr_mass_integral_noalloc(const double* dev_u, const double* dev_w, int64_t n, double* out_host,
+                             void* stream);
+
 /* Copy a field to/from host memory (synchronous): which = 0 phi, 1 psi,
  * 2 psi0; n_dof doubles.  fr_field_set also refreshes the stage copies and
  * flux-point traces. */

@@ -16,6 +16,8 @@ FR_FP64, FR_MIXED = 0, 1
 FR_VEL_UNIFORM, FR_VEL_RIDER_KOTHE, FR_VEL_LEVEQUE, FR_VEL_STREAM, FR_VEL_ROTATION = 0, 1, 2, 3, 4
 FR_MAX_MODES = 32
 FR_IC_CIRCLE, FR_IC_ARRAY = 0, 1
+FR_NOALLOC_MAX_BLOCKS = 16384
+FR_NOALLOC_MAX_VALUES = FR_NOALLOC_MAX_BLOCKS * 256 * 8
 
 _dp = C.POINTER(C.c_double)
 
@@ -72,6 +74,7 @@ _SIGS = {
     "fr_sync": (C.c_int, [_vp, _vp]),
     "fr_stats_get": (C.c_int, [_vp, _vp, C.POINTER(fr_stats)]),
     "fr_mass_integral": (C.c_int, [_vp, C.c_int, _dp, _vp]),
+    "fr_mass_integral_noalloc": (C.c_int, [_vp, _vp, C.c_int64, _dp, _vp]),
     "fr_field_get": (C.c_int, [_vp, C.c_int, _dp, _vp]),
     "fr_field_set": (C.c_int, [_vp, C.c_int, _dp, _vp]),
     "fr_field_get_device": (C.c_int, [_vp, C.c_int, _vp, _vp]),
