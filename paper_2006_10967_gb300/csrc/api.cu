@@ -18,10 +18,75 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, dstate, red, geo, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0;
-  size_t tri_xu, tri_xf, tri_nref, tri_L, tri_Dr, tri_Ds, tri_LIFT, tri_Vinv, tri_high;
+  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer;
+  size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t total;
 };
+
+// number of values in the packed dense triangle operators
+size_t tri_op_count(const fr_mesh& m) {
+  const size_t NU = m.nu, NF = m.nf;
+  return NU * 2 + NF * 2 + NF * 2 + NF * NU + 3 * NU * NU + NU * NF;
+}
+
+template <typename R>
+void pack_tri(const TriRef& t, std::vector<R>& out) {
+  out.clear();
+  for (const std::vector<double>* v : {&t.xu, &t.xf, &t.nref, &t.L, &t.Dr, &t.Ds, &t.LIFT, &t.Vinv})
+    for (double x : *v) out.push_back((R)x);
+}
+
+template <typename R>
+TriOpsT<R> tri_pointers(const TriRef& t, const R* base, const uint8_t* high) {
+  TriOpsT<R> o;
+  const R* p = base;
+  o.xu = p; p += t.xu.size();
+  o.xf = p; p += t.xf.size();
+  o.nref = p; p += t.nref.size();
+  o.L = p; p += t.L.size();
+  o.Dr = p; p += t.Dr.size();
+  o.Ds = p; p += t.Ds.size();
+  o.LIFT = p; p += t.LIFT.size();
+  o.Vinv = p;
+  o.high = high;
+  return o;
+}
+
+template <typename R>
+void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
+  std::memset(&b, 0, sizeof(b));
+  b.vel.kind = prm->vel.kind;
+  for (int c = 0; c < 3; ++c) b.vel.a[c] = (R)prm->vel.a[c];
+  if (prm->vel.kind == FR_VEL_STREAM) {
+    b.vel.n_modes = prm->vel.n_modes;
+    for (int k = 0; k < prm->vel.n_modes; ++k) {
+      b.vel.kx[k] = (R)prm->vel.kx[k];
+      b.vel.ky[k] = (R)prm->vel.ky[k];
+      b.vel.A[k] = (R)prm->vel.A[k];
+      b.vel.B[k] = (R)prm->vel.B[k];
+    }
+  }
+  b.prm.gamma = (R)prm->gamma;
+  b.prm.eps = (R)prm->eps;
+  b.prm.tau = (R)prm->tau;
+  b.prm.tau_psi = (R)prm->tau_psi;
+  b.prm.tau_pseudo = (R)prm->tau_pseudo;
+  b.prm.delta = (R)prm->delta;
+  if (m->etype != FR_TRI) {
+    const Tensor1D& t = m->t1;
+    for (int i = 0; i < t.n; ++i) {
+      b.ops.x[i] = (R)t.x[i];
+      b.ops.lend[0][i] = (R)t.lend[0][i];
+      b.ops.lend[1][i] = (R)t.lend[1][i];
+      b.ops.gLd[i] = (R)t.gLd[i];
+      b.ops.gRd[i] = (R)t.gRd[i];
+      for (int j = 0; j < t.n; ++j) {
+        b.ops.D[i][j] = (R)t.D[i][j];
+        b.ops.Vinv[i][j] = (R)t.Vinv[i][j];
+      }
+    }
+  }
+}
 
 Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
   Layout L{};
@@ -37,6 +102,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
   L.dstate = take(DS_WORDS * sizeof(double));
   L.red = take((size_t)(max_blocks + 1) * 2 * sizeof(double));
   L.geo = take(E * NG * sizeof(double));
+  L.geof = take(E * NG * sizeof(float));
   L.fnbr = take(E * NF * sizeof(int32_t));
   L.wdet = take(E * NU * sizeof(double));
   L.ustg = take(E * 2 * NU * tb);
@@ -46,15 +112,11 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
   L.tr = take(E * 2 * NF * tb);
   L.fc = take(E * 2 * NF * tb);
   L.psi0 = take(E * NU * sizeof(double));
+  L.xfer = take(E * NU * sizeof(double));
   if (m.etype == FR_TRI) {
-    L.tri_xu = take(NU * 2 * sizeof(double));
-    L.tri_xf = take(NF * 2 * sizeof(double));
-    L.tri_nref = take(NF * 2 * sizeof(double));
-    L.tri_L = take(NF * NU * sizeof(double));
-    L.tri_Dr = take(NU * NU * sizeof(double));
-    L.tri_Ds = take(NU * NU * sizeof(double));
-    L.tri_LIFT = take(NU * NF * sizeof(double));
-    L.tri_Vinv = take(NU * NU * sizeof(double));
+    const size_t nops = tri_op_count(m);
+    L.tri_d = take(nops * sizeof(double));
+    L.tri_f = take(nops * sizeof(float));
     L.tri_high = take(NU);
   }
   L.total = off;
@@ -90,23 +152,51 @@ int check_params(const fr_params* p) {
   } while (0)
 
 // ---- small kernels ---------------------------------------------------------
+// The solution u is double in the FP64 path and a float-float pair
+// (hi, lo) in the mixed path; these helpers read and write one value.
+__device__ __forceinline__ double u_get(const KArgs& A, int mixed, int64_t g) {
+  if (!mixed) return A.u[g];
+  const float2 v = reinterpret_cast<const float2*>(A.u)[g];
+  return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ void u_put(const KArgs& A, int mixed, int64_t g, double x) {
+  if (!mixed) {
+    A.u[g] = x;
+    return;
+  }
+  const float hi = (float)x;
+  reinterpret_cast<float2*>(A.u)[g] = make_float2(hi, (float)(x - (double)hi));
+}
+
 template <typename T>
-__global__ void k_reset_psi(KArgs A, int64_t NU) {
+__global__ void k_reset_psi(KArgs A, int64_t NU, int mixed) {
   const int64_t n = A.E * NU;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = g / NU, i = g % NU;
-    const double p0 = A.u[(e * 2 + 0) * NU + i] - 0.5;
+    const double p0 = u_get(A, mixed, (e * 2 + 0) * NU + i) - 0.5;
     A.psi0[g] = p0;
-    A.u[(e * 2 + 1) * NU + i] = p0;
+    u_put(A, mixed, (e * 2 + 1) * NU + i, p0);
     reinterpret_cast<T*>(A.ustg)[(e * 2 + 1) * NU + i] = (T)p0;
   }
 }
 
 template <typename T>
-__global__ void k_to_stage(KArgs A, int64_t NU) {
+__global__ void k_to_stage(KArgs A, int64_t NU, int mixed) {
   const int64_t n = A.E * 2 * NU;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    reinterpret_cast<T*>(A.ustg)[g] = (T)A.u[g];
+    reinterpret_cast<T*>(A.ustg)[g] = (T)u_get(A, mixed, g);
+}
+
+// field `fld` of u <-> contiguous double buffer
+__global__ void k_unpack(KArgs A, int64_t NU, int fld, int mixed, double* out) {
+  const int64_t n = A.E * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = u_get(A, mixed, (g / NU * 2 + fld) * NU + g % NU);
+}
+__global__ void k_pack(KArgs A, int64_t NU, int fld, int mixed, const double* in) {
+  const int64_t n = A.E * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    u_put(A, mixed, (g / NU * 2 + fld) * NU + g % NU, in[g]);
 }
 
 // Neumaier two-term accumulation
@@ -117,14 +207,14 @@ __device__ __forceinline__ void neu_add(double& s, double& c, double x) {
 }
 
 // Compensated, fixed-order integral of field `fld` with weights wdet.
-__global__ void k_mass(KArgs A, int64_t NU, int fld) {
+__global__ void k_mass(KArgs A, int64_t NU, int fld, int mixed) {
   __shared__ double ss[kThreads], sc[kThreads];
   __shared__ bool last;
   const int64_t n = A.E * NU;
   double s = 0.0, c = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = g / NU, i = g % NU;
-    neu_add(s, c, A.wdet[g] * A.u[(e * 2 + fld) * NU + i]);
+    neu_add(s, c, A.wdet[g] * u_get(A, mixed, (e * 2 + fld) * NU + i));
   }
   ss[threadIdx.x] = s;
   sc[threadIdx.x] = c;
@@ -165,6 +255,7 @@ struct fr_field {
   int64_t n_precond_done = 0;
   int sticky = FR_OK;
   int mass_grid = 1;
+  double* xfer = nullptr;  // E*nu doubles, staging for get/set in the mixed path
   // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
   int profiling = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];
@@ -198,8 +289,8 @@ void timed(fr_field* f, int cls, LaunchFn fn, const KArgs& a, cudaStream_t s) {
 int stage_and_traces(fr_field* f, cudaStream_t s) {
   int grid;
   launch_elementwise_grid(f->E * 2 * f->nu, &grid);
-  if (f->precision == FR_FP64) k_to_stage<double><<<grid, kThreads, 0, s>>>(f->args, f->nu);
-  else k_to_stage<float><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  if (f->precision == FR_FP64) k_to_stage<double><<<grid, kThreads, 0, s>>>(f->args, f->nu, 0);
+  else k_to_stage<float><<<grid, kThreads, 0, s>>>(f->args, f->nu, 1);
   KArgs a = f->args;
   a.stage = 0;
   f->ks.ka[0](a, s);
@@ -211,8 +302,8 @@ int run_precondition(fr_field* f, cudaStream_t s) {
   CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
   int grid;
   launch_elementwise_grid(f->E * f->nu, &grid);
-  if (f->precision == FR_FP64) k_reset_psi<double><<<grid, kThreads, 0, s>>>(f->args, f->nu);
-  else k_reset_psi<float><<<grid, kThreads, 0, s>>>(f->args, f->nu);
+  if (f->precision == FR_FP64) k_reset_psi<double><<<grid, kThreads, 0, s>>>(f->args, f->nu, 0);
+  else k_reset_psi<float><<<grid, kThreads, 0, s>>>(f->args, f->nu, 1);
   KArgs a = f->args;
   a.stage = 0;
   a.dt = f->prm.pseudo_dtau;
@@ -327,6 +418,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.dstate = reinterpret_cast<double*>(b + L.dstate);
   A.red = reinterpret_cast<double*>(b + L.red);
   A.geo = reinterpret_cast<const double*>(b + L.geo);
+  A.geof = reinterpret_cast<const float*>(b + L.geof);
   A.fnbr = reinterpret_cast<const int32_t*>(b + L.fnbr);
   A.wdet = reinterpret_cast<const double*>(b + L.wdet);
   A.ustg = b + L.ustg;
@@ -336,6 +428,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.tr = b + L.tr;
   A.fc = b + L.fc;
   A.psi0 = reinterpret_cast<double*>(b + L.psi0);
+  f->xfer = reinterpret_cast<double*>(b + L.xfer);
   A.out = nullptr;
   A.stage = 0;
   A.use_dev_time = 0;
@@ -352,34 +445,9 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.prm.nu_max = prm->nu_max;
   A.prm.pseudo_tol = prm->pseudo_tol;
   A.prm.pseudo_fixed = prm->pseudo_fixed;
-  std::memset(&A.vel, 0, sizeof(A.vel));
-  A.vel.kind = prm->vel.kind;
-  A.vel.T = prm->vel.T;
-  for (int c = 0; c < 3; ++c) A.vel.a[c] = prm->vel.a[c];
-  if (prm->vel.kind == FR_VEL_STREAM) {
-    A.vel.n_modes = prm->vel.n_modes;
-    for (int k = 0; k < prm->vel.n_modes; ++k) {
-      A.vel.kx[k] = prm->vel.kx[k];
-      A.vel.ky[k] = prm->vel.ky[k];
-      A.vel.A[k] = prm->vel.A[k];
-      A.vel.B[k] = prm->vel.B[k];
-    }
-  }
-  std::memset(&A.ops, 0, sizeof(A.ops));
-  if (m->etype != FR_TRI) {
-    const Tensor1D& t = m->t1;
-    for (int i = 0; i < t.n; ++i) {
-      A.ops.x[i] = t.x[i];
-      A.ops.lend[0][i] = t.lend[0][i];
-      A.ops.lend[1][i] = t.lend[1][i];
-      A.ops.gLd[i] = t.gLd[i];
-      A.ops.gRd[i] = t.gRd[i];
-      for (int j = 0; j < t.n; ++j) {
-        A.ops.D[i][j] = t.D[i][j];
-        A.ops.Vinv[i][j] = t.Vinv[i][j];
-      }
-    }
-  }
+  A.prm.T = prm->vel.T;
+  fill_bulk<double>(prm, m, A.cd);
+  fill_bulk<float>(prm, m, A.cf);
 
   int err = FR_OK;
   auto up = [&](size_t off, const void* src, size_t bytes) {
@@ -389,35 +457,38 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   up(L.geo, m->geo.data(), m->geo.size() * sizeof(double));
   up(L.fnbr, m->fnbr.data(), m->fnbr.size() * sizeof(int32_t));
   up(L.wdet, m->wdet.data(), m->wdet.size() * sizeof(double));
+  std::vector<float> geof(m->geo.begin(), m->geo.end());
+  up(L.geof, geof.data(), geof.size() * sizeof(float));
+  std::vector<double> trid;
+  std::vector<float> trif;
   if (m->etype == FR_TRI) {
-    const TriRef& t = m->tri;
-    up(L.tri_xu, t.xu.data(), t.xu.size() * 8);
-    up(L.tri_xf, t.xf.data(), t.xf.size() * 8);
-    up(L.tri_nref, t.nref.data(), t.nref.size() * 8);
-    up(L.tri_L, t.L.data(), t.L.size() * 8);
-    up(L.tri_Dr, t.Dr.data(), t.Dr.size() * 8);
-    up(L.tri_Ds, t.Ds.data(), t.Ds.size() * 8);
-    up(L.tri_LIFT, t.LIFT.data(), t.LIFT.size() * 8);
-    up(L.tri_Vinv, t.Vinv.data(), t.Vinv.size() * 8);
-    up(L.tri_high, t.high.data(), t.high.size());
-    A.tri.xu = reinterpret_cast<const double*>(b + L.tri_xu);
-    A.tri.xf = reinterpret_cast<const double*>(b + L.tri_xf);
-    A.tri.nref = reinterpret_cast<const double*>(b + L.tri_nref);
-    A.tri.L = reinterpret_cast<const double*>(b + L.tri_L);
-    A.tri.Dr = reinterpret_cast<const double*>(b + L.tri_Dr);
-    A.tri.Ds = reinterpret_cast<const double*>(b + L.tri_Ds);
-    A.tri.LIFT = reinterpret_cast<const double*>(b + L.tri_LIFT);
-    A.tri.Vinv = reinterpret_cast<const double*>(b + L.tri_Vinv);
-    A.tri.high = reinterpret_cast<const uint8_t*>(b + L.tri_high);
+    pack_tri(m->tri, trid);
+    pack_tri(m->tri, trif);
+    up(L.tri_d, trid.data(), trid.size() * sizeof(double));
+    up(L.tri_f, trif.data(), trif.size() * sizeof(float));
+    up(L.tri_high, m->tri.high.data(), m->tri.high.size());
+    const uint8_t* hi = reinterpret_cast<const uint8_t*>(b + L.tri_high);
+    A.trid = tri_pointers<double>(m->tri, reinterpret_cast<const double*>(b + L.tri_d), hi);
+    A.trif = tri_pointers<float>(m->tri, reinterpret_cast<const float*>(b + L.tri_f), hi);
   }
-  // u = [phi, phi - 1/2] element-major
+  // u = [phi, phi - 1/2] element-major (float-float pairs in the mixed path)
   std::vector<double> u0(m->E * 2 * m->nu);
   for (int64_t e = 0; e < m->E; ++e)
     for (int i = 0; i < m->nu; ++i) {
       u0[(e * 2 + 0) * m->nu + i] = phi[e * m->nu + i];
       u0[(e * 2 + 1) * m->nu + i] = phi[e * m->nu + i] - 0.5;
     }
-  up(L.u, u0.data(), u0.size() * sizeof(double));
+  if (prm->precision == FR_MIXED) {
+    std::vector<float> pairs(u0.size() * 2);
+    for (size_t g = 0; g < u0.size(); ++g) {
+      const float hi = (float)u0[g];
+      pairs[2 * g] = hi;
+      pairs[2 * g + 1] = (float)(u0[g] - (double)hi);
+    }
+    up(L.u, pairs.data(), pairs.size() * sizeof(float));
+  } else {
+    up(L.u, u0.data(), u0.size() * sizeof(double));
+  }
   std::vector<double> p0(ndof);
   for (int64_t g = 0; g < ndof; ++g) p0[g] = phi[g] - 0.5;
   up(L.psi0, p0.data(), p0.size() * sizeof(double));
@@ -479,7 +550,7 @@ extern "C" int fr_stats_get(fr_field* f, void* stream, fr_stats* out) {
 extern "C" int fr_mass_integral(fr_field* f, int which, double* out_host, void* stream) {
   if (!f || !out_host || which < 0 || which > 1) return FR_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  k_mass<<<f->mass_grid, kThreads, 0, s>>>(f->args, f->nu, which);
+  k_mass<<<f->mass_grid, kThreads, 0, s>>>(f->args, f->nu, which, f->precision == FR_MIXED);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out_host, f->args.dstate + DS_MASS, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -495,10 +566,23 @@ int copy_field(fr_field* f, int which, void* dst, const void* src, bool to_state
     else CK(cudaMemcpyAsync(dst, f->args.psi0, E * NU * 8, kind, s));
     return FR_OK;
   }
-  if (to_state)
-    CK(cudaMemcpy2DAsync(f->args.u + which * NU, 2 * NU * 8, src, NU * 8, NU * 8, E, kind, s));
-  else
-    CK(cudaMemcpy2DAsync(dst, NU * 8, f->args.u + which * NU, 2 * NU * 8, NU * 8, E, kind, s));
+  if (f->precision == FR_FP64) {
+    if (to_state)
+      CK(cudaMemcpy2DAsync(f->args.u + which * NU, 2 * NU * 8, src, NU * 8, NU * 8, E, kind, s));
+    else
+      CK(cudaMemcpy2DAsync(dst, NU * 8, f->args.u + which * NU, 2 * NU * 8, NU * 8, E, kind, s));
+    return FR_OK;
+  }
+  int grid;
+  launch_elementwise_grid(f->E * f->nu, &grid);
+  if (to_state) {
+    CK(cudaMemcpyAsync(f->xfer, src, E * NU * 8, kind, s));
+    k_pack<<<grid, kThreads, 0, s>>>(f->args, f->nu, which, 1, f->xfer);
+  } else {
+    k_unpack<<<grid, kThreads, 0, s>>>(f->args, f->nu, which, 1, f->xfer);
+    CK(cudaMemcpyAsync(dst, f->xfer, E * NU * 8, kind, s));
+  }
+  CK(cudaGetLastError());
   return FR_OK;
 }
 }  // namespace

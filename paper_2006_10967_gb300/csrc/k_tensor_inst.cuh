@@ -13,7 +13,7 @@ void launch_kb_tensor(const KArgs& A, cudaStream_t s) {
     cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
     init = true;
   }
-  launch_kernel(kb_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s);
+  launch_kernel(kb_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
 }
 
 template <int DIM, int N, typename T, int MODE>

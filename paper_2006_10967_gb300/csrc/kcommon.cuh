@@ -17,39 +17,61 @@ enum { ST_STATUS = 0, ST_PSEUDO_DONE = 1, ST_PSEUDO_ITERS = 2, ST_COUNTER = 3, S
 // double slots in the workspace
 enum { DS_TIME = 0, DS_PSEUDO_RMS = 1, DS_MASS = 2, DS_MASS_C = 3, DS_WORDS = 8 };
 
-struct VelDesc {
+// Velocity constants in the kernel's bulk precision R (the time factor
+// g(t) is evaluated once per block in double and passed in).
+template <typename R>
+struct VelDescT {
   int kind, n_modes;
-  double T;
-  double a[3];
-  double kx[kMaxModes], ky[kMaxModes], A[kMaxModes], B[kMaxModes];
+  R a[3];
+  R kx[kMaxModes], ky[kMaxModes], A[kMaxModes], B[kMaxModes];
+};
+
+// Physical parameters in the bulk precision (double copies for the host-side
+// and reduction logic live in PhysPrm).
+template <typename R>
+struct PrmT {
+  R gamma, eps, tau, tau_psi, tau_pseudo, delta;
 };
 
 struct PhysPrm {
   double gamma, eps, tau, tau_psi, tau_pseudo, delta, s0, kappa, nu_max, pseudo_tol;
   int pseudo_fixed;
+  double T;  // period of the velocity time factor (<= 0: none)
 };
 
-// 1D tensor operators (double); kernels stage them into shared memory.
-struct TensorOps {
-  double x[kMaxN], lend[2][kMaxN], D[kMaxN][kMaxN], gLd[kMaxN], gRd[kMaxN], Vinv[kMaxN][kMaxN];
+// 1D tensor operators; kernels stage them into shared memory.
+template <typename R>
+struct TensorOpsT {
+  R x[kMaxN], lend[2][kMaxN], D[kMaxN][kMaxN], gLd[kMaxN], gRd[kMaxN], Vinv[kMaxN][kMaxN];
+};
+typedef TensorOpsT<double> TensorOps;
+
+// Bulk-precision constants of one field, in both precisions.
+template <typename R>
+struct BulkConst {
+  VelDescT<R> vel;
+  PrmT<R> prm;
+  TensorOpsT<R> ops;
 };
 
-// Dense triangle operators live in device memory (double).
-struct TriOps {
-  const double* xu;   // nu x 2
-  const double* xf;   // nf x 2
-  const double* nref; // nf x 2
-  const double* L;    // nf x nu
-  const double* Dr;   // nu x nu
-  const double* Ds;   // nu x nu
-  const double* LIFT; // nu x nf
-  const double* Vinv; // nu x nu
+// Dense triangle operators live in device memory (one copy per precision).
+template <typename R>
+struct TriOpsT {
+  const R* xu;   // nu x 2
+  const R* xf;   // nf x 2
+  const R* nref; // nf x 2
+  const R* L;    // nf x nu
+  const R* Dr;   // nu x nu
+  const R* Ds;   // nu x nu
+  const R* LIFT; // nu x nf
+  const R* Vinv; // nu x nu
   const uint8_t* high;
 };
 
 struct KArgs {
   int64_t E;
-  const double* geo;     // E x dim x ncoef
+  const double* geo;     // E x dim x ncoef (fp64)
+  const float* geof;     // E x dim x ncoef (fp32 copy for the mixed path)
   const int32_t* fnbr;   // E x nf
   void* ustg;            // T   E x 2 x nu  stage input
   double* u;             // E x 2 x nu     solution (RK base)
@@ -67,17 +89,35 @@ struct KArgs {
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
   double t;              // KB: stage time when !use_dev_time
   double dt;             // physical dt or pseudo dtau
-  VelDesc vel;
   PhysPrm prm;
-  TensorOps ops;
-  TriOps tri;
+  BulkConst<double> cd;
+  BulkConst<float> cf;
+  TriOpsT<double> trid;
+  TriOpsT<float> trif;
 };
+
+template <typename T> __device__ __forceinline__ const BulkConst<T>& bulk(const KArgs& A);
+template <> __device__ __forceinline__ const BulkConst<double>& bulk<double>(const KArgs& A) { return A.cd; }
+template <> __device__ __forceinline__ const BulkConst<float>& bulk<float>(const KArgs& A) { return A.cf; }
+template <typename T> __device__ __forceinline__ const TriOpsT<T>& tri_of(const KArgs& A);
+template <> __device__ __forceinline__ const TriOpsT<double>& tri_of<double>(const KArgs& A) { return A.trid; }
+template <> __device__ __forceinline__ const TriOpsT<float>& tri_of<float>(const KArgs& A) { return A.trif; }
+template <typename T> __device__ __forceinline__ const T* geo_of(const KArgs& A);
+template <> __device__ __forceinline__ const double* geo_of<double>(const KArgs& A) { return A.geo; }
+template <> __device__ __forceinline__ const float* geo_of<float>(const KArgs& A) { return A.geof; }
+
+// Time factor g(t) = cos(pi t / T) of the modulated velocity fields, in double.
+__device__ __forceinline__ double time_factor(const KArgs& A, double t) {
+  return A.prm.T > 0.0 ? cospi(t / A.prm.T) : 1.0;
+}
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double spi(double x) { return sinpi(x); }
 __device__ __forceinline__ float spi(float x) { return sinpif(x); }
 __device__ __forceinline__ double cpi(double x) { return cospi(x); }
 __device__ __forceinline__ float cpi(float x) { return cospif(x); }
+__device__ __forceinline__ void scpi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void scpi(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
 __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
@@ -85,23 +125,27 @@ __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 
 // Analytic velocity (Sections 4.1-4.3); time modulation g(t) = cos(pi t / T).
 template <int DIM, typename R>
-__device__ __forceinline__ void velocity(const VelDesc& V, const R* x, double t, R* v) {
-  const R g = V.T > 0.0 ? (R)cospi(t / V.T) : (R)1;
+__device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, R* v) {
   switch (V.kind) {
     case 0:  // uniform
-      for (int c = 0; c < DIM; ++c) v[c] = (R)V.a[c];
+      for (int c = 0; c < DIM; ++c) v[c] = V.a[c];
       break;
-    case 1: {  // Rider-Kothe
-      const R sx = spi(x[0]), sy = spi(x[1]);
-      v[0] = -sx * sx * spi((R)2 * x[1]) * g;
-      v[1] = spi((R)2 * x[0]) * sy * sy * g;
+    case 1: {  // Rider-Kothe; sin(2 pi a) = 2 sin(pi a) cos(pi a)
+      R sx, cx, sy, cy;
+      scpi(x[0], &sx, &cx);
+      scpi(x[1], &sy, &cy);
+      v[0] = -sx * sx * ((R)2 * sy * cy) * g;
+      v[1] = ((R)2 * sx * cx) * sy * sy * g;
       if (DIM == 3) v[DIM - 1] = 0;
       break;
     }
     case 2: {  // LeVeque 3D deformation
       if (DIM == 3) {
-        const R sx = spi(x[0]), sy = spi(x[1]), sz = spi(x[DIM - 1]);
-        const R s2x = spi((R)2 * x[0]), s2y = spi((R)2 * x[1]), s2z = spi((R)2 * x[DIM - 1]);
+        R sx, cx, sy, cy, sz, cz;
+        scpi(x[0], &sx, &cx);
+        scpi(x[1], &sy, &cy);
+        scpi(x[DIM - 1], &sz, &cz);
+        const R s2x = (R)2 * sx * cx, s2y = (R)2 * sy * cy, s2z = (R)2 * sz * cz;
         v[0] = (R)2 * sx * sx * s2y * s2z * g;
         v[1] = -s2x * sy * sy * s2z * g;
         v[DIM - 1] = -s2x * s2y * sz * sz * g;
@@ -113,9 +157,9 @@ __device__ __forceinline__ void velocity(const VelDesc& V, const R* x, double t,
     case 3: {  // stream function
       R u0 = 0, u1 = 0;
       for (int m = 0; m < V.n_modes; ++m) {
-        const R kx = (R)V.kx[m], ky = (R)V.ky[m];
+        const R kx = V.kx[m], ky = V.ky[m];
         const R arg = (R)2 * (kx * x[0] + ky * x[1]);
-        const R d = (R)(2.0 * M_PI) * ((R)V.A[m] * cpi(arg) - (R)V.B[m] * spi(arg));
+        const R d = (R)(2.0 * M_PI) * (V.A[m] * cpi(arg) - V.B[m] * spi(arg));
         u0 += ky * d;
         u1 -= kx * d;
       }
@@ -150,6 +194,65 @@ __device__ __forceinline__ double rk_update(int s, double dt, double R, double& 
       return un;
     }
   }
+}
+
+// RK4 stage update of value g in the FP64 path: u, acc double.  Returns the
+// next stage input; adds the squared pseudo residual to *sq when asked.
+struct RKConstF;
+__device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, double* sq) {
+  double uu = A.u[g], aa = stage == 1 ? 0.0 : A.acc[g];
+  const double uold = uu;
+  const double y = rk_update(stage, A.dt, R, uu, aa);
+  if (stage < 4) A.acc[g] = aa;
+  else A.u[g] = uu;
+  if (sq) {
+    const double d = (uu - uold) / A.dt;
+    *sq += d * d;
+  }
+  return y;
+}
+
+// Mixed path: the solution u is a float-float pair (hi, lo) (48-bit
+// significand) so that float stage increments accumulate without FP64
+// instructions; acc = sum_s b_s k_s and the stage values are float.
+struct RKConstF {
+  float half_dt, dt, dt6;
+  double rdt;
+};
+
+__device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
+  const float bb = s - a;
+  return (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, float R, const RKConstF& c,
+                                          double* sq) {
+  float2* U = reinterpret_cast<float2*>(A.u);
+  float* Acc = reinterpret_cast<float*>(A.acc);
+  const float2 u = U[g];
+  switch (stage) {
+    case 1: Acc[g] = R; return u.x + fmaf(c.half_dt, R, u.y);
+    case 2: Acc[g] = fmaf(2.0f, R, Acc[g]); return u.x + fmaf(c.half_dt, R, u.y);
+    case 3: Acc[g] = fmaf(2.0f, R, Acc[g]); return u.x + fmaf(c.dt, R, u.y);
+    default: {
+      const float inc = c.dt6 * (Acc[g] + R);
+      const float s = u.x + inc;
+      const float e = two_sum_lo(u.x, inc, s) + u.y;
+      const float hi = s + e;
+      const float lo = e - (hi - s);
+      U[g] = make_float2(hi, lo);
+      if (sq) {
+        const double d = (((double)hi - (double)u.x) + ((double)lo - (double)u.y)) * c.rdt;
+        *sq += d * d;
+      }
+      return hi;
+    }
+  }
+}
+
+__device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, const RKConstF&,
+                                           double* sq) {
+  return rk_apply(A, stage, g, R, sq);
 }
 
 // Block-wide sum of one double (all threads get the result).

@@ -20,9 +20,9 @@ bool kernels_hex(int order, int precision, int64_t E, KernelSet* ks);
 bool kernels_tri(int order, int precision, int64_t E, KernelSet* ks);
 
 template <typename K>
-inline void launch_kernel(K kern, size_t smem, int et, const KArgs& A, cudaStream_t s) {
+inline void launch_kernel(K kern, size_t smem, int et, const KArgs& A, cudaStream_t s, int threads = kThreads) {
   const int64_t grid = (A.E + et - 1) / et;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(A);
+  kern<<<(unsigned)grid, threads, smem, s>>>(A);
 }
 
 }  // namespace frp

@@ -106,56 +106,74 @@ struct SOps {
 };
 
 template <int N, typename T>
-__device__ __forceinline__ void load_ops(const TensorOps& o, SOps<N, T>& s) {
+__device__ __forceinline__ void load_ops(const TensorOpsT<T>& o, SOps<N, T>& s) {
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    s.x[t] = (T)o.x[t];
-    s.lend[0][t] = (T)o.lend[0][t];
-    s.lend[1][t] = (T)o.lend[1][t];
-    s.gLd[t] = (T)o.gLd[t];
-    s.gRd[t] = (T)o.gRd[t];
+    s.x[t] = o.x[t];
+    s.lend[0][t] = o.lend[0][t];
+    s.lend[1][t] = o.lend[1][t];
+    s.gLd[t] = o.gLd[t];
+    s.gRd[t] = o.gRd[t];
   }
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-    s.D[t / N][t % N] = (T)o.D[t / N][t % N];
-    s.Vinv[t / N][t % N] = (T)o.Vinv[t / N][t % N];
+    s.D[t / N][t % N] = o.D[t / N][t % N];
+    s.Vinv[t / N][t % N] = o.Vinv[t / N][t % N];
   }
+}
+
+// Lines: along axis a, line l runs through the solution points whose other
+// coordinates (in increasing axis order, lowest fastest) encode l; it ends
+// at flux point l of faces (a, -) and (a, +).
+template <int DIM, int N>
+__device__ __forceinline__ int line_base(int a, int l) {
+  int base = 0, r = l;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    if (b == a) continue;
+    base += (r % N) * ipow(N, b);
+    r /= N;
+  }
+  return base;
 }
 
 template <int DIM, int N, typename T, int MODE>
 struct KBLayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr int PER_EL_T = NFLD * S::NU        // us
-                                  + 3 * NFLD * S::NF  // uf, uo, cor
-                                  + NFLD * DIM * S::NU // q / f~
-                                  + S::NG             // geometry
-                                  + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal scratch, nu_s
+  static constexpr int LN = S::NFP;  // lines per axis per element
+  static constexpr int PER_EL_T = NFLD * S::NU          // u, later the divergence
+                                  + NFLD * DIM * S::NU  // q~ -> q -> f~
+                                  + 3 * NFLD * S::NF    // uf, uo, cor
+                                  + S::NG               // geometry
+                                  + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + S::NF;
-  static constexpr int ETr = 40960 / BYTES_EL;
-  static constexpr int ET = ETr < 1 ? 1 : (ETr > 32 ? 32 : ETr);
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(SOps<N, T>) + 64;
+  static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
+  static constexpr int ET_S = 77824 / BYTES_EL < 1 ? 1 : 77824 / BYTES_EL;
+  static constexpr int ET = ET_T < ET_S ? ET_T : ET_S;
+  static constexpr int THREADS = ET * LN;
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
 };
 
 // ============================================================================
-// kb_tensor: Steps 1-6 on a tile of elements.
+// kb_tensor: Steps 1-6 on a tile of ET elements.  Line passes give each
+// thread one solution-point line; the 1D operators are read from the kernel
+// parameters (constant bank) with compile-time indices.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
+__global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   using S = TS<DIM, N>;
   using LY = KBLayout<DIM, N, T, MODE>;
-  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
   constexpr int F0 = MODE == 0 ? 0 : 1;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SOps<N, T>& op = *reinterpret_cast<SOps<N, T>*>(smem_raw);
-  T* base = reinterpret_cast<T*>(smem_raw + ((sizeof(SOps<N, T>) + 15) & ~size_t(15)));
-  T* us = base;                        // [ET][NFLD][NU]
-  T* uf = us + ET * NFLD * NU;         // [ET][NFLD][NF]
-  T* uo = uf + ET * NFLD * NF;         // [ET][NFLD][NF]
-  T* cor = uo + ET * NFLD * NF;        // [ET][NFLD][NF]
-  T* q = cor + ET * NFLD * NF;         // [ET][NFLD][DIM][NU]  (later f~)
-  T* gs = q + ET * NFLD * DIM * NU;    // [ET][NG]
-  T* chi = gs + ET * NG;               // MODE 1: [ET][2][NU]
-  T* nus = chi + (MODE == 1 ? ET * 2 * NU : 0);  // MODE 1: [ET]
+  T* us = reinterpret_cast<T*>(smem_raw);  // [ET][NFLD][NU]
+  T* qt = us + ET * NFLD * NU;             // [ET][NFLD][DIM][NU]
+  T* uf = qt + ET * NFLD * DIM * NU;       // [ET][NFLD][NF]
+  T* uo = uf + ET * NFLD * NF;             // [ET][NFLD][NF]
+  T* cor = uo + ET * NFLD * NF;            // [ET][NFLD][NF]
+  T* gs = cor + ET * NFLD * NF;            // [ET][NG]
+  T* chi = gs + ET * NG;                   // MODE 1: [ET][2][NU]
+  T* nus = chi + (MODE == 1 ? ET * 2 * NU : 0);
   unsigned char* lm = reinterpret_cast<unsigned char*>(nus + (MODE == 1 ? ET : 0));  // [ET][NF]
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
@@ -165,88 +183,109 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
   T* fc = reinterpret_cast<T*>(A.fc);
   T* rp = reinterpret_cast<T*>(A.rp);
   const int tid = threadIdx.x;
-  const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
-
-  load_ops<N, T>(A.ops, op);
+  const BulkConst<T>& BC = bulk<T>(A);
+  const TensorOpsT<T>& O = BC.ops;
+  const PrmT<T> P = BC.prm;
+  __shared__ T gfac_s;
+  if (tid == 0) {
+    const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
+    gfac_s = (T)time_factor(A, tstage);
+  }
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
     us[idx] = ustg[((e0 + el) * 2 + F0 + fld) * NU + i];
   }
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   __syncthreads();
+  const T gfac = gfac_s;
+  const int lel = tid / LN, ll = tid % LN;
+  const bool lact = lel < ne;
 
-  // ---- Step 1 and the partner traces (Step 2 needs them) -------------------
-  for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
-    const int el = idx / NF, k = idx % NF;
-    int a, s, b0;
-    fline<DIM, N>(k, a, s, b0);
-    const int32_t w = A.fnbr[(e0 + el) * NF + k];
-    const int isL = w & 1;
-    const int64_t pg = (int64_t)(w >> 1);
-    const int64_t pe = pg / NF, pk = pg % NF;
-    lm[el * NF + k] = (unsigned char)isL;
+  // ---- Steps 1-3, one pass per axis: traces at the line ends, partner
+  //      traces (Step 2), reference derivative plus the two end corrections;
+  //      the last pass maps q~ to the physical gradient q = J^{-T} q~.
 #pragma unroll
-    for (int fld = 0; fld < NFLD; ++fld) {
-      const T* ul = us + (el * NFLD + fld) * NU + b0;
-      T acc = 0;
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a);
+      const int base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+      const int32_t w0 = A.fnbr[(e0 + lel) * NF + k0], w1 = A.fnbr[(e0 + lel) * NF + k1];
+      lm[lel * NF + k0] = (unsigned char)(w0 & 1);
+      lm[lel * NF + k1] = (unsigned char)(w1 & 1);
+      const int64_t p0 = (int64_t)(w0 >> 1), p1 = (int64_t)(w1 >> 1);
 #pragma unroll
-      for (int j = 0; j < N; ++j) acc += op.lend[s][j] * ul[j * ipow(N, a)];
-      uf[(el * NFLD + fld) * NF + k] = acc;
-      uo[(el * NFLD + fld) * NF + k] = isL ? tr[(pe * 2 + F0 + fld) * NF + pk] : acc;
-    }
-  }
-  __syncthreads();
-
-  // ---- Step 3: corrected gradient at solution points -----------------------
-  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
-    const int el = idx / NU, i = idx % NU;
-    T xi[3], Sm[3][3];
-    upt_xi<DIM, N>(i, op.x, xi);
-    const T dj = metric<DIM>(gs + el * NG, xi, Sm);
-    const T rdj = (T)1 / dj;
+      for (int fld = 0; fld < NFLD; ++fld) {
+        const T* ul = us + (lel * NFLD + fld) * NU + base;
+        T v[N];
 #pragma unroll
-    for (int fld = 0; fld < NFLD; ++fld) {
-      const T* ul = us + (el * NFLD + fld) * NU;
-      const T* fo = uo + (el * NFLD + fld) * NF;
-      const T* ff = uf + (el * NFLD + fld) * NF;
-      const unsigned char* L = lm + el * NF;
-      T qt[3];
+        for (int j = 0; j < N; ++j) v[j] = ul[j * st];
+        T f0 = 0, f1 = 0;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const int ia = ucoord<N>(i, a), st = ipow(N, a), lb = i - ia * st;
-        T acc = 0;
+        for (int j = 0; j < N; ++j) {
+          f0 += O.lend[0][j] * v[j];
+          f1 += O.lend[1][j] * v[j];
+        }
+        const T o0 = (w0 & 1) ? tr[((p0 / NF) * 2 + F0 + fld) * NF + p0 % NF] : f0;
+        const T o1 = (w1 & 1) ? tr[((p1 / NF) * 2 + F0 + fld) * NF + p1 % NF] : f1;
+        const int fo = (lel * NFLD + fld) * NF;
+        uf[fo + k0] = f0;
+        uf[fo + k1] = f1;
+        uo[fo + k0] = o0;
+        uo[fo + k1] = o1;
+        const T jm = o0 - f0, jp = o1 - f1;
+        T* qa = qt + ((lel * NFLD + fld) * DIM + a) * NU + base;
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc += op.D[ia][j] * ul[lb + j * st];
-        const int km = fpt_of<DIM, N>(i, a, 0), kp = fpt_of<DIM, N>(i, a, 1);
-        const T jm = L[km] ? fo[km] - ff[km] : (T)0;
-        const T jp = L[kp] ? fo[kp] - ff[kp] : (T)0;
-        qt[a] = acc + op.gLd[ia] * jm + op.gRd[ia] * jp;
+        for (int j = 0; j < N; ++j) {
+          T acc = O.gLd[j] * jm + O.gRd[j] * jp;
+#pragma unroll
+          for (int m = 0; m < N; ++m) acc += O.D[j][m] * v[m];
+          qa[j * st] = acc;
+        }
       }
+      if (MODE == 1) {
+        // resolution indicator: chi = (Vinv x ... x Vinv) psi, one axis per pass
+        const T* src = a == 0 ? us + lel * NU : chi + (lel * 2 + ((a - 1) & 1)) * NU;
+        T* dst = chi + (lel * 2 + (a & 1)) * NU;
+        T v[N];
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T v = 0;
+        for (int j = 0; j < N; ++j) v[j] = src[base + j * st];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) v += Sm[a][b] * qt[a];
-        q[((el * NFLD + fld) * DIM + b) * NU + i] = v * rdj;
+        for (int j = 0; j < N; ++j) {
+          T acc = 0;
+#pragma unroll
+          for (int m = 0; m < N; ++m) acc += O.Vinv[j][m] * v[m];
+          dst[base + j * st] = acc;
+        }
+      }
+      if (a == DIM - 1) {
+        // physical gradient at this line's points (all axes are done)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int i = base + j * st;
+          T xi[3], Sm[3][3];
+          upt_xi<DIM, N>(i, O.x, xi);
+          const T rdj = (T)1 / metric<DIM>(gs + lel * NG, xi, Sm);
+#pragma unroll
+          for (int fld = 0; fld < NFLD; ++fld) {
+            T* q = qt + (lel * NFLD + fld) * DIM * NU + i;
+            T qv[3];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) qv[c] = q[c * NU];
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) {
+              T r = 0;
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) r += Sm[c][b] * qv[c];
+              q[b * NU] = r * rdj;
+            }
+          }
+        }
       }
     }
+    __syncthreads();
   }
-  // ---- MODE 1: resolution indicator on psi and element viscosity ----------
   if (MODE == 1) {
-    // chi = (Vinv x ... x Vinv) psi by DIM line passes (ping-pong in chi)
-    for (int pass = 0; pass < DIM; ++pass) {
-      for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
-        const int el = idx / NU, i = idx % NU;
-        const T* src = pass == 0 ? us + el * NU : chi + (el * 2 + ((pass - 1) & 1)) * NU;
-        T* dst = chi + (el * 2 + (pass & 1)) * NU;
-        const int ia = ucoord<N>(i, pass), st = ipow(N, pass), lb = i - ia * st;
-        T acc = 0;
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc += op.Vinv[ia][j] * src[lb + j * st];
-        dst[i] = acc;
-      }
-      __syncthreads();
-    }
     for (int el = tid; el < ne; el += blockDim.x) {
       const T* c = chi + (el * 2 + ((DIM - 1) & 1)) * NU;
       double tot = 0.0, hi = 0.0;
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
         tot += v;
         bool top = false;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) top = top || (ucoord<N>(i, a) == N - 1);
+        for (int b = 0; b < DIM; ++b) top = top || (ucoord<N>(i, b) == N - 1);
         if (top) hi += v;
       }
       double nu = 0.0;
@@ -268,10 +307,10 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
       }
       nus[el] = (T)nu;
     }
+    __syncthreads();
   }
-  __syncthreads();
 
-  // ---- Step 5 on L flux points (needs q^f, Eq. extrapolateGrad) ------------
+  // ---- Step 5 on L flux points (q^f by Eq. extrapolateGrad) ----------------
   for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
     const int el = idx / NF, k = idx % NF;
     if (!lm[el * NF + k]) {
@@ -282,19 +321,24 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
     T xi[3], Sm[3][3];
-    fpt_xi<DIM, N>(k, op.x, xi);
+    fpt_xi<DIM, N>(k, O.x, xi);
     metric<DIM>(gs + el * NG, xi, Sm);
     const T sg = s ? (T)1 : (T)-1;
     T pn[3], pm = 0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      pn[c] = sg * Sm[a][c];
+      T sac = Sm[0][c];
+#pragma unroll
+      for (int b = 1; b < DIM; ++b)
+        if (b == a) sac = Sm[b][c];
+      pn[c] = sg * sac;
       pm += pn[c] * pn[c];
     }
     pm = sqrt_(pm);
+    const T rpm = (T)1 / pm;
     T nh[3];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) nh[c] = pn[c] / pm;
+    for (int c = 0; c < DIM; ++c) nh[c] = pn[c] * rpm;
     const int st = ipow(N, a);
     if (MODE == 0) {
       T qf[2][3];
@@ -302,15 +346,15 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
       for (int fld = 0; fld < 2; ++fld)
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
-          const T* ql = q + ((el * 2 + fld) * DIM + c) * NU + b0;
+          const T* ql = qt + ((el * 2 + fld) * DIM + c) * NU + b0;
           T acc = 0;
 #pragma unroll
-          for (int j = 0; j < N; ++j) acc += op.lend[s][j] * ql[j * st];
+          for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
           qf[fld][c] = acc;
         }
       T x[3], v[3];
       map_point<S::ET_, T>(gs + el * NG, xi, x);
-      velocity<DIM, T>(A.vel, x, tstage, v);
+      velocity<DIM, T>(BC.vel, x, gfac, v);
       T vn = 0, v2 = 0, g2 = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
@@ -318,16 +362,16 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
         v2 += v[c] * v[c];
         g2 += qf[1][c] * qf[1][c];
       }
-      const T M = fmax(sqrt_(v2), (T)A.prm.gamma);
-      const T gm = fmax(sqrt_(g2), (T)A.prm.delta);
+      const T M = fmax(sqrt_(v2), P.gamma);
+      const T gm = fmax(sqrt_(g2), P.delta);
       const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
       const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
-      const T sharp = (T)A.prm.gamma * pL * ((T)1 - pL) / gm;
+      const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) fvn += nh[c] * M * ((T)A.prm.eps * qf[0][c] - sharp * qf[1][c]);
-      const T Fp = (T)0.5 * (pL + pR) * vn - fvn + (T)A.prm.tau * (pL - pR);
-      const T Fs = (T)0.5 * (sL + sR) * vn + (T)A.prm.tau_psi * (sL - sR);
+      for (int c = 0; c < DIM; ++c) fvn += nh[c] * (P.eps * qf[0][c] - sharp * qf[1][c]);
+      const T Fp = (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
+      const T Fs = (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
       fc[((e0 + el) * 2 + 1) * NF + k] = Fs;
       cor[(el * 2 + 0) * NF + k] = pm * Fp;
@@ -336,14 +380,13 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
       T gn = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        const T* ql = q + (el * DIM + c) * NU + b0;
+        const T* ql = qt + (el * DIM + c) * NU + b0;
         T acc = 0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc += op.lend[s][j] * ql[j * st];
+        for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
         gn += nh[c] * acc;
       }
-      const T L_ = uf[el * NF + k], R_ = uo[el * NF + k];
-      const T F = -nus[el] * gn + (T)A.prm.tau_pseudo * (L_ - R_);
+      const T F = -nus[el] * gn + P.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       cor[el * NF + k] = pm * F;
     }
@@ -354,28 +397,28 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
   for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
-    upt_xi<DIM, N>(i, op.x, xi);
+    upt_xi<DIM, N>(i, O.x, xi);
     const T dj = metric<DIM>(gs + el * NG, xi, Sm);
     if (MODE == 0) {
       T x[3], v[3];
       map_point<S::ET_, T>(gs + el * NG, xi, x);
-      velocity<DIM, T>(A.vel, x, tstage, v);
+      velocity<DIM, T>(BC.vel, x, gfac, v);
       T qp[3], qs[3], v2 = 0, g2 = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        qp[c] = q[((el * 2 + 0) * DIM + c) * NU + i];
-        qs[c] = q[((el * 2 + 1) * DIM + c) * NU + i];
+        qp[c] = qt[((el * 2 + 0) * DIM + c) * NU + i];
+        qs[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
         v2 += v[c] * v[c];
         g2 += qs[c] * qs[c];
       }
-      const T M = fmax(sqrt_(v2), (T)A.prm.gamma);
-      const T gm = fmax(sqrt_(g2), (T)A.prm.delta);
+      const T M = fmax(sqrt_(v2), P.gamma);
+      const T gm = fmax(sqrt_(g2), P.delta);
       const T ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];
-      const T sharp = (T)A.prm.gamma * ph * ((T)1 - ph) / gm;
+      const T sharp = P.gamma * ph * ((T)1 - ph) / gm;
       T f0[3], f1[3];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        f0[c] = ph * v[c] - M * ((T)A.prm.eps * qp[c] - sharp * qs[c]);
+        f0[c] = ph * v[c] - M * (P.eps * qp[c] - sharp * qs[c]);
         f1[c] = ps * v[c];
       }
 #pragma unroll
@@ -386,14 +429,14 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
           t0 += Sm[a][c] * f0[c];
           t1 += Sm[a][c] * f1[c];
         }
-        q[((el * 2 + 0) * DIM + a) * NU + i] = t0;
-        q[((el * 2 + 1) * DIM + a) * NU + i] = t1;
+        qt[((el * 2 + 0) * DIM + a) * NU + i] = t0;
+        qt[((el * 2 + 1) * DIM + a) * NU + i] = t1;
       }
     } else {
       T qs[3], g2 = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        qs[c] = q[(el * DIM + c) * NU + i];
+        qs[c] = qt[(el * DIM + c) * NU + i];
         g2 += qs[c] * qs[c];
       }
       const T nu = nus[el];
@@ -402,47 +445,56 @@ __global__ void __launch_bounds__(kThreads) kb_tensor(const KArgs A) {
         T t0 = 0;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) t0 += Sm[a][c] * (-nu * qs[c]);
-        q[(el * DIM + a) * NU + i] = t0;
+        qt[(el * DIM + a) * NU + i] = t0;
       }
       const T qm = sqrt_(g2);
       const T p0 = (T)A.psi0[(e0 + el) * NU + i];
-      const T src = tanh_(p0 / fmax(qm, (T)A.prm.delta)) * ((T)1 - qm);
-      us[el * NU + i] = src * dj;  // psi itself is no longer needed
+      chi[el * 2 * NU + i] = tanh_(p0 / fmax(qm, P.delta)) * ((T)1 - qm) * dj;
     }
   }
   __syncthreads();
 
-  // ---- Step 4/6: discontinuous normal flux and flux jump at flux points ---
-  for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
-    const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
-    int a, s, b0;
-    fline<DIM, N>(k, a, s, b0);
-    const T* fl = q + ((el * NFLD + fld) * DIM + a) * NU + b0;
-    const int st = ipow(N, a);
-    T acc = 0;
+  // ---- Steps 4/6 by axis: normal flux at the line ends, flux jumps, the
+  //      line derivative and the two end lifts, summed into us
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc += op.lend[s][j] * fl[j * st];
-    const T fperp = s ? acc : -acc;
-    cor[idx] = cor[idx] - fperp;
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a);
+      const int base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+#pragma unroll
+      for (int fld = 0; fld < NFLD; ++fld) {
+        const T* fl = qt + ((lel * NFLD + fld) * DIM + a) * NU + base;
+        T v[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = fl[j * st];
+        T fp0 = 0, fp1 = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          fp0 += O.lend[0][j] * v[j];
+          fp1 += O.lend[1][j] * v[j];
+        }
+        const int fo = (lel * NFLD + fld) * NF;
+        const T c0 = cor[fo + k0] + fp0;   // F~ - f~perp with f~perp = -f~_a(-1)
+        const T c1 = cor[fo + k1] - fp1;   // F~ - f~perp with f~perp = +f~_a(+1)
+        T* dv = us + (lel * NFLD + fld) * NU + base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          T acc = -O.gLd[j] * c0 + O.gRd[j] * c1;
+#pragma unroll
+          for (int m = 0; m < N; ++m) acc += O.D[j][m] * v[m];
+          dv[j * st] = a == 0 ? acc : dv[j * st] + acc;
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-
-  // ---- Step 6: divergence with the lift of the known flux jumps ------------
+  // ---- coalesced write of the partial divergence
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-    const T* cr = cor + (el * NFLD + fld) * NF;
-    T div = 0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const int ia = ucoord<N>(i, a), st = ipow(N, a), lb = i - ia * st;
-      const T* fl = q + ((el * NFLD + fld) * DIM + a) * NU;
-      T acc = 0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) acc += op.D[ia][j] * fl[lb + j * st];
-      div += acc - op.gLd[ia] * cr[fpt_of<DIM, N>(i, a, 0)] + op.gRd[ia] * cr[fpt_of<DIM, N>(i, a, 1)];
-    }
-    if (MODE == 1) div -= us[el * NU + i];
-    rp[((e0 + el) * 2 + F0 + fld) * NU + i] = div;
+    T d = us[idx];
+    if (MODE == 1) d -= chi[el * 2 * NU + i];
+    rp[((e0 + el) * 2 + F0 + fld) * NU + i] = d;
   }
 }
 
@@ -485,8 +537,8 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
   const int tid = threadIdx.x;
   const int stage = A.stage;
 
-  load_ops<N, T>(A.ops, op);
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  load_ops<N, T>(bulk<T>(A).ops, op);
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
     const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
@@ -495,6 +547,11 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
   __syncthreads();
 
   double sq = 0.0;
+  RKConstF rkc;
+  rkc.half_dt = (float)(0.5 * A.dt);
+  rkc.dt = (float)A.dt;
+  rkc.dt6 = (float)(A.dt / 6.0);
+  rkc.rdt = 1.0 / A.dt;
   if (stage != 0) {
     // ---- common flux on R flux points: minus L's physical flux, this side's metric
     for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
@@ -512,7 +569,13 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
       const int a = (k / S::NFP) >> 1;
       T pm = 0;
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) pm += Sm[a][c] * Sm[a][c];
+      for (int c = 0; c < DIM; ++c) {
+        T sac = Sm[0][c];
+#pragma unroll
+        for (int b = 1; b < DIM; ++b)
+          if (b == a) sac = Sm[b][c];
+        pm += sac * sac;
+      }
       pm = sqrt_(pm);
 #pragma unroll
       for (int fld = 0; fld < NFLD; ++fld)
@@ -532,23 +595,14 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
       T xi[3], Sm[3][3];
       upt_xi<DIM, N>(i, op.x, xi);
       const T dj = metric<DIM>(gs + el * NG, xi, Sm);
-      const double R = (double)(-div / dj);
+      const T R = -div / dj;
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
-        A.out[(int64_t)(F0 + fld - F0) * A.E * NU + (e0 + el) * NU + i] = R;
+        A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
         continue;
       }
-      double uu = A.u[g], aa = stage == 1 ? 0.0 : A.acc[g];
-      const double uold = uu;
-      const double y = rk_update(stage, A.dt, R, uu, aa);
-      if (stage < 4) A.acc[g] = aa;
-      else A.u[g] = uu;
-      if (MODE == 1 && stage == 4) {
-        const double d = (uu - uold) / A.dt;
-        sq += d * d;
-      }
-      if (!isfinite(y)) atomicExch(&A.status[ST_STATUS], -4);
-      const T yt = (T)y;
+      const T yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
+      if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
       ustg[g] = yt;
       ys[idx] = yt;
     }

@@ -24,20 +24,20 @@ struct TriOpsS {
 };
 
 template <int P, typename T>
-__device__ __forceinline__ void load_tri_ops(const TriOps& o, TriOpsS<P, T>& s) {
+__device__ __forceinline__ void load_tri_ops(const TriOpsT<T>& o, TriOpsS<P, T>& s) {
   constexpr int NU = TriS<P>::NU, NF = TriS<P>::NF;
   for (int t = threadIdx.x; t < NF * NU; t += blockDim.x) {
-    s.L[t / NU][t % NU] = (T)o.L[t];
-    s.LIFT[t / NF][t % NF] = (T)o.LIFT[t];
+    s.L[t / NU][t % NU] = o.L[t];
+    s.LIFT[t / NF][t % NF] = o.LIFT[t];
   }
   for (int t = threadIdx.x; t < NU * NU; t += blockDim.x) {
-    s.Dr[t / NU][t % NU] = (T)o.Dr[t];
-    s.Ds[t / NU][t % NU] = (T)o.Ds[t];
-    s.Vinv[t / NU][t % NU] = (T)o.Vinv[t];
+    s.Dr[t / NU][t % NU] = o.Dr[t];
+    s.Ds[t / NU][t % NU] = o.Ds[t];
+    s.Vinv[t / NU][t % NU] = o.Vinv[t];
   }
   for (int t = threadIdx.x; t < NF * 2; t += blockDim.x) {
-    s.xf[t / 2][t % 2] = (T)o.xf[t];
-    s.nref[t / 2][t % 2] = (T)o.nref[t];
+    s.xf[t / 2][t % 2] = o.xf[t];
+    s.nref[t / 2][t % 2] = o.nref[t];
   }
   for (int t = threadIdx.x; t < NU; t += blockDim.x) s.high[t] = o.high[t];
 }
@@ -100,14 +100,20 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   T* fc = reinterpret_cast<T*>(A.fc);
   T* rp = reinterpret_cast<T*>(A.rp);
   const int tid = threadIdx.x;
-  const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
+  const BulkConst<T>& BC = bulk<T>(A);
+  const PrmT<T> Pm = BC.prm;
+  __shared__ T gfac_s;
+  if (tid == 0) {
+    const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
+    gfac_s = (T)time_factor(A, tstage);
+  }
 
-  load_tri_ops<P, T>(A.tri, op);
+  load_tri_ops<P, T>(tri_of<T>(A), op);
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
     us[idx] = ustg[((e0 + el) * 2 + F0 + fld) * NU + i];
   }
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   __syncthreads();
   for (int el = tid; el < ne; el += blockDim.x) {
     TriMet<T> m;
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     met[el * 5 + 3] = m.S[1][1];
     met[el * 5 + 4] = m.dj;
   }
+  const T gfac = gfac_s;
   // ---- Step 1 and partner traces
   for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
     const int el = idx / NF, k = idx % NF;
@@ -215,18 +222,18 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
         }
       T x[3], v[3];
       map_point<ET_TRI, T>(gs + el * NG, op.xf[k], x);
-      velocity<2, T>(A.vel, x, tstage, v);
+      velocity<2, T>(BC.vel, x, gfac, v);
       const T vn = v[0] * nh[0] + v[1] * nh[1];
-      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), (T)A.prm.gamma);
-      const T gm = fmax(sqrt_(qf[1][0] * qf[1][0] + qf[1][1] * qf[1][1]), (T)A.prm.delta);
+      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
+      const T gm = fmax(sqrt_(qf[1][0] * qf[1][0] + qf[1][1] * qf[1][1]), Pm.delta);
       const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
       const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
-      const T sharp = (T)A.prm.gamma * pL * ((T)1 - pL) / gm;
+      const T sharp = Pm.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * ((T)A.prm.eps * qf[0][c] - sharp * qf[1][c]);
-      const T Fp = (T)0.5 * (pL + pR) * vn - fvn + (T)A.prm.tau * (pL - pR);
-      const T Fs = (T)0.5 * (sL + sR) * vn + (T)A.prm.tau_psi * (sL - sR);
+      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qf[0][c] - sharp * qf[1][c]);
+      const T Fp = (T)0.5 * (pL + pR) * vn - fvn + Pm.tau * (pL - pR);
+      const T Fs = (T)0.5 * (sL + sR) * vn + Pm.tau_psi * (sL - sR);
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
       fc[((e0 + el) * 2 + 1) * NF + k] = Fs;
       cor[(el * 2 + 0) * NF + k] = pm * Fp;
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
         for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
         gn += nh[c] * acc;
       }
-      const T F = -nus[el] * gn + (T)A.prm.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
+      const T F = -nus[el] * gn + Pm.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       cor[el * NF + k] = pm * F;
     }
@@ -263,15 +270,15 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
         xi[1] = (T)(2.0 * (jj + 1) / (P + 3) - 1.0);
       }
       map_point<ET_TRI, T>(gs + el * NG, xi, x);
-      velocity<2, T>(A.vel, x, tstage, v);
+      velocity<2, T>(BC.vel, x, gfac, v);
       const T qp0 = q[((el * 2 + 0) * 2 + 0) * NU + i], qp1 = q[((el * 2 + 0) * 2 + 1) * NU + i];
       const T qs0 = q[((el * 2 + 1) * 2 + 0) * NU + i], qs1 = q[((el * 2 + 1) * 2 + 1) * NU + i];
-      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), (T)A.prm.gamma);
-      const T gm = fmax(sqrt_(qs0 * qs0 + qs1 * qs1), (T)A.prm.delta);
+      const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
+      const T gm = fmax(sqrt_(qs0 * qs0 + qs1 * qs1), Pm.delta);
       const T ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];
-      const T sharp = (T)A.prm.gamma * ph * ((T)1 - ph) / gm;
-      const T f00 = ph * v[0] - M * ((T)A.prm.eps * qp0 - sharp * qs0);
-      const T f01 = ph * v[1] - M * ((T)A.prm.eps * qp1 - sharp * qs1);
+      const T sharp = Pm.gamma * ph * ((T)1 - ph) / gm;
+      const T f00 = ph * v[0] - M * (Pm.eps * qp0 - sharp * qs0);
+      const T f01 = ph * v[1] - M * (Pm.eps * qp1 - sharp * qs1);
       const T f10 = ps * v[0], f11 = ps * v[1];
       q[((el * 2 + 0) * 2 + 0) * NU + i] = mt[0] * f00 + mt[1] * f01;
       q[((el * 2 + 0) * 2 + 1) * NU + i] = mt[2] * f00 + mt[3] * f01;
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       q[(el * 2 + 1) * NU + i] = mt[2] * (-nu * qs0) + mt[3] * (-nu * qs1);
       const T qm = sqrt_(qs0 * qs0 + qs1 * qs1);
       const T p0 = (T)A.psi0[(e0 + el) * NU + i];
-      us[el * NU + i] = tanh_(p0 / fmax(qm, (T)A.prm.delta)) * ((T)1 - qm) * mt[4];
+      us[el * NU + i] = tanh_(p0 / fmax(qm, Pm.delta)) * ((T)1 - qm) * mt[4];
     }
   }
   __syncthreads();
@@ -355,8 +362,8 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   const int tid = threadIdx.x;
   const int stage = A.stage;
 
-  load_tri_ops<P, T>(A.tri, op);
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = (T)A.geo[e0 * NG + idx];
+  load_tri_ops<P, T>(tri_of<T>(A), op);
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
     const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
@@ -364,6 +371,11 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   }
   __syncthreads();
   double sq = 0.0;
+  RKConstF rkc;
+  rkc.half_dt = (float)(0.5 * A.dt);
+  rkc.dt = (float)A.dt;
+  rkc.dt6 = (float)(A.dt / 6.0);
+  rkc.rdt = 1.0 / A.dt;
   if (stage != 0) {
     for (int el = tid; el < ne; el += blockDim.x) {
       TriMet<T> m;
@@ -395,23 +407,14 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
       T div = ys[idx];
 #pragma unroll
       for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * c[k];
-      const double R = (double)(-div / djs[el]);
+      const T R = -div / djs[el];
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
-        A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = R;
+        A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
         continue;
       }
-      double uu = A.u[g], aa = stage == 1 ? 0.0 : A.acc[g];
-      const double uold = uu;
-      const double y = rk_update(stage, A.dt, R, uu, aa);
-      if (stage < 4) A.acc[g] = aa;
-      else A.u[g] = uu;
-      if (MODE == 1 && stage == 4) {
-        const double d = (uu - uold) / A.dt;
-        sq += d * d;
-      }
-      if (!isfinite(y)) atomicExch(&A.status[ST_STATUS], -4);
-      const T yt = (T)y;
+      const T yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
+      if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
       ustg[g] = yt;
       ys[idx] = yt;
     }
