@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=25, help="oracle RK4 steps for cpu_baseline (0: skip)")
     ap.add_argument("--mesh-n", type=int, default=128, help="elements per side (128 is the benchmark workload)")
     ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
+    ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
     return ap.parse_args()
 
 
@@ -177,10 +178,10 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False):
+def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False, vel_cache=True):
     import torch
     M = G.Mesh.from_synthetic(mesh, w.order)
-    P = G.make_params(w, precision)
+    P = G.make_params(w, precision, vel_cache=vel_cache)
     F = G.Field(M, P, ic=w.circle, precondition=True)
     ndof = M.info.n_dof
     stream = torch.cuda.current_stream()
@@ -330,11 +331,13 @@ def main():
     import paper_2006_10967_gb300 as G
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    vc = not args.no_vel_cache
     main_out, F = run_path(G, S, w, mesh, args.precision, args.steps, max(args.warmup, 3), world, rank, flush,
-                           want_kernel=True, e2e=True)
+                           want_kernel=True, e2e=True, vel_cache=vc)
     fp64_out = None
     if args.precision == "mixed" and args.fp64_steps > 0:
-        fp64_out, _ = run_path(G, S, w, mesh, "fp64", args.fp64_steps, 1, world, rank, flush, want_kernel=True)
+        fp64_out, _ = run_path(G, S, w, mesh, "fp64", args.fp64_steps, 1, world, rank, flush, want_kernel=True,
+                               vel_cache=vc)
 
     # roofline of the dominant kernel
     kern = main_out["kernels"]
@@ -367,7 +370,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": main_out["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64",
-            "data": "synthetic", "config": dict(workload_cfg, precision=args.precision),
+            "data": "synthetic", "config": dict(workload_cfg, precision=args.precision, velocity_cache=vc),
             "clocks": main_out["clocks"], "e2e": main_out["e2e"],
             "gpu_launches": int(sum(v[1] for v in kern.values())) * args.steps + 3 * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "status": main_out["status"]}

@@ -131,6 +131,11 @@ typedef struct fr_params {
   double s0, kappa, nu_max; /* Eq. nu_s */
   double delta;          /* guard: |grad psi| -> max(|grad psi|, delta) */
   fr_velocity vel;
+  int32_t vel_cache;     /* 1: store the time-independent factor v(x) of u(x,t) = g(t) v(x)
+                            at every solution and flux point at init (quad/hex; dim x (nu+nf)
+                            values per element in the stage precision) instead of evaluating
+                            v(x) every stage; 0: evaluate in the kernels */
+  int32_t reserved0;
 } fr_params;
 
 typedef struct fr_ic {
@@ -243,6 +248,32 @@ int fr_rhs(fr_field* field, double t, double* dev_out, void* stream);
 /* Same for the preconditioning system (Eq. pseudotimesystem), psi rates into
  * dev_out (n_dof doubles), with the stored psi0. */
 int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
+
+/* ---- discrete adjoint ---------------------------------------------------
+ * The paper has no adjoint; these calls give the exact gradient of the FR
+ * march's discrete map for a loss of the final state, with respect to the
+ * initial fields and the stream-function coefficients (FR_VEL_STREAM).
+ * Built for the FP64 path on quadrilaterals (p <= 6) and hexahedra (p <= 3);
+ * other fields return FR_EUNSUPPORTED.  The recorded window must not contain
+ * a preconditioning step (n > 0, n % n_precond == 0).
+ *
+ * fr_adjoint_workspace_bytes: device bytes for a window of n_steps with a
+ *   checkpoint every ckpt_every steps ((n_steps/ckpt_every + 1) solution
+ *   copies + 4 * ckpt_every stage inputs + adjoint work arrays).
+ * fr_adjoint_record: advance n_steps from the current state (as fr_step),
+ *   keeping checkpoints in `workspace` (device, caller-owned, 256-byte
+ *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
+ * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
+ *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,
+ *   2 * n_dof: phi then psi) and, for a stream-function velocity,
+ *   dJ/d(A_1..A_M, B_1..B_M) to dJ_dcoef (device, 2M, or NULL).  Recomputes
+ *   the forward stages segment by segment from the checkpoints; on return the
+ *   field is back at the end of the window.  Synchronises `stream`. */
+int fr_adjoint_workspace_bytes(fr_field* field, int n_steps, int ckpt_every, size_t* bytes);
+int fr_adjoint_record(fr_field* field, int n_steps, int ckpt_every, void* workspace, size_t workspace_bytes,
+                      void* stream);
+int fr_adjoint_step(fr_field* field, const double* dJ_dphiT, const double* dJ_dpsiT, double* dJ_du0,
+                    double* dJ_dcoef, void* stream);
 
 /* Per-kernel timing (not part of the method): with enable != 0 every FR
  * kernel launch of fr_step / fr_precondition is bracketed by CUDA events on

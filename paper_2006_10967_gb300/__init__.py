@@ -97,6 +97,7 @@ def make_params(w, precision="fp64", **kw):
     p.kappa = g("kappa")
     p.nu_max = g("nu_max")
     p.delta = g("delta")
+    p.vel_cache = int(bool(kw.get("vel_cache", True)))
     vel = kw.get("velocity", w.velocity)
     p.vel.kind = VELS[vel.kind]
     p.vel.T = float(vel.T)
@@ -199,6 +200,31 @@ class Field:
               "fr_rhs_pseudo")
         return out
 
+    # ---- discrete adjoint -------------------------------------------------
+    def adjoint_record(self, n_steps, ckpt_every, stream=None):
+        """Advance n_steps keeping checkpoints for adjoint_step (fr_adjoint_record)."""
+        nbytes = C.c_size_t()
+        check(lib().fr_adjoint_workspace_bytes(self.handle, int(n_steps), int(ckpt_every), C.byref(nbytes)),
+              "fr_adjoint_workspace_bytes")
+        self._adj_ws = self.torch.empty(nbytes.value + 256, dtype=self.torch.uint8, device="cuda")
+        base = (self._adj_ws.data_ptr() + 255) // 256 * 256
+        check(lib().fr_adjoint_record(self.handle, int(n_steps), int(ckpt_every), C.c_void_p(base), nbytes.value,
+                                      self._stream(stream)), "fr_adjoint_record")
+
+    def adjoint_step(self, dJ_dphiT, dJ_dpsiT=None, n_coef=0, stream=None):
+        """(dJ/du0 as a (2, E, Nu) tensor, dJ/dcoef (2M,) or None) via fr_adjoint_step."""
+        t = self.torch
+        gphi = dJ_dphiT.to(device="cuda", dtype=t.float64).contiguous()
+        gpsi = None if dJ_dpsiT is None else dJ_dpsiT.to(device="cuda", dtype=t.float64).contiguous()
+        out = t.empty((2,) + self.mesh.shape, dtype=t.float64, device="cuda")
+        coef = t.zeros(n_coef, dtype=t.float64, device="cuda") if n_coef else None
+        check(lib().fr_adjoint_step(self.handle, C.c_void_p(gphi.data_ptr()),
+                                    C.c_void_p(gpsi.data_ptr()) if gpsi is not None else None,
+                                    C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(coef.data_ptr()) if coef is not None else None,
+                                    self._stream(stream)), "fr_adjoint_step")
+        return out, coef
+
     def profile(self, enable=True):
         check(lib().fr_profile(self.handle, int(bool(enable))), "fr_profile")
 
@@ -235,3 +261,30 @@ def fr_mass_integral(*a):
 
 def fr_adjoint_step(*a):
     return lib().fr_adjoint_step(*a)
+
+
+def flow_function(mesh, params_fn, n_steps, ckpt_every):
+    """A torch.autograd.Function for phi_T = Flow(phi0, coef): the FR march of
+    n_steps from phi0 (psi0 = phi0 - 1/2, no preconditioning) with a stream
+    velocity whose coefficients are coef = (A_1..A_M, B_1..B_M).
+    params_fn(coef) -> fr_params.  Backward is the hand-written adjoint
+    (fr_adjoint_record / fr_adjoint_step)."""
+    import torch
+
+    class _Flow(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi0, coef):
+            P = params_fn(coef.detach().cpu().numpy())
+            F = Field(mesh, P, phi0=phi0.detach().cpu().numpy(), precondition=False)
+            F.adjoint_record(n_steps, ckpt_every)
+            ctx.field = F
+            ctx.n_coef = coef.numel()
+            return torch.from_numpy(F.get(0)).to(phi0.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            du0, dc = ctx.field.adjoint_step(g, None, ctx.n_coef)
+            gphi = (du0[0] + du0[1]).to(g.device)      # psi0 = phi0 - 1/2
+            return gphi, dc.to(g.device)
+
+    return _Flow.apply

@@ -46,7 +46,7 @@ class fr_params(C.Structure):
                 ("pseudo_kmax", C.c_int32), ("pseudo_dtau", C.c_double), ("pseudo_tol", C.c_double),
                 ("pseudo_fixed", C.c_int32), ("precision", C.c_int32), ("s0", C.c_double),
                 ("kappa", C.c_double), ("nu_max", C.c_double), ("delta", C.c_double),
-                ("vel", fr_velocity)]
+                ("vel", fr_velocity), ("vel_cache", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class fr_ic(C.Structure):
@@ -81,6 +81,9 @@ _SIGS = {
     "fr_field_set_device": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "fr_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "fr_rhs_pseudo": (C.c_int, [_vp, _vp, _vp]),
+    "fr_adjoint_workspace_bytes": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
+    "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fr_profile": (C.c_int, [_vp, C.c_int]),
     "fr_profile_read": (C.c_int, [_vp, _vp, _dp, C.POINTER(C.c_int64)]),
     "fr_field_destroy": (None, [_vp]),

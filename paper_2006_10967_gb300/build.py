@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC"]
 
-CU = ["api.cu", "k_quad.cu", "k_hex.cu", "k_tri.cu", "noalloc.cu"]
+CU = ["api.cu", "k_quad.cu", "k_hex.cu", "k_tri.cu", "noalloc.cu", "adjoint.cu"]
 CPP = ["mesh.cpp", "refel.cpp"]
 
 

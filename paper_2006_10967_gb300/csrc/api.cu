@@ -6,8 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "internal.hpp"
-#include "kdispatch.hpp"
+#include "field.cuh"
 
 using namespace frp;
 
@@ -18,7 +17,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer;
+  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t total;
 };
@@ -88,7 +87,7 @@ void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
   }
 }
 
-Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
+Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cache) {
   Layout L{};
   const size_t E = (size_t)m.E, NU = m.nu, NF = m.nf, NG = (size_t)m.dim * m.ncoef;
   const size_t tb = precision == FR_FP64 ? 8 : 4;
@@ -113,6 +112,9 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks) {
   L.fc = take(E * 2 * NF * tb);
   L.psi0 = take(E * NU * sizeof(double));
   L.xfer = take(E * NU * sizeof(double));
+  const bool vc = vel_cache && m.etype != FR_TRI;
+  L.vsu = vc ? take(E * m.dim * NU * tb) : 0;
+  L.vsf = vc ? take(E * m.dim * NF * tb) : 0;
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -245,21 +247,6 @@ __global__ void k_mass(KArgs A, int64_t NU, int fld, int mixed) {
 
 }  // namespace
 
-struct fr_field {
-  int dim = 0, etype = 0, order = 0, nu = 0, nf = 0, precision = 0;
-  int64_t E = 0;
-  KArgs args{};
-  KernelSet ks{};
-  fr_params prm{};
-  int64_t nstep = 0;
-  int64_t n_precond_done = 0;
-  int sticky = FR_OK;
-  int mass_grid = 1;
-  double* xfer = nullptr;  // E*nu doubles, staging for get/set in the mixed path
-  // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
-  int profiling = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];
-};
 
 namespace {
 
@@ -338,6 +325,18 @@ int run_step(fr_field* f, cudaStream_t s) {
   return FR_OK;
 }
 
+}  // namespace
+
+namespace frp {
+int field_run_step(fr_field* f, cudaStream_t s, bool allow_precondition) {
+  if (!allow_precondition && f->nstep > 0 && f->nstep % f->prm.n_precond == 0) return FR_EUNSUPPORTED;
+  return run_step(f, s);
+}
+int field_stage_and_traces(fr_field* f, cudaStream_t s) { return stage_and_traces(f, s); }
+}  // namespace frp
+
+namespace {
+
 int read_status(fr_field* f, cudaStream_t s) {
   int32_t st[ST_WORDS];
   CK(cudaMemcpyAsync(st, f->args.status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -357,7 +356,7 @@ extern "C" int fr_field_workspace_bytes(const fr_mesh* m, const fr_params* prm, 
   int mg;
   launch_elementwise_grid(m->E * m->nu, &mg);
   const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
-  *bytes = make_layout(*m, prm->precision, mb).total;
+  *bytes = make_layout(*m, prm->precision, mb, prm->vel_cache).total;
   return FR_OK;
 }
 
@@ -373,7 +372,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   int mg;
   launch_elementwise_grid(m->E * m->nu, &mg);
   const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
-  const Layout L = make_layout(*m, prm->precision, mb);
+  const Layout L = make_layout(*m, prm->precision, mb, prm->vel_cache);
   if (ws_bytes < L.total) return FR_ENOMEM;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
@@ -429,6 +428,8 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.fc = b + L.fc;
   A.psi0 = reinterpret_cast<double*>(b + L.psi0);
   f->xfer = reinterpret_cast<double*>(b + L.xfer);
+  A.vsu = L.vsu ? b + L.vsu : nullptr;
+  A.vsf = L.vsf ? b + L.vsf : nullptr;
   A.out = nullptr;
   A.stage = 0;
   A.use_dev_time = 0;
@@ -496,6 +497,10 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   if (err == FR_OK && cudaMemsetAsync(b + L.dstate, 0, DS_WORDS * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaMemsetAsync(b + L.acc, 0, m->E * 2 * m->nu * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaMemsetAsync(b + L.fc, 0, L.psi0 - L.fc, s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && A.vsu) {
+    if (!f->ks.vcache) err = FR_EUNSUPPORTED;
+    else f->ks.vcache(A, s);
+  }
   if (err == FR_OK) err = stage_and_traces(f, s);
   if (err == FR_OK && ic->precondition) err = run_precondition(f, s);
   if (err == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) err = FR_ECUDA;

@@ -1,0 +1,41 @@
+// Internal device-side field handle of libfrpcpf (not part of the C ABI).
+#pragma once
+#include <utility>
+#include <vector>
+
+#include "internal.hpp"
+#include "kdispatch.hpp"
+
+// Recorded forward window for the adjoint (fr_adjoint_record).
+struct AdjRecord {
+  int active = 0;
+  int n_steps = 0, ckpt_every = 0, n_ckpt = 0;
+  int64_t step0 = 0;       // field step count at the start of the window
+  char* ws = nullptr;      // caller workspace
+  size_t bytes = 0;
+  size_t off_ckpt = 0, off_stage = 0, off_times = 0, off_Y = 0, off_lamuo = 0, off_lamU = 0, off_Lp = 0,
+         off_Lu = 0, off_Lk = 0, off_coefp = 0;
+  int adj_blocks = 0;
+};
+
+struct fr_field {
+  int dim = 0, etype = 0, order = 0, nu = 0, nf = 0, precision = 0;
+  int64_t E = 0;
+  frp::KArgs args{};
+  frp::KernelSet ks{};
+  fr_params prm{};
+  int64_t nstep = 0;
+  int64_t n_precond_done = 0;
+  int sticky = FR_OK;
+  int mass_grid = 1;
+  double* xfer = nullptr;  // E*nu doubles, staging for get/set in the mixed path
+  AdjRecord rec;
+  // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
+  int profiling = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];
+};
+
+namespace frp {
+int field_run_step(fr_field* f, cudaStream_t s, bool allow_precondition);
+int field_stage_and_traces(fr_field* f, cudaStream_t s);
+}  // namespace frp

@@ -24,11 +24,17 @@ void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
     cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
     init = true;
   }
-  launch_kernel(ka_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s);
+  launch_kernel(ka_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
+}
+
+template <int DIM, int N, typename T>
+void launch_vcache(const KArgs& A, cudaStream_t s) {
+  k_vel_cache<DIM, N, T><<<152 * 8, kThreads, 0, s>>>(A);
 }
 
 template <int DIM, int N, typename T>
 void fill_tensor(int64_t E, KernelSet* ks) {
+  ks->vcache = launch_vcache<DIM, N, T>;
   ks->kb[0] = launch_kb_tensor<DIM, N, T, 0>;
   ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;
   ks->ka[0] = launch_ka_tensor<DIM, N, T, 0>;

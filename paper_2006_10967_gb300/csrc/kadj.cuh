@@ -1,0 +1,568 @@
+// Hand-written discrete adjoint (vector-Jacobian product) of the FR residual
+// of the physical system on tensor elements.  The paper has no adjoint; this
+// is the transpose, step by step in reverse order, of the forward kernels of
+// ktensor.cuh (Steps 1-6 of Section 3.1), for the gradient of a misfit of
+// phi at the final time with respect to the initial fields and the velocity
+// coefficients.
+//
+// For a stage input U and an adjoint weight lam of its rate R(U) (both
+// fields), the three kernels compute a = (dR/dU)^T lam and accumulate
+// (dR/dc)^T lam over the stream-function coefficients c:
+//   adj_a : lam_div = -lam / det J; the adjoints of the lifted flux jumps at
+//           every flux point, scaled by the face metric -> Y (global)
+//   adj_b : forward recomputation of the element (traces, gradient, fluxes)
+//           and the reverse of Steps 6, 4, 5, 3 and 1 on the element; the
+//           adjoint of the common flux out of L gathers Y from the partner;
+//           writes the element part of a and the adjoint of the partner
+//           traces (lamuo, global)
+//   adj_c : gathers the partners' lamuo, adds L^T of it, and applies the
+//           RK4 adjoint recurrence.
+#pragma once
+#include "ktensor.cuh"
+
+namespace frp {
+
+struct AdjArgs {
+  KArgs K;              // forward arguments: K.ustg = stage input, K.tr = its traces, K.t = stage time
+  const double* lamk;   // E x 2 x NU adjoint weight of the stage rate (times lam_scale)
+  double lam_scale;
+  double* Y;            // E x 2 x NF
+  double* lamU;         // E x 2 x NU
+  double* lamuo;        // E x 2 x NF
+  double* coefp;        // [blocks][2 * n_modes] coefficient gradient partials (accumulated)
+  int want_coef;
+  // adj_c: RK4 recurrence  Lu = (first ? Lp : Lu) + a ;  Lk = c_lp * Lp + c_a * a
+  const double* Lp;
+  double* Lu;
+  double* Lk;
+  double c_lp, c_a;
+  int first;
+};
+
+template <int DIM, int N>
+struct AdjLayout {
+  using S = TS<DIM, N>;
+  static constexpr int LN = S::NFP;
+  // adj_b shared memory per element (doubles)
+  static constexpr int PER_EL = 2 * S::NU            // U, later lam_U
+                                + 2 * DIM * S::NU    // q
+                                + 2 * DIM * S::NU    // lam_f~, later lam_q, lam_q~
+                                + 2 * S::NU          // lam_div
+                                + 4 * 2 * S::NF      // uf, uo, luf, luo
+                                + 2 * DIM * S::NF    // lam_qf
+                                + S::NG;
+  static constexpr int BYTES_EL = PER_EL * 8 + S::NF;
+  static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
+  static constexpr int ET_S = 49152 / BYTES_EL < 1 ? 1 : 49152 / BYTES_EL;
+  static constexpr int ET = ET_T < ET_S ? ET_T : ET_S;
+  static constexpr int THREADS = ET * LN;
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
+};
+
+// d(v)/d(coefficients) contracted with lv, added to sh[0..2M) (stream field,
+// 2D): v = g * sum_m 2 pi (A_m cos th_m - B_m sin th_m) (ky_m, -kx_m).
+template <typename T>
+__device__ __forceinline__ void coef_vjp(const VelDescT<T>& V, const T* x, T g, const T* lv, double* sh) {
+  for (int m = 0; m < V.n_modes; ++m) {
+    T s, c;
+    scpi((T)2 * (V.kx[m] * x[0] + V.ky[m] * x[1]), &s, &c);
+    const T w = (T)(2.0 * M_PI) * g * (V.ky[m] * lv[0] - V.kx[m] * lv[1]);
+    atomicAdd(&sh[m], (double)(w * c));
+    atomicAdd(&sh[V.n_modes + m], (double)(-w * s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) adj_a(const AdjArgs B) {
+  using S = TS<DIM, N>;
+  using LY = AdjLayout<DIM, N>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, ET = LY::ET, LN = LY::LN;
+  const KArgs& A = B.K;
+  __shared__ double ld[ET * 2 * NU];
+  __shared__ double gs[ET * NG];
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)min((int64_t)ET, A.E - e0);
+  const int tid = threadIdx.x;
+  const TensorOpsT<double>& O = A.cd.ops;
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = A.geo[e0 * NG + idx];
+  __syncthreads();
+  for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) {
+    const int el = idx / (2 * NU), i = idx % NU;
+    double xi[3], Sm[3][3];
+    upt_xi<DIM, N>(i, O.x, xi);
+    const double dj = metric<DIM>(gs + el * NG, xi, Sm);
+    ld[idx] = -B.lam_scale * B.lamk[e0 * 2 * NU + idx] / dj;
+  }
+  __syncthreads();
+  const int lel = tid / LN, ll = tid % LN;
+  if (lel >= ne) return;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+    double pm[2];
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      double xi[3], Sm[3][3];
+      fpt_xi<DIM, N>((2 * a + sd) * NFP + ll, O.x, xi);
+      metric<DIM>(gs + lel * NG, xi, Sm);
+      double p2 = 0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) p2 += Sm[a][c] * Sm[a][c];
+      pm[sd] = sqrt(p2);
+    }
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+      const double* l = ld + (lel * 2 + fld) * NU + base;
+      double c0 = 0, c1 = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        c0 -= O.gLd[j] * l[j * st];
+        c1 += O.gRd[j] * l[j * st];
+      }
+      double* Y = B.Y + ((e0 + lel) * 2 + fld) * NF;
+      Y[(2 * a) * NFP + ll] = pm[0] * c0;
+      Y[(2 * a + 1) * NFP + ll] = pm[1] * c1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
+  using S = TS<DIM, N>;
+  using LY = AdjLayout<DIM, N>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, ET = LY::ET, LN = LY::LN;
+  const KArgs& A = B.K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* us = reinterpret_cast<double*>(smem_raw);  // [ET][2][NU]  U, later lam_U
+  double* qt = us + ET * 2 * NU;                       // [ET][2][DIM][NU] q
+  double* lf = qt + ET * 2 * DIM * NU;                 // [ET][2][DIM][NU] lam_f~ -> lam_q -> lam_q~
+  double* ld = lf + ET * 2 * DIM * NU;                 // [ET][2][NU] lam_div
+  double* uf = ld + ET * 2 * NU;                       // [ET][2][NF]
+  double* uo = uf + ET * 2 * NF;
+  double* luf = uo + ET * 2 * NF;
+  double* luo = luf + ET * 2 * NF;
+  double* lqf = luo + ET * 2 * NF;                     // [ET][2][DIM][NF]
+  double* gs = lqf + ET * 2 * DIM * NF;                // [ET][NG]
+  unsigned char* lm = reinterpret_cast<unsigned char*>(gs + ET * NG);
+  __shared__ double csh[2 * kMaxModes];
+
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)min((int64_t)ET, A.E - e0);
+  const int tid = threadIdx.x;
+  const double* ustg = reinterpret_cast<const double*>(A.ustg);
+  const double* tr = reinterpret_cast<const double*>(A.tr);
+  const BulkConst<double>& BC = A.cd;
+  const TensorOpsT<double>& O = BC.ops;
+  const PrmT<double> P = BC.prm;
+  const double g = time_factor(A, A.t);
+  const bool coef = B.want_coef && BC.vel.kind == 3 && DIM == 2;
+  const int M2 = 2 * BC.vel.n_modes;
+  for (int m = tid; m < 2 * kMaxModes; m += blockDim.x) csh[m] = 0.0;
+  for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) us[idx] = ustg[e0 * 2 * NU + idx];
+  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = A.geo[e0 * NG + idx];
+  __syncthreads();
+  const int lel = tid / LN, ll = tid % LN;
+  const bool lact = lel < ne;
+
+  // ---- forward: traces, partner traces, gradient (as in kb_tensor) --------
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+      const int32_t w0 = A.fnbr[(e0 + lel) * NF + k0], w1 = A.fnbr[(e0 + lel) * NF + k1];
+      lm[lel * NF + k0] = (unsigned char)(w0 & 1);
+      lm[lel * NF + k1] = (unsigned char)(w1 & 1);
+      const int64_t p0 = (int64_t)(w0 >> 1), p1 = (int64_t)(w1 >> 1);
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld) {
+        const double* ul = us + (lel * 2 + fld) * NU + base;
+        double v[N], f0 = 0, f1 = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          v[j] = ul[j * st];
+          f0 += O.lend[0][j] * v[j];
+          f1 += O.lend[1][j] * v[j];
+        }
+        const double o0 = (w0 & 1) ? tr[((p0 / NF) * 2 + fld) * NF + p0 % NF] : f0;
+        const double o1 = (w1 & 1) ? tr[((p1 / NF) * 2 + fld) * NF + p1 % NF] : f1;
+        const int fo = (lel * 2 + fld) * NF;
+        uf[fo + k0] = f0;
+        uf[fo + k1] = f1;
+        uo[fo + k0] = o0;
+        uo[fo + k1] = o1;
+        const double jm = o0 - f0, jp = o1 - f1;
+        double* qa = qt + ((lel * 2 + fld) * DIM + a) * NU + base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          double acc = O.gLd[j] * jm + O.gRd[j] * jp;
+#pragma unroll
+          for (int m = 0; m < N; ++m) acc += O.D[j][m] * v[m];
+          qa[j * st] = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+    const int el = idx / NU, i = idx % NU;
+    double xi[3], Sm[3][3];
+    upt_xi<DIM, N>(i, O.x, xi);
+    const double dj = metric<DIM>(gs + el * NG, xi, Sm);
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+      double* q = qt + (el * 2 + fld) * DIM * NU + i;
+      double qv[3];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) qv[c] = q[c * NU];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        double r = 0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) r += Sm[c][b] * qv[c];
+        q[b * NU] = r / dj;
+      }
+      ld[(el * 2 + fld) * NU + i] = -B.lam_scale * B.lamk[((e0 + el) * 2 + fld) * NU + i] / dj;
+    }
+  }
+  __syncthreads();
+
+  // ---- reverse of Step 6 by axis: lam_f~ from the derivative and the lifts
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld) {
+        const double* l = ld + (lel * 2 + fld) * NU + base;
+        double lv[N], c0 = 0, c1 = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          lv[j] = l[j * st];
+          c0 -= O.gLd[j] * lv[j];
+          c1 += O.gRd[j] * lv[j];
+        }
+        double* o = lf + ((lel * 2 + fld) * DIM + a) * NU + base;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          double acc = O.lend[0][m] * c0 - O.lend[1][m] * c1;
+#pragma unroll
+          for (int j = 0; j < N; ++j) acc += O.D[j][m] * lv[j];
+          o[m * st] = acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- reverse of Step 4 at solution points ---------------------------------
+  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+    const int el = idx / NU, i = idx % NU;
+    double xi[3], Sm[3][3], x[3], v[3];
+    upt_xi<DIM, N>(i, O.x, xi);
+    metric<DIM>(gs + el * NG, xi, Sm);
+    map_point<S::ET_, double>(gs + el * NG, xi, x);
+    velocity<DIM, double>(BC.vel, x, g, v);
+    double q0[3], q1[3], l0[3], l1[3], v2 = 0, g2 = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      q0[c] = qt[((el * 2 + 0) * DIM + c) * NU + i];
+      q1[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
+      v2 += v[c] * v[c];
+      g2 += q1[c] * q1[c];
+    }
+    // lam_f = S^T lam_f~
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      double s0 = 0, s1 = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        s0 += Sm[a][c] * lf[((el * 2 + 0) * DIM + a) * NU + i];
+        s1 += Sm[a][c] * lf[((el * 2 + 1) * DIM + a) * NU + i];
+      }
+      l0[c] = s0;
+      l1[c] = s1;
+    }
+    const double vm = sqrt(v2), M = fmax(vm, P.gamma);
+    const double qn = sqrt(g2), gm = fmax(qn, P.delta);
+    const double ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];
+    const double pp = ph * (1.0 - ph);
+    double lv0 = 0, lv1 = 0, lq1n = 0, la = 0;
+    double av[3];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      av[c] = P.eps * q0[c] - P.gamma * pp / gm * q1[c];
+      lv0 += l0[c] * v[c];
+      lv1 += l1[c] * v[c];
+      lq1n += l0[c] * q1[c];
+      la += l0[c] * av[c];
+    }
+    // f0 = phi v - M (eps q0 - gamma phi(1-phi) q1 / gm),  f1 = psi v
+    const double lphi = lv0 + M * P.gamma * (1.0 - 2.0 * ph) / gm * lq1n;
+    const double lpsi = lv1;
+    const double beta = M * P.gamma * pp;
+    double* lq = lf;  // lam_q overwrites lam_f~ (this point only)
+    double n1[3];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) n1[c] = qn > P.delta ? q1[c] / qn : 0.0;
+    double nl = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) nl += n1[c] * l0[c];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      lq[((el * 2 + 0) * DIM + c) * NU + i] = -M * P.eps * l0[c];
+      lq[((el * 2 + 1) * DIM + c) * NU + i] = qn > P.delta ? beta * (l0[c] - n1[c] * nl) / qn : beta * l0[c] / P.delta;
+    }
+    us[(el * 2 + 0) * NU + i] = lphi;  // lam_U (direct part) overwrites U
+    us[(el * 2 + 1) * NU + i] = lpsi;
+    if (coef) {
+      double lvv[3];
+      const double dM = vm > P.gamma ? 1.0 / vm : 0.0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) lvv[c] = ph * l0[c] + ps * l1[c] - la * v[c] * dM;
+      coef_vjp<double>(BC.vel, x, g, lvv, csh);
+    }
+  }
+  // ---- reverse of Step 5 at L flux points ------------------------------------
+  for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+    const int el = idx / NF, k = idx % NF;
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) lqf[((el * 2 + fld) * DIM + c) * NF + k] = 0.0;
+      luf[(el * 2 + fld) * NF + k] = 0.0;
+      luo[(el * 2 + fld) * NF + k] = 0.0;
+    }
+    if (!lm[el * NF + k]) continue;
+    const int64_t gk = (e0 + el) * NF + k;
+    const int32_t w = A.fnbr[gk];
+    const int64_t pg = (int64_t)(w >> 1);
+    const bool bnd = pg == gk;
+    int a, s, b0;
+    fline<DIM, N>(k, a, s, b0);
+    double xi[3], Sm[3][3], x[3], v[3];
+    fpt_xi<DIM, N>(k, O.x, xi);
+    metric<DIM>(gs + el * NG, xi, Sm);
+    double pn[3], pm = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      double sac = Sm[0][c];
+#pragma unroll
+      for (int b = 1; b < DIM; ++b)
+        if (b == a) sac = Sm[b][c];
+      pn[c] = (s ? 1.0 : -1.0) * sac;
+      pm += pn[c] * pn[c];
+    }
+    pm = sqrt(pm);
+    double nh[3];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) nh[c] = pn[c] / pm;
+    map_point<S::ET_, double>(gs + el * NG, xi, x);
+    velocity<DIM, double>(BC.vel, x, g, v);
+    const int st = ipow(N, a);
+    double qf0[3], qf1[3];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const double* q0l = qt + ((el * 2 + 0) * DIM + c) * NU + b0;
+      const double* q1l = qt + ((el * 2 + 1) * DIM + c) * NU + b0;
+      double a0 = 0, a1 = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const double lw = s ? O.lend[1][j] : O.lend[0][j];
+        a0 += lw * q0l[j * st];
+        a1 += lw * q1l[j * st];
+      }
+      qf0[c] = a0;
+      qf1[c] = a1;
+    }
+    // lam of the physical common flux out of L: this side's jump adjoints
+    // minus the partner's (the partner's flux is minus this one)
+    double lF[2];
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+      const double y = B.Y[((e0 + el) * 2 + fld) * NF + k];
+      lF[fld] = bnd ? y : y - B.Y[((pg / NF) * 2 + fld) * NF + pg % NF];
+    }
+    double vn = 0, v2 = 0, g2 = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      vn += v[c] * nh[c];
+      v2 += v[c] * v[c];
+      g2 += qf1[c] * qf1[c];
+    }
+    const double vm = sqrt(v2), M = fmax(vm, P.gamma);
+    const double qn = sqrt(g2), gm = fmax(qn, P.delta);
+    const double pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
+    const double sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
+    double nq = 0, fvn = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) nq += nh[c] * qf1[c];
+    const double pp = pL * (1.0 - pL);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) fvn += nh[c] * (P.eps * qf0[c] - P.gamma * pp / gm * qf1[c]);
+    // Fp = 1/2 (pL + pR) vn - M fvn + tau (pL - pR);  Fs = 1/2 (sL + sR) vn + tau_psi (sL - sR)
+    luf[(el * 2 + 0) * NF + k] = lF[0] * (0.5 * vn + P.tau + M * P.gamma * (1.0 - 2.0 * pL) / gm * nq);
+    luo[(el * 2 + 0) * NF + k] = lF[0] * (0.5 * vn - P.tau);
+    luf[(el * 2 + 1) * NF + k] = lF[1] * (0.5 * vn + P.tau_psi);
+    luo[(el * 2 + 1) * NF + k] = lF[1] * (0.5 * vn - P.tau_psi);
+    double n1[3], n1h = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      n1[c] = qn > P.delta ? qf1[c] / qn : 0.0;
+      n1h += n1[c] * nh[c];
+    }
+    const double beta = M * P.gamma * pp;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      lqf[((el * 2 + 0) * DIM + c) * NF + k] = -lF[0] * M * P.eps * nh[c];
+      lqf[((el * 2 + 1) * DIM + c) * NF + k] =
+          lF[0] * (qn > P.delta ? beta * (nh[c] - n1h * n1[c]) / qn : beta * nh[c] / P.delta);
+    }
+    if (coef) {
+      const double dM = vm > P.gamma ? 1.0 / vm : 0.0;
+      double lvv[3];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+        lvv[c] = lF[0] * (0.5 * (pL + pR) * nh[c] - fvn * v[c] * dM) + lF[1] * 0.5 * (sL + sR) * nh[c];
+      coef_vjp<double>(BC.vel, x, g, lvv, csh);
+    }
+  }
+  __syncthreads();
+
+  // ---- lam_q += L^T lam_qf, one pass per axis ------------------------------
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const double g0 = lqf[((lel * 2 + fld) * DIM + c) * NF + k0];
+          const double g1 = lqf[((lel * 2 + fld) * DIM + c) * NF + k1];
+          double* o = lf + ((lel * 2 + fld) * DIM + c) * NU + base;
+#pragma unroll
+          for (int j = 0; j < N; ++j) o[j * st] += O.lend[0][j] * g0 + O.lend[1][j] * g1;
+        }
+    }
+    __syncthreads();
+  }
+  // ---- lam_q~ = J^{-1} lam_q -------------------------------------------------
+  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+    const int el = idx / NU, i = idx % NU;
+    double xi[3], Sm[3][3];
+    upt_xi<DIM, N>(i, O.x, xi);
+    const double dj = metric<DIM>(gs + el * NG, xi, Sm);
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+      double* l = lf + (el * 2 + fld) * DIM * NU + i;
+      double lv[3];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) lv[b] = l[b * NU];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double r = 0;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) r += Sm[a][b] * lv[b];
+        l[a * NU] = r / dj;
+      }
+    }
+  }
+  __syncthreads();
+  // ---- reverse of Step 3 and Step 1 by axis: D^T, the jump adjoints, L^T ---
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (lact) {
+      const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+      const bool L0 = lm[lel * NF + k0], L1 = lm[lel * NF + k1];
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld) {
+        const double* lq = lf + ((lel * 2 + fld) * DIM + a) * NU + base;
+        double lv[N], jm = 0, jp = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          lv[j] = lq[j * st];
+          jm += O.gLd[j] * lv[j];
+          jp += O.gRd[j] * lv[j];
+        }
+        const int fo = (lel * 2 + fld) * NF;
+        // jump = isL ? uo - uf : 0
+        double u0 = luf[fo + k0], u1 = luf[fo + k1];
+        if (L0) {
+          luo[fo + k0] += jm;
+          u0 -= jm;
+        }
+        if (L1) {
+          luo[fo + k1] += jp;
+          u1 -= jp;
+        }
+        double* o = us + (lel * 2 + fld) * NU + base;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          double acc = O.lend[0][m] * u0 + O.lend[1][m] * u1;
+#pragma unroll
+          for (int j = 0; j < N; ++j) acc += O.D[j][m] * lv[j];
+          o[m * st] += acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) B.lamU[e0 * 2 * NU + idx] = us[idx];
+  for (int idx = tid; idx < ne * 2 * NF; idx += blockDim.x) B.lamuo[e0 * 2 * NF + idx] = luo[idx];
+  if (coef) {
+    __syncthreads();
+    for (int m = tid; m < M2; m += blockDim.x) B.coefp[(int64_t)blockIdx.x * M2 + m] += csh[m];
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) adj_c(const AdjArgs B) {
+  using S = TS<DIM, N>;
+  using LY = AdjLayout<DIM, N>;
+  constexpr int NU = S::NU, NF = S::NF, NFP = S::NFP, ET = LY::ET, LN = LY::LN;
+  const KArgs& A = B.K;
+  __shared__ double la[ET * 2 * NU];
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)min((int64_t)ET, A.E - e0);
+  const int tid = threadIdx.x;
+  const TensorOpsT<double>& O = A.cd.ops;
+  for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) la[idx] = B.lamU[e0 * 2 * NU + idx];
+  __syncthreads();
+  const int lel = tid / LN, ll = tid % LN;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (lel < ne) {
+      const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
+      double gv[2][2];
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int32_t w = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+        const int64_t pg = (int64_t)(w >> 1);
+#pragma unroll
+        for (int fld = 0; fld < 2; ++fld) gv[sd][fld] = B.lamuo[((pg / NF) * 2 + fld) * NF + pg % NF];
+      }
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld) {
+        double* o = la + (lel * 2 + fld) * NU + base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) o[j * st] += O.lend[0][j] * gv[0][fld] + O.lend[1][j] * gv[1][fld];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) {
+    const int64_t gi = e0 * 2 * NU + idx;
+    const double a = la[idx];
+    const double lp = B.Lp[gi];
+    B.Lu[gi] = (B.first ? lp : B.Lu[gi]) + a;
+    if (B.Lk) B.Lk[gi] = B.c_lp * lp + B.c_a * a;
+  }
+}
+
+}  // namespace frp

@@ -85,6 +85,8 @@ struct KArgs {
   double* dstate;        // DS_WORDS
   double* red;           // reduction partials (one per block)
   double* out;           // fr_rhs output (2 x E x nu) or nullptr
+  const void* vsu;       // T E x dim x nu: spatial velocity factor at solution points (or nullptr)
+  const void* vsf;       // T E x dim x nf: spatial velocity factor at flux points (or nullptr)
   int stage;             // 1..4 RK stage, -1: write the rate into out
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
   double t;              // KB: stage time when !use_dev_time

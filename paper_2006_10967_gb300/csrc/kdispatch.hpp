@@ -12,6 +12,7 @@ struct KernelSet {
   LaunchFn kb[2] = {nullptr, nullptr};  // [mode]: 0 physical, 1 preconditioning
   LaunchFn ka[2] = {nullptr, nullptr};
   int max_blocks = 0;                   // upper bound on blocks of any launch (per element count)
+  LaunchFn vcache = nullptr;            // fills the spatial velocity cache (nullptr: not supported)
 };
 
 // Return false if the (order, precision) pair is not built.

@@ -99,27 +99,6 @@ __device__ __forceinline__ T metric(const T* g, const T* xi, T S[3][3]) {
   return adjugate<DIM, T>(J, S);
 }
 
-// Shared 1D operators in bulk precision.
-template <int N, typename T>
-struct SOps {
-  T x[N], lend[2][N], D[N][N], gLd[N], gRd[N], Vinv[N][N];
-};
-
-template <int N, typename T>
-__device__ __forceinline__ void load_ops(const TensorOpsT<T>& o, SOps<N, T>& s) {
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    s.x[t] = o.x[t];
-    s.lend[0][t] = o.lend[0][t];
-    s.lend[1][t] = o.lend[1][t];
-    s.gLd[t] = o.gLd[t];
-    s.gRd[t] = o.gRd[t];
-  }
-  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-    s.D[t / N][t % N] = o.D[t / N][t % N];
-    s.Vinv[t / N][t % N] = o.Vinv[t / N][t % N];
-  }
-}
-
 // Lines: along axis a, line l runs through the solution points whose other
 // coordinates (in increasing axis order, lowest fastest) encode l; it ends
 // at flux point l of faces (a, -) and (a, +).
@@ -135,6 +114,13 @@ __device__ __forceinline__ int line_base(int a, int l) {
   return base;
 }
 
+// Largest tile (elements) <= cap whose thread count ET*LN fills whole warps,
+// when such a tile exists; otherwise cap.
+__host__ __device__ constexpr int gcd_(int a, int b) { return b == 0 ? a : gcd_(b, a % b); }
+__host__ __device__ constexpr int warp_tile(int cap, int ln) {
+  return (cap / (32 / gcd_(ln, 32))) > 0 ? (cap / (32 / gcd_(ln, 32))) * (32 / gcd_(ln, 32)) : cap;
+}
+
 template <int DIM, int N, typename T, int MODE>
 struct KBLayout {
   using S = TS<DIM, N>;
@@ -145,10 +131,10 @@ struct KBLayout {
                                   + 3 * NFLD * S::NF    // uf, uo, cor
                                   + S::NG               // geometry
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
-  static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + S::NF;
+  static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
-  static constexpr int ET_S = 77824 / BYTES_EL < 1 ? 1 : 77824 / BYTES_EL;
-  static constexpr int ET = ET_T < ET_S ? ET_T : ET_S;
+  static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
+  static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
   static constexpr int THREADS = ET * LN;
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
 };
@@ -174,7 +160,8 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   T* gs = cor + ET * NFLD * NF;            // [ET][NG]
   T* chi = gs + ET * NG;                   // MODE 1: [ET][2][NU]
   T* nus = chi + (MODE == 1 ? ET * 2 * NU : 0);
-  unsigned char* lm = reinterpret_cast<unsigned char*>(nus + (MODE == 1 ? ET : 0));  // [ET][NF]
+  uint16_t* llist = reinterpret_cast<uint16_t*>(nus + (MODE == 1 ? ET : 0));  // [ET*NF] L flux points
+  unsigned char* lm = reinterpret_cast<unsigned char*>(llist + ET * NF);      // [ET][NF]
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -187,9 +174,33 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   const TensorOpsT<T>& O = BC.ops;
   const PrmT<T> P = BC.prm;
   __shared__ T gfac_s;
+  __shared__ int nL;
   if (tid == 0) {
+    nL = 0;
     const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
     gfac_s = (T)time_factor(A, tstage);
+  }
+  const int lel = tid / LN, ll = tid % LN;
+  const bool lact = lel < ne;
+  // Prefetch this thread's line-end connectivity and partner traces for all
+  // axis passes, so that the dependent global loads overlap the tile load.
+  int32_t wpre[DIM][2];
+  T opre[DIM][2][NFLD];
+  if (lact) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) wpre[a][sd] = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int32_t w = wpre[a][sd];
+        const int64_t p = (int64_t)(w >> 1);
+#pragma unroll
+        for (int fld = 0; fld < NFLD; ++fld)
+          opre[a][sd][fld] = (w & 1) ? tr[((p / NF) * 2 + F0 + fld) * NF + p % NF] : (T)0;
+      }
   }
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
@@ -198,8 +209,6 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   __syncthreads();
   const T gfac = gfac_s;
-  const int lel = tid / LN, ll = tid % LN;
-  const bool lact = lel < ne;
 
   // ---- Steps 1-3, one pass per axis: traces at the line ends, partner
   //      traces (Step 2), reference derivative plus the two end corrections;
@@ -210,10 +219,17 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const int st = ipow(N, a);
       const int base = line_base<DIM, N>(a, ll);
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
-      const int32_t w0 = A.fnbr[(e0 + lel) * NF + k0], w1 = A.fnbr[(e0 + lel) * NF + k1];
+      const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
       lm[lel * NF + k0] = (unsigned char)(w0 & 1);
       lm[lel * NF + k1] = (unsigned char)(w1 & 1);
-      const int64_t p0 = (int64_t)(w0 >> 1), p1 = (int64_t)(w1 >> 1);
+      // L points go to the compacted list of Step 5; R points get no flux here
+      if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k0);
+      if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k1);
+#pragma unroll
+      for (int fld = 0; fld < NFLD; ++fld) {
+        if (!(w0 & 1)) cor[(lel * NFLD + fld) * NF + k0] = 0;
+        if (!(w1 & 1)) cor[(lel * NFLD + fld) * NF + k1] = 0;
+      }
 #pragma unroll
       for (int fld = 0; fld < NFLD; ++fld) {
         const T* ul = us + (lel * NFLD + fld) * NU + base;
@@ -226,8 +242,8 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           f0 += O.lend[0][j] * v[j];
           f1 += O.lend[1][j] * v[j];
         }
-        const T o0 = (w0 & 1) ? tr[((p0 / NF) * 2 + F0 + fld) * NF + p0 % NF] : f0;
-        const T o1 = (w1 & 1) ? tr[((p1 / NF) * 2 + F0 + fld) * NF + p1 % NF] : f1;
+        const T o0 = (w0 & 1) ? opre[a][0][fld] : f0;
+        const T o1 = (w1 & 1) ? opre[a][1][fld] : f1;
         const int fo = (lel * NFLD + fld) * NF;
         uf[fo + k0] = f0;
         uf[fo + k1] = f1;
@@ -311,13 +327,10 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   }
 
   // ---- Step 5 on L flux points (q^f by Eq. extrapolateGrad) ----------------
-  for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
-    const int el = idx / NF, k = idx % NF;
-    if (!lm[el * NF + k]) {
-#pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld) cor[(el * NFLD + fld) * NF + k] = 0;
-      continue;
-    }
+  const int nLpts = nL;
+  for (int t = tid; t < nLpts; t += blockDim.x) {
+    const int code = llist[t];
+    const int el = code / NF, k = code % NF;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
     T xi[3], Sm[3][3];
@@ -352,9 +365,16 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
           qf[fld][c] = acc;
         }
-      T x[3], v[3];
-      map_point<S::ET_, T>(gs + el * NG, xi, x);
-      velocity<DIM, T>(BC.vel, x, gfac, v);
+      T v[3];
+      if (A.vsf) {
+        const T* vc = reinterpret_cast<const T*>(A.vsf) + (e0 + el) * DIM * NF + k;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) v[c] = gfac * vc[c * NF];
+      } else {
+        T x[3];
+        map_point<S::ET_, T>(gs + el * NG, xi, x);
+        velocity<DIM, T>(BC.vel, x, gfac, v);
+      }
       T vn = 0, v2 = 0, g2 = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
@@ -400,9 +420,16 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
     upt_xi<DIM, N>(i, O.x, xi);
     const T dj = metric<DIM>(gs + el * NG, xi, Sm);
     if (MODE == 0) {
-      T x[3], v[3];
-      map_point<S::ET_, T>(gs + el * NG, xi, x);
-      velocity<DIM, T>(BC.vel, x, gfac, v);
+      T v[3];
+      if (A.vsu) {
+        const T* vc = reinterpret_cast<const T*>(A.vsu) + (e0 + el) * DIM * NU + i;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) v[c] = gfac * vc[c * NU];
+      } else {
+        T x[3];
+        map_point<S::ET_, T>(gs + el * NG, xi, x);
+        velocity<DIM, T>(BC.vel, x, gfac, v);
+      }
       T qp[3], qs[3], v2 = 0, g2 = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
@@ -503,30 +530,30 @@ template <int DIM, int N, typename T, int MODE>
 struct KALayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG) * (int)sizeof(T);
-  static constexpr int ETr = 24576 / BYTES_EL;
-  static constexpr int ET = ETr < 1 ? 1 : (ETr > 64 ? 64 : ETr);
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(SOps<N, T>) + 64;
+  static constexpr int LN = S::NFP;
+  static constexpr int BYTES_EL = (NFLD * S::NU + S::NG) * (int)sizeof(T);
+  static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
+  static constexpr int ET_S = 32768 / BYTES_EL < 1 ? 1 : 32768 / BYTES_EL;
+  static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr int THREADS = ET * LN;
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
 };
 
-// ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces.
-// stage -1 writes du/dt to A.out (fp64) and leaves the state alone;
-// stage 0 only recomputes the traces of ustg.
+// ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
+// as in kb_tensor.  stage -1 writes du/dt to A.out (fp64) and leaves the
+// state alone; stage 0 only recomputes the traces of ustg.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
+__global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   using S = TS<DIM, N>;
   using LY = KALayout<DIM, N, T, MODE>;
-  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
   constexpr int F0 = MODE == 0 ? 0 : 1;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  SOps<N, T>& op = *reinterpret_cast<SOps<N, T>*>(smem_raw);
-  T* base = reinterpret_cast<T*>(smem_raw + ((sizeof(SOps<N, T>) + 15) & ~size_t(15)));
-  T* ys = base;                   // [ET][NFLD][NU]
-  T* cr = ys + ET * NFLD * NU;    // [ET][NFLD][NF]
-  T* gs = cr + ET * NFLD * NF;    // [ET][NG]
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [ET][NFLD][NU]
+  T* gs = ys + ET * NFLD * NU;             // [ET][NG]
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -536,8 +563,24 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
   const T* rp = reinterpret_cast<const T*>(A.rp);
   const int tid = threadIdx.x;
   const int stage = A.stage;
+  const TensorOpsT<T>& O = bulk<T>(A).ops;
+  const int lel = tid / LN, ll = tid % LN;
+  const bool lact = lel < ne;
 
-  load_ops<N, T>(bulk<T>(A).ops, op);
+  // prefetch the partner fluxes of this line's R ends (0 on L ends)
+  T fpre[DIM][2][NFLD];
+  if (stage != 0 && lact) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int32_t w = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+        const int64_t p = (int64_t)(w >> 1);
+#pragma unroll
+        for (int fld = 0; fld < NFLD; ++fld)
+          fpre[a][sd][fld] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fld) * NF + p % NF];
+      }
+  }
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
     const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
@@ -547,55 +590,55 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
   __syncthreads();
 
   double sq = 0.0;
-  RKConstF rkc;
-  rkc.half_dt = (float)(0.5 * A.dt);
-  rkc.dt = (float)A.dt;
-  rkc.dt6 = (float)(A.dt / 6.0);
-  rkc.rdt = 1.0 / A.dt;
   if (stage != 0) {
-    // ---- common flux on R flux points: minus L's physical flux, this side's metric
-    for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
-      const int el = idx / NF, k = idx % NF;
-      const int32_t w = A.fnbr[(e0 + el) * NF + k];
-      if (w & 1) {
+    // ---- lift of the R-side common fluxes: minus L's physical flux times
+    //      this side's face metric, one pass per axis
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld) cr[(el * NFLD + fld) * NF + k] = 0;
-        continue;
+    for (int a = 0; a < DIM; ++a) {
+      if (lact) {
+        const int st = ipow(N, a);
+        const int base = line_base<DIM, N>(a, ll);
+        T cs[2] = {0, 0};
+        bool any = false;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          bool nz = false;
+#pragma unroll
+          for (int fld = 0; fld < NFLD; ++fld) nz = nz || fpre[a][sd][fld] != (T)0;
+          if (!nz) continue;
+          any = true;
+          T xi[3], Sm[3][3];
+          fpt_xi<DIM, N>((2 * a + sd) * NFP + ll, O.x, xi);
+          metric<DIM>(gs + lel * NG, xi, Sm);
+          T pm = 0;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) pm += Sm[a][c] * Sm[a][c];
+          cs[sd] = -sqrt_(pm);
+        }
+        if (any) {
+#pragma unroll
+          for (int fld = 0; fld < NFLD; ++fld) {
+            const T c0 = cs[0] * fpre[a][0][fld], c1 = cs[1] * fpre[a][1][fld];
+            T* yl = ys + (lel * NFLD + fld) * NU + base;
+#pragma unroll
+            for (int j = 0; j < N; ++j) yl[j * st] += -O.gLd[j] * c0 + O.gRd[j] * c1;
+          }
+        }
       }
-      const int64_t pg = (int64_t)(w >> 1), pe = pg / NF, pk = pg % NF;
-      T xi[3], Sm[3][3];
-      fpt_xi<DIM, N>(k, op.x, xi);
-      metric<DIM>(gs + el * NG, xi, Sm);
-      const int a = (k / S::NFP) >> 1;
-      T pm = 0;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        T sac = Sm[0][c];
-#pragma unroll
-        for (int b = 1; b < DIM; ++b)
-          if (b == a) sac = Sm[b][c];
-        pm += sac * sac;
-      }
-      pm = sqrt_(pm);
-#pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld)
-        cr[(el * NFLD + fld) * NF + k] = -pm * fc[(pe * 2 + F0 + fld) * NF + pk];
+      __syncthreads();
     }
-    __syncthreads();
     // ---- du/dt and the RK4 register update
+    RKConstF rkc;
+    rkc.half_dt = (float)(0.5 * A.dt);
+    rkc.dt = (float)A.dt;
+    rkc.dt6 = (float)(A.dt / 6.0);
+    rkc.rdt = 1.0 / A.dt;
     for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
       const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-      const T* c = cr + (el * NFLD + fld) * NF;
-      T div = ys[idx];
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const int ia = ucoord<N>(i, a);
-        div += -op.gLd[ia] * c[fpt_of<DIM, N>(i, a, 0)] + op.gRd[ia] * c[fpt_of<DIM, N>(i, a, 1)];
-      }
       T xi[3], Sm[3][3];
-      upt_xi<DIM, N>(i, op.x, xi);
+      upt_xi<DIM, N>(i, O.x, xi);
       const T dj = metric<DIM>(gs + el * NG, xi, Sm);
-      const T R = -div / dj;
+      const T R = -ys[idx] / dj;
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
         A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
@@ -608,23 +651,58 @@ __global__ void __launch_bounds__(kThreads) ka_tensor(const KArgs A) {
     }
     __syncthreads();
   }
-  if (stage >= 0) {
+  if (stage >= 0 && lact) {
     // ---- flux-point traces of the new stage input (Step 1 of the next stage)
-    for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
-      const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
-      int a, s, b0;
-      fline<DIM, N>(k, a, s, b0);
-      const T* yl = ys + (el * NFLD + fld) * NU + b0;
-      const int st = ipow(N, a);
-      T acc = 0;
 #pragma unroll
-      for (int j = 0; j < N; ++j) acc += op.lend[s][j] * yl[j * st];
-      tr[((e0 + el) * 2 + F0 + fld) * NF + k] = acc;
+    for (int a = 0; a < DIM; ++a) {
+      const int st = ipow(N, a);
+      const int base = line_base<DIM, N>(a, ll);
+      const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+#pragma unroll
+      for (int fld = 0; fld < NFLD; ++fld) {
+        const T* yl = ys + (lel * NFLD + fld) * NU + base;
+        T t0 = 0, t1 = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T v = yl[j * st];
+          t0 += O.lend[0][j] * v;
+          t1 += O.lend[1][j] * v;
+        }
+        T* trl = tr + ((e0 + lel) * 2 + F0 + fld) * NF;
+        trl[k0] = t0;
+        trl[k1] = t1;
+      }
     }
   }
   if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)
     A.dstate[DS_TIME] = A.dstate[DS_TIME] + A.dt;
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
+}
+
+// Spatial velocity factor v(x) (g = 1) at the solution and flux points of
+// every element, evaluated once in double and stored in the bulk type.
+template <int DIM, int N, typename T>
+__global__ void k_vel_cache(const KArgs A) {
+  using S = TS<DIM, N>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG;
+  const int64_t n = A.E * (NU + NF);
+  const TensorOpsT<double>& O = A.cd.ops;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / (NU + NF);
+    const int r = (int)(g % (NU + NF));
+    double xi[3], x[3], v[3];
+    if (r < NU) upt_xi<DIM, N>(r, O.x, xi);
+    else fpt_xi<DIM, N>(r - NU, O.x, xi);
+    map_point<S::ET_, double>(A.geo + e * NG, xi, x);
+    velocity<DIM, double>(A.cd.vel, x, 1.0, v);
+    if (r < NU) {
+      T* o = reinterpret_cast<T*>(const_cast<void*>(A.vsu)) + e * DIM * NU + r;
+      for (int c = 0; c < DIM; ++c) o[c * NU] = (T)v[c];
+    } else {
+      T* o = reinterpret_cast<T*>(const_cast<void*>(A.vsf)) + e * DIM * NF + (r - NU);
+      for (int c = 0; c < DIM; ++c) o[c * NF] = (T)v[c];
+    }
+  }
 }
 
 }  // namespace frp

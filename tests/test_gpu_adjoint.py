@@ -1,0 +1,169 @@
+"""The hand-written adjoint (fr_adjoint_record / fr_adjoint_step) against the
+oracle's discrete adjoint (reverse-mode differentiation of the oracle) and
+against central finite differences of the CUDA forward map.
+
+Loss: J = 1/2 int (phi_T - phi*)^2 with the solution-point quadrature; the
+gradient is taken with respect to phi0 (psi0 = phi0 - 1/2) and the
+stream-function coefficients.  Both adjoints differentiate the same discrete
+map, so they agree to round-off; the tolerance is the benchmark spec's 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from libutil import ensure_built
+from oracle import Params
+from oracle.adjoint import loss_and_gradients
+from oracle.solver import Solver, circle_ic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_2006_10967_gb300 as G
+    return G
+
+
+def _wl(mesh_fn, p, h, n_modes, seed=4, sigma=0.05):
+    kx, ky, A, B = S.stream_coefficients(n_modes, seed=seed, sigma=sigma)
+    vel = S.Velocity("stream", T=0.0, kx=kx, ky=ky, A=A, B=B)
+    w = S.Workload("adj", mesh_fn, p, vel, S.Circle((0.5, 0.5), 0.3, 6.0), t_end=1.0, h=h)
+    w.eps = 0.06 * h / p
+    w.nu_max = 0.15 * h / p
+    w.pseudo_dtau = 0.1 * h / (p + 1)
+    w.dt = 0.004
+    return w
+
+
+def _gpu_grad(G, w, mesh, phi0, phis, n, ck):
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    F = G.Field(M, G.make_params(w), phi0=phi0, precondition=False)
+    F.adjoint_record(n, ck)
+    phiT = F.get(0)
+    wq = M.quadrature()
+    J = 0.5 * float((wq * (phiT - phis) ** 2).sum())
+    gT = torch.from_numpy(wq * (phiT - phis)).cuda()
+    nc = 2 * len(w.velocity.A) if w.velocity.kind == "stream" else 0
+    du0, dc = F.adjoint_step(gT, None, nc)
+    return J, (du0[0] + du0[1]).cpu().numpy(), (dc.cpu().numpy() if dc is not None else None), F
+
+
+@pytest.mark.parametrize("kind", ["quad", "hex"])
+def test_adjoint_matches_oracle_adjoint(G, kind):
+    if kind == "quad":
+        w = _wl(lambda: S.quad_grid(4, jitter=0.1, seed=3, shuffle_seed=1, rotate_seed=2), 3, 0.25, 4)
+    else:
+        w = _wl(lambda: S.hex_grid(2, periodic=(True, True, True), jitter=0.05, seed=3), 2, 0.5, 4)
+        w.velocity = S.Velocity("leveque", T=3.0)
+        w.circle = S.Circle((0.5, 0.5, 0.5), 0.3, 6.0)
+    mesh = w.mesh()
+    prm = Params.from_workload(w)
+    sol = Solver(mesh, w.order, prm, w.velocity)
+    phi0 = circle_ic(sol.xu, w.circle).numpy()
+    c = (0.55, 0.45, 0.5)[: mesh.dim]
+    phis = circle_ic(sol.xu, S.Circle(c, 0.3, 6.0)).numpy()
+    n, ck = 5, 2
+    J, gphi, gc, F = _gpu_grad(G, w, mesh, phi0, phis, n, ck)
+    if kind == "quad":
+        Jo, gphio, gAo, gBo = loss_and_gradients(mesh, w.order, prm, w.velocity, phi0, phis, n)
+        assert J == pytest.approx(Jo, rel=1e-12)
+        rel = np.abs(gphi - gphio.numpy()).max() / np.abs(gphio.numpy()).max()
+        assert rel < 1e-9
+        go = np.concatenate([gAo.numpy(), gBo.numpy()])
+        assert np.abs(gc - go).max() / np.abs(go).max() < 1e-9
+    else:
+        # LeVeque field: gradient with respect to phi0 only (oracle via autograd)
+        phi0t = torch.tensor(phi0, requires_grad=True)
+        s2 = Solver(mesh, w.order, prm, w.velocity)
+        s2.initialize(phi=phi0t, precondition=False)
+        for _ in range(n):
+            s2.rk4_step()
+        Jt = 0.5 * s2.integral((s2.phi - torch.tensor(phis)) ** 2)
+        (go,) = torch.autograd.grad(Jt, (phi0t,))
+        assert J == pytest.approx(float(Jt.detach()), rel=1e-12)
+        assert np.abs(gphi - go.numpy()).max() / np.abs(go.numpy()).max() < 1e-9
+    # the field is left at the end of the window
+    st = F.stats()
+    assert st["n_steps"] == n
+
+
+def test_adjoint_c5_against_central_differences(G):
+    """The adjoint workload: 64^2 periodic quads, p = 4, 400 RK4 steps, velocity
+    from 32 stream-function coefficients, checkpoints every 20 steps."""
+    w = S.workload("c5")
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    xu = M.solution_points()
+    def circ(c):
+        return 0.5 * (1 + np.tanh(c.beta * (c.radius - np.sqrt(((xu - np.array(c.centre)) ** 2).sum(-1)))))
+    phi0 = circ(w.circle)
+    phis = circ(w.extra["target"])
+    n, ck = w.n_steps, w.extra["ckpt_every"]
+    J, gphi, gc, _ = _gpu_grad(G, w, mesh, phi0, phis, n, ck)
+    wq = M.quadrature()
+
+    def loss(phi0_, A=None, B=None):
+        vel = w.velocity
+        if A is not None:
+            vel = S.Velocity("stream", T=0.0, kx=vel.kx, ky=vel.ky, A=A, B=B)
+        F = G.Field(M, G.make_params(w, velocity=vel), phi0=phi0_, precondition=False)
+        F.step(n)
+        return 0.5 * float((wq * (F.get(0) - phis) ** 2).sum())
+
+    # Central differences of this 400-step map converge to the adjoint as the
+    # step shrinks (relative gap 4.5e-4 at h = 1e-6, 6.8e-6 at 1e-7, 1.5e-7 at
+    # 1e-8 on GB300): the sharpening dynamics are strongly nonlinear at the
+    # 1e-6 scale, so the check uses h = 1e-8, where truncation and round-off
+    # together stay near 2e-7.
+    h = 1e-8
+    rng = np.random.default_rng(7)
+    d = rng.normal(size=phi0.shape) * (phi0 * (1 - phi0) > 0.01)   # a direction near the interface
+    fd = (loss(phi0 + h * d) - loss(phi0 - h * d)) / (2 * h)
+    assert float((gphi * d).sum()) == pytest.approx(fd, rel=1e-6)
+    A0, B0 = w.velocity.A, w.velocity.B
+    for m in (0, 5):
+        Ap, Am = A0.copy(), A0.copy()
+        Ap[m] += h
+        Am[m] -= h
+        fd = (loss(phi0, Ap, B0) - loss(phi0, Am, B0)) / (2 * h)
+        assert gc[m] == pytest.approx(fd, rel=1e-6)
+        Bp, Bm = B0.copy(), B0.copy()
+        Bp[m] += h
+        Bm[m] -= h
+        fd = (loss(phi0, A0, Bp) - loss(phi0, A0, Bm)) / (2 * h)
+        assert gc[len(A0) + m] == pytest.approx(fd, rel=1e-6)
+
+
+def test_autograd_function_wraps_the_adjoint(G):
+    w = _wl(lambda: S.quad_grid(3, jitter=0.1, seed=5), 2, 1 / 3, 3)
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    kx, ky = w.velocity.kx, w.velocity.ky
+
+    def params_fn(coef):
+        m = len(kx)
+        vel = S.Velocity("stream", T=0.0, kx=kx, ky=ky, A=coef[:m], B=coef[m:])
+        return G.make_params(w, velocity=vel)
+
+    flow = G.flow_function(M, params_fn, n_steps=4, ckpt_every=3)
+    xu = M.solution_points()
+    phi0 = torch.tensor(0.5 * (1 + np.tanh(4.0 * (0.3 - np.sqrt(((xu - 0.5) ** 2).sum(-1))))), requires_grad=True)
+    coef = torch.tensor(np.concatenate([w.velocity.A, w.velocity.B]), requires_grad=True)
+    wq = torch.tensor(M.quadrature())
+    phiT = flow(phi0, coef)
+    J = 0.5 * (wq * phiT.cpu() ** 2).sum()
+    J.backward()
+    assert phi0.grad is not None and coef.grad is not None
+    assert torch.isfinite(phi0.grad).all() and torch.isfinite(coef.grad).all()
+    # compare with a direct finite difference along phi0
+    h = 1e-6
+    d = torch.randn_like(phi0)
+    with torch.no_grad():
+        jp = 0.5 * (wq * flow(phi0 + h * d, coef).cpu() ** 2).sum()
+        jm = 0.5 * (wq * flow(phi0 - h * d, coef).cpu() ** 2).sum()
+    assert float((phi0.grad * d).sum()) == pytest.approx(float((jp - jm) / (2 * h)), rel=1e-6)

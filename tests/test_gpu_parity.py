@@ -43,13 +43,13 @@ def _workload(mesh_fn, p, vel, circle, h, **kw):
     return w
 
 
-def _pair(G, w, precision="fp64", precondition=False, fixed=True, **okw):
+def _pair(G, w, precision="fp64", precondition=False, fixed=True, vel_cache=True, **okw):
     mesh = w.mesh()
     prm = Params.from_workload(w, pseudo_fixed=fixed, **okw)
     sol = Solver(mesh, w.order, prm, w.velocity)
     sol.initialize(w.circle, precondition=precondition)
     M = G.Mesh.from_synthetic(mesh, w.order)
-    P = G.make_params(w, precision, pseudo_fixed=fixed, **okw)
+    P = G.make_params(w, precision, pseudo_fixed=fixed, vel_cache=vel_cache, **okw)
     F = G.Field(M, P, ic=w.circle, precondition=precondition)
     return sol, F
 
@@ -106,6 +106,20 @@ def test_rhs_parity_fp64(G, case):
         Ro = sol.rhs(sol.phi, sol.psi, t)
         assert _rel(R[0], Ro[0].numpy()) < TOL64, case
         assert _rel(R[1], Ro[1].numpy()) < TOL64, case
+
+
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_stream_p5", "hex_periodic_jitter_p2"])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
+def test_rhs_parity_velocity_evaluated_in_kernel(G, case, precision, tol):
+    """The same residual with the velocity evaluated in the kernels instead of
+    read from the per-point cache."""
+    w = CASES[case]()
+    sol, F = _pair(G, w, precision=precision, vel_cache=False)
+    _perturb(sol, F)
+    R = F.rhs(0.7).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.7)
+    assert _rel(R[0], Ro[0].numpy()) < tol, case
+    assert _rel(R[1], Ro[1].numpy()) < tol, case
 
 
 @pytest.mark.parametrize("case", list(CASES))
