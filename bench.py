@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--mesh-n", type=int, default=128, help="elements per side (128 is the benchmark workload)")
     ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
+    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3"],
+                    help="c2q: 128^2 jittered quads p=4 (the benchmark); c2t: ~30k Delaunay triangles p=3; "
+                         "c3: 64^3 hexes p=3 (LeVeque)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     return ap.parse_args()
 
 
@@ -247,6 +251,46 @@ def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=Fal
     return out, F
 
 
+def adjoint_ratio(G, S):
+    """Wall time of the hand-written adjoint (checkpointed recompute + reverse
+    sweep) over the forward march on the adjoint workload: 64^2 periodic quads,
+    p = 4, 400 RK4 steps, 32 stream-function coefficients, checkpoints every 20."""
+    import numpy as np
+    import torch
+    w = S.workload("c5")
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    xu = M.solution_points()
+    circ = lambda c: 0.5 * (1 + np.tanh(c.beta * (c.radius - np.sqrt(((xu - np.array(c.centre)) ** 2).sum(-1)))))
+    phi0 = circ(w.circle)
+    phis = torch.from_numpy(circ(w.extra["target"])).cuda()
+    wq = torch.from_numpy(M.quadrature()).cuda()
+    n, ck = w.n_steps, w.extra["ckpt_every"]
+    res = {}
+    F = G.Field(M, G.make_params(w), phi0=phi0, precondition=False)
+    F.step(n)                      # warm-up (kernel attributes, caches)
+    torch.cuda.synchronize()
+    for rep in range(2):
+        F = G.Field(M, G.make_params(w), phi0=phi0, precondition=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.step(n)
+        F.sync()
+        tf = time.perf_counter() - t0
+        F = G.Field(M, G.make_params(w), phi0=phi0, precondition=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.adjoint_record(n, ck)
+        phiT = torch.empty_like(wq)
+        F.get_device(0, phiT)
+        F.adjoint_step(wq * (phiT - phis), None, 32)
+        ta = time.perf_counter() - t0
+        res = {"forward_s": tf, "forward_plus_adjoint_s": ta, "adjoint_over_forward": (ta - tf) / tf,
+               "workload": "stream-function quad64 p4 fp64, 400 RK4 steps, checkpoints every 20",
+               "note": "adjoint = checkpointed forward recompute + reverse sweep; ratio excludes the recorded forward"}
+    return res
+
+
 def cpu_baseline(S, w, mesh, nsteps):
     import torch
     from oracle import Params, Solver
@@ -292,10 +336,19 @@ def main():
     args = parse()
     rank, world = dist_init()
     import synthetic as S
-    w = S.workload("c2q", n=args.mesh_n)
+    if args.workload == "c2q":
+        w = S.workload("c2q", n=args.mesh_n)
+        wname = f"rider_kothe_quad{args.mesh_n}_jitter_p4"
+    elif args.workload == "c2t":
+        w = S.workload("c2t")
+        wname = "rider_kothe_tri_delaunay_p3"
+    else:
+        w = S.workload("c3")
+        wname = "leveque_hex64_p3"
     mesh = w.mesh()
-    workload_cfg = {"workload": f"rider_kothe_quad{args.mesh_n}_jitter_p4", "elements": mesh.n_elems, "order": w.order,
-                    "solution_points": mesh.n_elems * (w.order + 1) ** 2, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
+    nu_el = {"quad": (w.order + 1) ** 2, "tri": (w.order + 1) * (w.order + 2) // 2, "hex": (w.order + 1) ** 3}[mesh.etype]
+    workload_cfg = {"workload": wname, "elements": mesh.n_elems, "order": w.order,
+                    "solution_points": mesh.n_elems * nu_el, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
                     "stages_per_rk_step": 4, "precondition_every": w.n_precond, "pseudo_kmax": w.pseudo_kmax,
                     "l2": "flushed before each timed step (512 MiB write); working set L2-resident within a step",
                     "parallelism": f"replicas x{world}"}
@@ -352,11 +405,11 @@ def main():
         peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12     # FP64: 2 DFMA/clk/SM
         peak_note = "FP64: 152 SM x 2 DFMA x 2 flop x max SM clock"
     ndof = main_out["ndof"]
-    flops_launch = alg_flops_per_dof(2, w.order) * ndof
+    flops_launch = alg_flops_per_dof(mesh.dim, w.order) * ndof
     achieved = flops_launch / (ms / nl * 1e-3) / 1e12 if dom == "kb_phys" else None
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": load_traffic(f"kb_phys_quad_p4_{args.precision}"),
+            "traffic": load_traffic(f"kb_phys_{args.workload}_{args.precision}"),
             "peak_source": peak_note + " (derived, nominal units and clocks)",
             "avg_launch_us": ms / nl * 1e3,
             "share_of_step": ms / sum(v[0] for v in kern.values()),
@@ -380,6 +433,8 @@ def main():
         line["speedup_mixed_over_fp64"] = main_out["value"] / fp64_out["value"]
     if args.accuracy:
         line["accuracy"] = accuracy(G, S, w, mesh)
+    if not args.no_adjoint and world == 1:
+        line["adjoint"] = adjoint_ratio(G, S)
     if rank == 0:
         print(json.dumps(line))
 

@@ -11,8 +11,11 @@ Readings of points the paper leaves open (each is a parameter):
   * LDG beta = +1/2 relative to the L side of each face: the common solution
     is the R trace and the viscous flux is the L side's (Steps 2 and 5).
   * The penalty enters the total common normal flux out of L as
-    +tau (u_L - u_R), the dissipative sign.  psi's advection flux carries
-    tau_psi (default 0: central flux only).
+    +tau (u_L - u_R), the dissipative sign, for both components of
+    u = [phi, psi] (Eq. viscousFlux is written for the vector u); tau_psi is
+    the value used for psi (default tau).  Without it psi's advection is a
+    pure central flux whose weakly growing aliasing mode takes float32
+    round-off to O(1) within one Rider-Kothe period.
   * The common normal flux out of R is minus the one out of L (Eq. commonFlux),
     each side scaling the physical flux by its own face metric |det J J^{-T} n~|.
   * |grad psi| is guarded as max(|grad psi|, delta) in the normal and in the
@@ -41,7 +44,7 @@ class Params:
     gamma: float = 0.09
     eps: float = 0.0
     tau: float = 0.1
-    tau_psi: float = 0.0
+    tau_psi: float = 0.1
     tau_pseudo: float = 0.1
     dt: float = 0.0
     n_precond: int = 1000

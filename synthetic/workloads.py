@@ -55,7 +55,7 @@ class Workload:
     gamma: float = 0.09
     eps: float = 0.0
     tau: float = 0.1           # LDG penalty on phi (not given in the paper)
-    tau_psi: float = 0.0       # penalty on psi advection (inviscid only)
+    tau_psi: float = 0.1       # penalty on psi's jumps (the LDG penalty applies to u = [phi, psi])
     tau_pseudo: float = 0.1    # LDG penalty in the preconditioning equation
     dt: float = 0.0
     n_steps: int = 0
