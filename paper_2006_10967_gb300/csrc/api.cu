@@ -17,7 +17,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf;
+  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t total;
 };
@@ -75,6 +75,13 @@ void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
     const Tensor1D& t = m->t1;
     for (int i = 0; i < t.n; ++i) {
       b.ops.x[i] = (R)t.x[i];
+      b.ops.w[i] = (R)t.w[i];
+      for (int j = 0; j < (m->dim == 2 ? 1 : t.n); ++j) {
+        // face weight of face point i + n j: w_i (2D) or w_i w_j (3D)
+        const double wf = m->dim == 2 ? t.w[i] : t.w[i] * t.w[j];
+        const float hi = (float)wf;
+        b.ops.wff[i + t.n * j] = make_float2(hi, (float)(wf - (double)hi));
+      }
       b.ops.lend[0][i] = (R)t.lend[0][i];
       b.ops.lend[1][i] = (R)t.lend[1][i];
       b.ops.gLd[i] = (R)t.gLd[i];
@@ -115,6 +122,8 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   const bool vc = vel_cache && m.etype != FR_TRI;
   L.vsu = vc ? take(E * m.dim * NU * tb) : 0;
   L.vsf = vc ? take(E * m.dim * NF * tb) : 0;
+  L.tacc = take(E * 2 * sizeof(double));
+  L.wdetf = take(E * NU * 2 * sizeof(float));
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -430,6 +439,9 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   f->xfer = reinterpret_cast<double*>(b + L.xfer);
   A.vsu = L.vsu ? b + L.vsu : nullptr;
   A.vsf = L.vsf ? b + L.vsf : nullptr;
+  // element flux balances of the mixed path's conservation correction (tensor elements)
+  A.tacc = (prm->precision == FR_MIXED && m->etype != FR_TRI) ? reinterpret_cast<double*>(b + L.tacc) : nullptr;
+  A.wdetf = reinterpret_cast<const float2*>(b + L.wdetf);
   A.out = nullptr;
   A.stage = 0;
   A.use_dev_time = 0;
@@ -458,6 +470,13 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   up(L.geo, m->geo.data(), m->geo.size() * sizeof(double));
   up(L.fnbr, m->fnbr.data(), m->fnbr.size() * sizeof(int32_t));
   up(L.wdet, m->wdet.data(), m->wdet.size() * sizeof(double));
+  std::vector<float> wdetf(m->wdet.size() * 2);
+  for (size_t g = 0; g < m->wdet.size(); ++g) {
+    const float hi = (float)m->wdet[g];
+    wdetf[2 * g] = hi;
+    wdetf[2 * g + 1] = (float)(m->wdet[g] - (double)hi);
+  }
+  up(L.wdetf, wdetf.data(), wdetf.size() * sizeof(float));
   std::vector<float> geof(m->geo.begin(), m->geo.end());
   up(L.geof, geof.data(), geof.size() * sizeof(float));
   std::vector<double> trid;

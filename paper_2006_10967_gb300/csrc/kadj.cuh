@@ -9,7 +9,7 @@
 // fields), the three kernels compute a = (dR/dU)^T lam and accumulate
 // (dR/dc)^T lam over the stream-function coefficients c:
 //   adj_a : lam_div = -lam / det J; the adjoints of the lifted flux jumps at
-//           every flux point, scaled by the face metric -> Y (global)
+//           every flux point -> Y (global)
 //   adj_b : forward recomputation of the element (traces, gradient, fluxes)
 //           and the reverse of Steps 6, 4, 5, 3 and 1 on the element; the
 //           adjoint of the common flux out of L gathers Y from the partner;
@@ -100,17 +100,6 @@ __global__ void __launch_bounds__(256) adj_a(const AdjArgs B) {
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     const int st = ipow(N, a), base = line_base<DIM, N>(a, ll);
-    double pm[2];
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      double xi[3], Sm[3][3];
-      fpt_xi<DIM, N>((2 * a + sd) * NFP + ll, O.x, xi);
-      metric<DIM>(gs + lel * NG, xi, Sm);
-      double p2 = 0;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) p2 += Sm[a][c] * Sm[a][c];
-      pm[sd] = sqrt(p2);
-    }
 #pragma unroll
     for (int fld = 0; fld < 2; ++fld) {
       const double* l = ld + (lel * 2 + fld) * NU + base;
@@ -121,8 +110,8 @@ __global__ void __launch_bounds__(256) adj_a(const AdjArgs B) {
         c1 += O.gRd[j] * l[j * st];
       }
       double* Y = B.Y + ((e0 + lel) * 2 + fld) * NF;
-      Y[(2 * a) * NFP + ll] = pm[0] * c0;
-      Y[(2 * a + 1) * NFP + ll] = pm[1] * c1;
+      Y[(2 * a) * NFP + ll] = c0;
+      Y[(2 * a + 1) * NFP + ll] = c1;
     }
   }
 }
@@ -377,13 +366,13 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
       qf0[c] = a0;
       qf1[c] = a1;
     }
-    // lam of the physical common flux out of L: this side's jump adjoints
-    // minus the partner's (the partner's flux is minus this one)
+    // lam of the physical common flux out of L: the transformed flux pm F
+    // enters this side's lift and (negated) the partner's
     double lF[2];
 #pragma unroll
     for (int fld = 0; fld < 2; ++fld) {
       const double y = B.Y[((e0 + el) * 2 + fld) * NF + k];
-      lF[fld] = bnd ? y : y - B.Y[((pg / NF) * 2 + fld) * NF + pg % NF];
+      lF[fld] = pm * (bnd ? y : y - B.Y[((pg / NF) * 2 + fld) * NF + pg % NF]);
     }
     double vn = 0, v2 = 0, g2 = 0;
 #pragma unroll

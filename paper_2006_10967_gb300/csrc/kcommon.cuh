@@ -42,7 +42,8 @@ struct PhysPrm {
 // 1D tensor operators; kernels stage them into shared memory.
 template <typename R>
 struct TensorOpsT {
-  R x[kMaxN], lend[2][kMaxN], D[kMaxN][kMaxN], gLd[kMaxN], gRd[kMaxN], Vinv[kMaxN][kMaxN];
+  R x[kMaxN], w[kMaxN], lend[2][kMaxN], D[kMaxN][kMaxN], gLd[kMaxN], gRd[kMaxN], Vinv[kMaxN][kMaxN];
+  float2 wff[kMaxN * kMaxN];  // face quadrature weights (products of GL weights) as float-float pairs
 };
 typedef TensorOpsT<double> TensorOps;
 
@@ -87,6 +88,8 @@ struct KArgs {
   double* out;           // fr_rhs output (2 x E x nu) or nullptr
   const void* vsu;       // T E x dim x nu: spatial velocity factor at solution points (or nullptr)
   const void* vsf;       // T E x dim x nf: spatial velocity factor at flux points (or nullptr)
+  double* tacc;          // E x 2: RK accumulation of the element flux balances (mixed path) or nullptr
+  const float2* wdetf;   // E x nu: w_i det J_i as float-float pairs (mixed path)
   int stage;             // 1..4 RK stage, -1: write the rate into out
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
   double t;              // KB: stage time when !use_dev_time
@@ -225,6 +228,21 @@ struct RKConstF {
 __device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
   const float bb = s - a;
   return (a - (s - bb)) + (b - bb);
+}
+
+// float-float arithmetic (pairs (hi, lo), |lo| <= ulp(hi)/2)
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float e = two_sum_lo(a.x, b.x, s) + (a.y + b.y);
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+// (pair) x (float), exact product of the high parts by FMA
+__device__ __forceinline__ float2 ff_mul(float2 a, float b) {
+  const float p = a.x * b;
+  const float e = fmaf(a.x, b, -p) + a.y * b;
+  const float hi = p + e;
+  return make_float2(hi, e - (hi - p));
 }
 
 __device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, float R, const RKConstF& c,

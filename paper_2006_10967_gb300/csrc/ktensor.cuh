@@ -392,10 +392,13 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       for (int c = 0; c < DIM; ++c) fvn += nh[c] * (P.eps * qf[0][c] - sharp * qf[1][c]);
       const T Fp = (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
       const T Fs = (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
-      fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
-      fc[((e0 + el) * 2 + 1) * NF + k] = Fs;
-      cor[(el * 2 + 0) * NF + k] = pm * Fp;
-      cor[(el * 2 + 1) * NF + k] = pm * Fs;
+      // the transformed common flux F~ = |pn| F out of L; the R side uses -F~
+      const T Fp_t = pm * Fp, Fs_t = pm * Fs;
+      fc[((e0 + el) * 2 + 0) * NF + k] = Fp_t;
+      fc[((e0 + el) * 2 + 1) * NF + k] = Fs_t;
+      cor[(el * 2 + 0) * NF + k] = Fp_t;
+      cor[(el * 2 + 1) * NF + k] = Fs_t;
+
     } else {
       T gn = 0;
 #pragma unroll
@@ -406,9 +409,9 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
         for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
         gn += nh[c] * acc;
       }
-      const T F = -nus[el] * gn + P.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
+      const T F = pm * (-nus[el] * gn + P.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]));
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
-      cor[el * NF + k] = pm * F;
+      cor[el * NF + k] = F;
     }
   }
   __syncthreads();
@@ -567,18 +570,24 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   const int lel = tid / LN, ll = tid % LN;
   const bool lact = lel < ne;
 
-  // prefetch the partner fluxes of this line's R ends (0 on L ends)
-  T fpre[DIM][2][NFLD];
+  // prefetch the partner fluxes of this line's R ends (0 on L ends) and, for
+  // the mixed path's flux balance, this element's own L-end fluxes
+  constexpr bool kCons = sizeof(T) == 4 && MODE == 0;
+  const bool cons = kCons && A.tacc != nullptr && stage >= 1;
+  T fpre[DIM][2][NFLD], fown[kCons ? DIM : 1][2][NFLD];
   if (stage != 0 && lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        const int32_t w = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+        const int k = (2 * a + sd) * NFP + ll;
+        const int32_t w = A.fnbr[(e0 + lel) * NF + k];
         const int64_t p = (int64_t)(w >> 1);
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld)
+        for (int fld = 0; fld < NFLD; ++fld) {
           fpre[a][sd][fld] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fld) * NF + p % NF];
+          if (kCons) fown[kCons ? a : 0][sd][fld] = (cons && (w & 1)) ? fc[((e0 + lel) * 2 + F0 + fld) * NF + k] : (T)0;
+        }
       }
   }
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
@@ -590,42 +599,56 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   __syncthreads();
 
   double sq = 0.0;
+  // mixed path: element flux balances (float-float partial sums per line)
+  __shared__ float2 fb[kCons ? 2 * ET * LN : 1];
+  __shared__ float2 wb[kCons ? ET * LN : 1];
+  __shared__ double tgt[kCons ? 2 * ET : 1];
+  __shared__ float dlt[kCons ? 4 * ET : 1];
   if (stage != 0) {
-    // ---- lift of the R-side common fluxes: minus L's physical flux times
-    //      this side's face metric, one pass per axis
+    // ---- lift of the R-side common fluxes: minus L's transformed flux, one
+    //      pass per axis
+    float2 bal[NFLD];
+#pragma unroll
+    for (int fld = 0; fld < NFLD; ++fld) bal[fld] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (lact) {
         const int st = ipow(N, a);
         const int base = line_base<DIM, N>(a, ll);
-        T cs[2] = {0, 0};
-        bool any = false;
 #pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-          bool nz = false;
-#pragma unroll
-          for (int fld = 0; fld < NFLD; ++fld) nz = nz || fpre[a][sd][fld] != (T)0;
-          if (!nz) continue;
-          any = true;
-          T xi[3], Sm[3][3];
-          fpt_xi<DIM, N>((2 * a + sd) * NFP + ll, O.x, xi);
-          metric<DIM>(gs + lel * NG, xi, Sm);
-          T pm = 0;
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) pm += Sm[a][c] * Sm[a][c];
-          cs[sd] = -sqrt_(pm);
-        }
-        if (any) {
-#pragma unroll
-          for (int fld = 0; fld < NFLD; ++fld) {
-            const T c0 = cs[0] * fpre[a][0][fld], c1 = cs[1] * fpre[a][1][fld];
-            T* yl = ys + (lel * NFLD + fld) * NU + base;
-#pragma unroll
-            for (int j = 0; j < N; ++j) yl[j * st] += -O.gLd[j] * c0 + O.gRd[j] * c1;
+        for (int fld = 0; fld < NFLD; ++fld) {
+          const T c0 = -fpre[a][0][fld], c1 = -fpre[a][1][fld];
+          if (cons) {
+            // outward transformed flux at both ends: own F~ (L) or -partner F~ (R)
+            // (one of own / partner flux is zero at each end, so each sum is exact)
+            const float2 wf = O.wff[ll];
+            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)(fown[kCons ? a : 0][0][fld] + c0)));
+            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)(fown[kCons ? a : 0][1][fld] + c1)));
           }
+          if (c0 == (T)0 && c1 == (T)0) continue;
+          T* yl = ys + (lel * NFLD + fld) * NU + base;
+#pragma unroll
+          for (int j = 0; j < N; ++j) yl[j * st] += -O.gLd[j] * c0 + O.gRd[j] * c1;
         }
       }
       __syncthreads();
+    }
+    if (cons) {
+      if (lact)
+#pragma unroll
+        for (int fld = 0; fld < NFLD; ++fld) fb[(lel * 2 + fld) * LN + ll] = bal[fld];
+      __syncthreads();
+      // element mass rate = -sum_k w_f F~_out,k, accumulated with the RK4
+      // weights; stage 4 turns it into the step's target mass change
+      for (int t = tid; t < 2 * ne; t += blockDim.x) {
+        float2 sm = make_float2(0.f, 0.f);
+        for (int l = 0; l < LN; ++l) sm = ff_add(sm, fb[t * LN + l]);
+        const double Te = -((double)sm.x + (double)sm.y);
+        const int64_t gt = e0 * 2 + t;
+        if (stage == 1) A.tacc[gt] = Te;
+        else if (stage < 4) A.tacc[gt] += 2.0 * Te;
+        else tgt[t] = A.dt / 6.0 * (A.tacc[gt] + Te);
+      }
     }
     // ---- du/dt and the RK4 register update
     RKConstF rkc;
@@ -644,12 +667,75 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
         continue;
       }
+      if (kCons && cons && stage == 4) {
+        // float-float update now, the element's uniform correction below
+        float2* U = reinterpret_cast<float2*>(A.u);
+        const float* Acc = reinterpret_cast<const float*>(A.acc);
+        const float2 u = U[g];
+        const float inc = rkc.dt6 * (Acc[g] + (float)R);
+        const float s2 = u.x + inc;
+        const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
+        const float hi = s2 + e2;
+        U[g] = make_float2(hi, e2 - (hi - s2));
+        ys[idx] = (T)inc;
+        continue;
+      }
       const T yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
       if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
       ustg[g] = yt;
       ys[idx] = yt;
     }
     __syncthreads();
+    if (kCons && cons && stage == 4) {
+      // per line: sum of w det J * increment (and of w det J), float-float
+      if (lact) {
+        const int base = line_base<DIM, N>(0, ll);
+        const float2* wd = A.wdetf + (e0 + lel) * NU + base;
+        float2 wsl = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int fld = 0; fld < NFLD; ++fld) {
+          float2 sl = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const float2 w2 = wd[j];
+            sl = ff_add(sl, ff_mul(w2, (float)ys[(lel * NFLD + fld) * NU + base + j]));
+            if (fld == 0) wsl = ff_add(wsl, w2);
+          }
+          fb[(lel * 2 + fld) * LN + ll] = sl;
+        }
+        wb[lel * LN + ll] = wsl;
+      }
+      __syncthreads();
+      for (int t = tid; t < 2 * ne; t += blockDim.x) {
+        const int el = t / 2;
+        float2 S2 = make_float2(0.f, 0.f), W2 = make_float2(0.f, 0.f);
+        for (int l = 0; l < LN; ++l) {
+          S2 = ff_add(S2, fb[t * LN + l]);
+          W2 = ff_add(W2, wb[el * LN + l]);
+        }
+        const double S = (double)S2.x + (double)S2.y, W = (double)W2.x + (double)W2.y;
+        const double d = (tgt[t] - S) / W;
+        const float dh = (float)d;
+        dlt[2 * t] = dh;
+        dlt[2 * t + 1] = (float)(d - (double)dh);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+        const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+        const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
+        float2* U = reinterpret_cast<float2*>(A.u);
+        const float2 u = U[g];
+        const float dh = dlt[2 * (el * 2 + fld)], dl = dlt[2 * (el * 2 + fld) + 1];
+        const float s2 = u.x + dh;
+        const float e2 = two_sum_lo(u.x, dh, s2) + (u.y + dl);
+        const float hi = s2 + e2;
+        U[g] = make_float2(hi, e2 - (hi - s2));
+        if (!isfinite(hi)) atomicExch(&A.status[ST_STATUS], -4);
+        ustg[g] = (T)hi;
+        ys[idx] = (T)hi;
+      }
+      __syncthreads();
+    }
   }
   if (stage >= 0 && lact) {
     // ---- flux-point traces of the new stage input (Step 1 of the next stage)
