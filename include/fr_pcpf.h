@@ -147,6 +147,17 @@ typedef struct fr_ic {
   const double* phi0;    /* FR_IC_ARRAY: host, n_dof */
 } fr_ic;
 
+/* One instance of a batch (fr_field_init_batch): elements
+ * [elem_begin, elem_end) of the union mesh with their own time step,
+ * interface width eps, maximum artificial viscosity nu_max, pseudo time step,
+ * velocity field and initial circle. */
+typedef struct fr_instance {
+  int64_t elem_begin, elem_end;
+  double dt, eps, nu_max, pseudo_dtau;
+  fr_velocity vel;       /* vel.T must equal the batch's params->vel.T */
+  fr_ic ic;              /* FR_IC_CIRCLE; ic.precondition is ignored */
+} fr_instance;
+
 typedef struct fr_stats {
   int64_t n_steps;       /* physical steps taken since init */
   double t;              /* physical time */
@@ -173,6 +184,11 @@ int fr_mesh_solution_points(const fr_mesh* mesh, double* out);
 int fr_mesh_quadrature(const fr_mesh* mesh, double* out);
 void fr_mesh_destroy(fr_mesh* mesh);
 
+/* Union of n meshes of the same element type and order (their elements in
+ * order, each keeping its own faces and periodicity): the mesh of a batch of
+ * independent instances.  Inputs are not modified. */
+int fr_mesh_concat(const fr_mesh* const* meshes, int n, fr_mesh** out);
+
 /* ---- field ----------------------------------------------------------- */
 
 /* Bytes of device workspace fr_field_init needs for this mesh and params. */
@@ -185,6 +201,18 @@ int fr_field_workspace_bytes(const fr_mesh* mesh, const fr_params* prm, size_t* 
  * finite), FR_EUNSUPPORTED, FR_ECUDA. */
 int fr_field_init(const fr_mesh* mesh, const fr_params* prm, const fr_ic* ic,
                   void* workspace, size_t workspace_bytes, void* stream, fr_field** out);
+
+/* A field over a batch of independent instances sharing one union mesh
+ * (fr_mesh_concat of quad or hex meshes of one order): each instance marches
+ * with its own dt, eps, nu_max, pseudo_dtau and velocity; gamma, tau, the
+ * preconditioning schedule, the sensor ramp, the precision and the velocity
+ * period come from `params`.  Needs params->vel_cache = 1 (the velocities are
+ * stored per point).  The instances step together: fr_step(n) advances every
+ * instance n of its own steps.  Preconditioning at t = 0 when `precondition`.
+ * Errors as fr_field_init; FR_EUNSUPPORTED for triangles. */
+int fr_field_init_batch(const fr_mesh* mesh, const fr_params* params, int n_instances,
+                        const fr_instance* instances, int precondition, void* workspace,
+                        size_t workspace_bytes, void* stream, fr_field** out);
 
 /* Advance n_steps physical RK4 steps on `stream` (asynchronous).  Before step
  * n (n > 0, n % n_precond == 0) psi is reset to phi - 1/2 and preconditioned.

@@ -52,6 +52,19 @@ class Mesh:
         check(lib().fr_mesh_info_get(h, C.byref(self.info)), "fr_mesh_info_get")
 
     @classmethod
+    def concat(cls, meshes):
+        """Union mesh of a batch of instances (fr_mesh_concat)."""
+        arr = (C.c_void_p * len(meshes))(*[m.handle for m in meshes])
+        h = C.c_void_p()
+        check(lib().fr_mesh_concat(arr, len(meshes), C.byref(h)), "fr_mesh_concat")
+        obj = cls.__new__(cls)
+        obj.handle = h
+        obj.info = capi.fr_mesh_info()
+        check(lib().fr_mesh_info_get(h, C.byref(obj.info)), "fr_mesh_info_get")
+        obj.parts = [m.info.n_elems for m in meshes]
+        return obj
+
+    @classmethod
     def from_synthetic(cls, m, order):
         return cls(m.nodes, m.conn, m.etype, order, tuple(m.periodic) + (False,) * (3 - len(m.periodic)),
                    tuple(m.period) + (1.0,) * (3 - len(m.period)))
@@ -145,6 +158,51 @@ class Field:
         check(lib().fr_field_init(mesh.handle, C.byref(params), C.byref(icd), C.c_void_p(self._base),
                                   nbytes.value, self._stream(stream), C.byref(h)), "fr_field_init")
         self.handle = h
+
+    @classmethod
+    def batch(cls, mesh, params, instances, precondition=True, stream=None):
+        """A field over a batch of instances on a union mesh (fr_field_init_batch).
+
+        instances: list of dicts with elem_begin, elem_end, dt, eps, nu_max,
+        pseudo_dtau, velocity (synthetic.Velocity-like) and circle."""
+        import torch
+        obj = cls.__new__(cls)
+        obj.mesh = mesh
+        obj.params = params
+        obj.torch = torch
+        nbytes = C.c_size_t()
+        check(lib().fr_field_workspace_bytes(mesh.handle, C.byref(params), C.byref(nbytes)),
+              "fr_field_workspace_bytes")
+        obj.workspace_bytes = nbytes.value
+        obj._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+        obj._base = (obj._ws.data_ptr() + 255) // 256 * 256
+        arr = (capi.fr_instance * len(instances))()
+        obj._keep = []
+        for k, d in enumerate(instances):
+            I = arr[k]
+            I.elem_begin, I.elem_end = int(d["elem_begin"]), int(d["elem_end"])
+            I.dt, I.eps, I.nu_max, I.pseudo_dtau = d["dt"], d["eps"], d["nu_max"], d["pseudo_dtau"]
+            v = d["velocity"]
+            I.vel.kind = VELS[v.kind]
+            I.vel.T = float(v.T)
+            for a in range(3):
+                I.vel.a[a] = float(v.a[a]) if a < len(v.a) else 0.0
+            if v.kind == "stream":
+                arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (v.kx, v.ky, v.A, v.B)]
+                obj._keep += arrs
+                I.vel.n_modes = len(arrs[0])
+                I.vel.kx, I.vel.ky, I.vel.A, I.vel.B = [_ptr(x) for x in arrs]
+            c = d["circle"]
+            I.ic.kind = FR_IC_CIRCLE
+            for a in range(3):
+                I.ic.centre[a] = float(c.centre[a]) if a < len(c.centre) else 0.0
+            I.ic.radius, I.ic.beta = float(c.radius), float(c.beta)
+        h = C.c_void_p()
+        check(lib().fr_field_init_batch(mesh.handle, C.byref(params), len(instances), arr, int(bool(precondition)),
+                                        C.c_void_p(obj._base), nbytes.value, obj._stream(stream), C.byref(h)),
+              "fr_field_init_batch")
+        obj.handle = h
+        return obj
 
     def _stream(self, stream=None):
         s = stream if stream is not None else self.torch.cuda.current_stream()
@@ -288,3 +346,25 @@ def flow_function(mesh, params_fn, n_steps, ckpt_every):
             return gphi, dc.to(g.device)
 
     return _Flow.apply
+
+
+def batch_from_workloads(workloads, precision="mixed", precondition=True, **kw):
+    """Group workload records (synthetic.Workload, all quad or hex) by order and
+    build one batch field per order.  Returns [(order, Field, [element ranges])]."""
+    groups = {}
+    for w in workloads:
+        groups.setdefault(w.order, []).append(w)
+    out = []
+    for p in sorted(groups):
+        ws = groups[p]
+        meshes = [Mesh.from_synthetic(w.mesh(), p) for w in ws]
+        U = Mesh.concat(meshes)
+        inst, e = [], 0
+        for w, m in zip(ws, meshes):
+            n = m.info.n_elems
+            inst.append(dict(elem_begin=e, elem_end=e + n, dt=w.dt, eps=w.eps, nu_max=w.nu_max,
+                             pseudo_dtau=w.pseudo_dtau, velocity=w.velocity, circle=w.circle))
+            e += n
+        P = make_params(ws[0], precision, **kw)
+        out.append((p, Field.batch(U, P, inst, precondition=precondition), [(d["elem_begin"], d["elem_end"]) for d in inst]))
+    return out

@@ -54,6 +54,11 @@ class fr_ic(C.Structure):
                 ("radius", C.c_double), ("beta", C.c_double), ("phi0", _dp)]
 
 
+class fr_instance(C.Structure):
+    _fields_ = [("elem_begin", C.c_int64), ("elem_end", C.c_int64), ("dt", C.c_double), ("eps", C.c_double),
+                ("nu_max", C.c_double), ("pseudo_dtau", C.c_double), ("vel", fr_velocity), ("ic", fr_ic)]
+
+
 class fr_stats(C.Structure):
     _fields_ = [("n_steps", C.c_int64), ("t", C.c_double), ("last_pseudo_iters", C.c_int32),
                 ("status", C.c_int32), ("last_pseudo_rms", C.c_double), ("n_preconditions", C.c_int64)]
@@ -66,6 +71,9 @@ _SIGS = {
     "fr_mesh_solution_points": (C.c_int, [_vp, _dp]),
     "fr_mesh_quadrature": (C.c_int, [_vp, _dp]),
     "fr_mesh_destroy": (None, [_vp]),
+    "fr_mesh_concat": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "fr_field_init_batch": (C.c_int, [_vp, C.POINTER(fr_params), C.c_int, C.POINTER(fr_instance), C.c_int, _vp,
+                                      C.c_size_t, _vp, C.POINTER(_vp)]),
     "fr_field_workspace_bytes": (C.c_int, [_vp, C.POINTER(fr_params), C.POINTER(C.c_size_t)]),
     "fr_field_init": (C.c_int, [_vp, C.POINTER(fr_params), C.POINTER(fr_ic), _vp, C.c_size_t, _vp,
                                 C.POINTER(_vp)]),

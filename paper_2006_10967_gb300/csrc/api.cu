@@ -17,7 +17,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf;
+  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf, ep;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t total;
 };
@@ -52,19 +52,25 @@ TriOpsT<R> tri_pointers(const TriRef& t, const R* base, const uint8_t* high) {
 }
 
 template <typename R>
-void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
-  std::memset(&b, 0, sizeof(b));
-  b.vel.kind = prm->vel.kind;
-  for (int c = 0; c < 3; ++c) b.vel.a[c] = (R)prm->vel.a[c];
-  if (prm->vel.kind == FR_VEL_STREAM) {
-    b.vel.n_modes = prm->vel.n_modes;
-    for (int k = 0; k < prm->vel.n_modes; ++k) {
-      b.vel.kx[k] = (R)prm->vel.kx[k];
-      b.vel.ky[k] = (R)prm->vel.ky[k];
-      b.vel.A[k] = (R)prm->vel.A[k];
-      b.vel.B[k] = (R)prm->vel.B[k];
+void fill_vel(const fr_velocity& v, VelDescT<R>& d) {
+  std::memset(&d, 0, sizeof(d));
+  d.kind = v.kind;
+  for (int c = 0; c < 3; ++c) d.a[c] = (R)v.a[c];
+  if (v.kind == FR_VEL_STREAM) {
+    d.n_modes = v.n_modes;
+    for (int k = 0; k < v.n_modes; ++k) {
+      d.kx[k] = (R)v.kx[k];
+      d.ky[k] = (R)v.ky[k];
+      d.A[k] = (R)v.A[k];
+      d.B[k] = (R)v.B[k];
     }
   }
+}
+
+template <typename R>
+void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
+  std::memset(&b, 0, sizeof(b));
+  fill_vel<R>(prm->vel, b.vel);
   b.prm.gamma = (R)prm->gamma;
   b.prm.eps = (R)prm->eps;
   b.prm.tau = (R)prm->tau;
@@ -124,6 +130,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   L.vsf = vc ? take(E * m.dim * NF * tb) : 0;
   L.tacc = take(E * 2 * sizeof(double));
   L.wdetf = take(E * NU * 2 * sizeof(float));
+  L.ep = take(E * sizeof(ElemPar));
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -442,6 +449,8 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   // element flux balances of the mixed path's conservation correction (tensor elements)
   A.tacc = (prm->precision == FR_MIXED && m->etype != FR_TRI) ? reinterpret_cast<double*>(b + L.tacc) : nullptr;
   A.wdetf = reinterpret_cast<const float2*>(b + L.wdetf);
+  A.ep = nullptr;
+  f->ep_region = reinterpret_cast<ElemPar*>(b + L.ep);
   A.out = nullptr;
   A.stage = 0;
   A.use_dev_time = 0;
@@ -531,6 +540,84 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   err = read_status(f, s);
   *out = f;
   return err;
+}
+
+extern "C" int fr_field_init_batch(const fr_mesh* m, const fr_params* prm, int n_inst, const fr_instance* inst,
+                                   int precondition, void* ws, size_t ws_bytes, void* stream, fr_field** out) {
+  if (!m || !prm || !inst || n_inst < 1 || !out) return FR_EINVAL;
+  *out = nullptr;
+  if (m->etype == FR_TRI) return FR_EUNSUPPORTED;
+  if (!prm->vel_cache) return FR_EINVAL;
+  int64_t next = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const fr_instance& I = inst[i];
+    if (I.elem_begin != next || I.elem_end <= I.elem_begin || I.elem_end > m->E) return FR_EINVAL;
+    next = I.elem_end;
+    if (!(I.dt > 0.0) || !(I.eps >= 0.0) || !(I.nu_max >= 0.0)) return FR_EINVAL;
+    if (prm->pseudo_kmax > 0 && !(I.pseudo_dtau > 0.0)) return FR_EINVAL;
+    if (I.vel.T != prm->vel.T || I.ic.kind != FR_IC_CIRCLE) return FR_EINVAL;
+    if (I.vel.kind == FR_VEL_STREAM && (I.vel.n_modes < 1 || I.vel.n_modes > FR_MAX_MODES)) return FR_EINVAL;
+  }
+  if (next != m->E) return FR_EINVAL;
+  // initial phi per instance
+  const int64_t ndof = m->E * m->nu;
+  std::vector<double> phi(ndof);
+  for (int i = 0; i < n_inst; ++i) {
+    const fr_instance& I = inst[i];
+    for (int64_t g = I.elem_begin * m->nu; g < I.elem_end * m->nu; ++g) {
+      double r2 = 0.0;
+      for (int c = 0; c < m->dim; ++c) {
+        const double d = m->xu[g * m->dim + c] - I.ic.centre[c];
+        r2 += d * d;
+      }
+      phi[g] = 0.5 * (1.0 + std::tanh(I.ic.beta * (I.ic.radius - std::sqrt(r2))));
+    }
+  }
+  fr_ic ic{};
+  ic.kind = FR_IC_ARRAY;
+  ic.precondition = 0;
+  ic.phi0 = phi.data();
+  fr_field* f = nullptr;
+  int rc = fr_field_init(m, prm, &ic, ws, ws_bytes, stream, &f);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<ElemPar> ep(m->E);
+  for (int i = 0; i < n_inst; ++i) {
+    const fr_instance& I = inst[i];
+    for (int64_t e = I.elem_begin; e < I.elem_end; ++e) {
+      ep[e].dt = I.dt;
+      ep[e].dtau = I.pseudo_dtau;
+      ep[e].t = 0.0;
+      ep[e].eps = I.eps;
+      ep[e].nu_max = I.nu_max;
+    }
+    // this instance's velocity factor at its points
+    KArgs a = f->args;
+    a.E = I.elem_end - I.elem_begin;
+    a.geo = f->args.geo + I.elem_begin * m->dim * m->ncoef;
+    const size_t tb = f->precision == FR_FP64 ? 8 : 4;
+    a.vsu = reinterpret_cast<const char*>(f->args.vsu) + I.elem_begin * m->dim * m->nu * tb;
+    a.vsf = reinterpret_cast<const char*>(f->args.vsf) + I.elem_begin * m->dim * m->nf * tb;
+    fill_vel<double>(I.vel, a.cd.vel);
+    f->ks.vcache(a, s);
+  }
+  if (cudaMemcpyAsync(f->ep_region, ep.data(), ep.size() * sizeof(ElemPar), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess) {
+    delete f;
+    return FR_ECUDA;
+  }
+  f->args.ep = f->ep_region;
+  // the batch's pseudo step for the launch arguments is per element; keep a positive value
+  rc = FR_OK;
+  if (precondition) rc = run_precondition(f, s);
+  if (rc == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FR_ECUDA;
+  if (rc == FR_OK) rc = read_status(f, s);
+  if (rc != FR_OK && rc != FR_ENONFINITE) {
+    delete f;
+    return rc;
+  }
+  *out = f;
+  return rc;
 }
 
 extern "C" int fr_step(fr_field* f, int n_steps, void* stream) {

@@ -30,6 +30,7 @@ struct fr_field {
   int mass_grid = 1;
   double* xfer = nullptr;  // E*nu doubles, staging for get/set in the mixed path
   AdjRecord rec;
+  frp::ElemPar* ep_region = nullptr;  // per-element parameters (used by batch fields)
   // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
   int profiling = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];

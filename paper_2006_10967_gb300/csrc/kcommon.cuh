@@ -69,6 +69,14 @@ struct TriOpsT {
   const uint8_t* high;
 };
 
+// Per-element parameters of a batch of independent instances (one union
+// mesh): each instance keeps its own time step, time, eps and nu_max.
+struct ElemPar {
+  double dt, dtau;  // physical and pseudo time steps
+  double t;         // physical time at the start of the current step
+  double eps, nu_max;
+};
+
 struct KArgs {
   int64_t E;
   const double* geo;     // E x dim x ncoef (fp64)
@@ -89,6 +97,7 @@ struct KArgs {
   const void* vsu;       // T E x dim x nu: spatial velocity factor at solution points (or nullptr)
   const void* vsf;       // T E x dim x nf: spatial velocity factor at flux points (or nullptr)
   double* tacc;          // E x 2: RK accumulation of the element flux balances (mixed path) or nullptr
+  ElemPar* ep;           // E per-element parameters (batched instances) or nullptr (uniform)
   const float2* wdetf;   // E x nu: w_i det J_i as float-float pairs (mixed path)
   int stage;             // 1..4 RK stage, -1: write the rate into out
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
@@ -203,15 +212,14 @@ __device__ __forceinline__ double rk_update(int s, double dt, double R, double& 
 
 // RK4 stage update of value g in the FP64 path: u, acc double.  Returns the
 // next stage input; adds the squared pseudo residual to *sq when asked.
-struct RKConstF;
-__device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, double* sq) {
+__device__ __forceinline__ double rk_apply_d(const KArgs& A, int stage, int64_t g, double R, double dt, double* sq) {
   double uu = A.u[g], aa = stage == 1 ? 0.0 : A.acc[g];
   const double uold = uu;
-  const double y = rk_update(stage, A.dt, R, uu, aa);
+  const double y = rk_update(stage, dt, R, uu, aa);
   if (stage < 4) A.acc[g] = aa;
   else A.u[g] = uu;
   if (sq) {
-    const double d = (uu - uold) / A.dt;
+    const double d = (uu - uold) / dt;
     *sq += d * d;
   }
   return y;
@@ -222,8 +230,18 @@ __device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g,
 // instructions; acc = sum_s b_s k_s and the stage values are float.
 struct RKConstF {
   float half_dt, dt, dt6;
-  double rdt;
+  double rdt, ddt;
 };
+
+__device__ __forceinline__ RKConstF rk_const(double dt) {
+  RKConstF c;
+  c.half_dt = (float)(0.5 * dt);
+  c.dt = (float)dt;
+  c.dt6 = (float)(dt / 6.0);
+  c.rdt = 1.0 / dt;
+  c.ddt = dt;
+  return c;
+}
 
 __device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
   const float bb = s - a;
@@ -270,9 +288,9 @@ __device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, 
   }
 }
 
-__device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, const RKConstF&,
+__device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, const RKConstF& c,
                                            double* sq) {
-  return rk_apply(A, stage, g, R, sq);
+  return rk_apply_d(A, stage, g, R, c.ddt, sq);
 }
 
 // Block-wide sum of one double (all threads get the result).

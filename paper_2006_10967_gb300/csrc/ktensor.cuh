@@ -174,12 +174,19 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   const TensorOpsT<T>& O = BC.ops;
   const PrmT<T> P = BC.prm;
   __shared__ T gfac_s;
+  __shared__ T gfe[ET], epe[ET];  // per-element time factor and eps (batched instances)
   __shared__ int nL;
   if (tid == 0) {
     nL = 0;
     const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
     gfac_s = (T)time_factor(A, tstage);
   }
+  if (A.ep)
+    for (int el = tid; el < ne; el += blockDim.x) {
+      const ElemPar& ep = A.ep[e0 + el];
+      gfe[el] = A.prm.T > 0.0 ? cpi((T)((ep.t + rk_c(A.stage) * ep.dt) / A.prm.T)) : (T)1;
+      epe[el] = (T)ep.eps;
+    }
   const int lel = tid / LN, ll = tid % LN;
   const bool lact = lel < ne;
   // Prefetch this thread's line-end connectivity and partner traces for all
@@ -314,12 +321,13 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
         if (top) hi += v;
       }
       double nu = 0.0;
+      const double nmax = A.ep ? (double)A.ep[e0 + el].nu_max : A.prm.nu_max;
       if (tot > 0.0 && hi > 0.0) {
         const double se = log10(hi / tot);
         const double lo = A.prm.s0 - A.prm.kappa, up = A.prm.s0 + A.prm.kappa;
         if (se < lo) nu = 0.0;
-        else if (se > up) nu = A.prm.nu_max;
-        else nu = 0.5 * A.prm.nu_max * (1.0 + sin(M_PI * (se - A.prm.s0) / (2.0 * A.prm.kappa)));
+        else if (se > up) nu = nmax;
+        else nu = 0.5 * nmax * (1.0 + sin(M_PI * (se - A.prm.s0) / (2.0 * A.prm.kappa)));
       }
       nus[el] = (T)nu;
     }
@@ -366,14 +374,16 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           qf[fld][c] = acc;
         }
       T v[3];
+      const T gel = A.ep ? gfe[el] : gfac;
+      const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsf) {
         const T* vc = reinterpret_cast<const T*>(A.vsf) + (e0 + el) * DIM * NF + k;
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) v[c] = gfac * vc[c * NF];
+        for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NF];
       } else {
         T x[3];
         map_point<S::ET_, T>(gs + el * NG, xi, x);
-        velocity<DIM, T>(BC.vel, x, gfac, v);
+        velocity<DIM, T>(BC.vel, x, gel, v);
       }
       T vn = 0, v2 = 0, g2 = 0;
 #pragma unroll
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) fvn += nh[c] * (P.eps * qf[0][c] - sharp * qf[1][c]);
+      for (int c = 0; c < DIM; ++c) fvn += nh[c] * (epsel * qf[0][c] - sharp * qf[1][c]);
       const T Fp = (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
       const T Fs = (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
       // the transformed common flux F~ = |pn| F out of L; the R side uses -F~
@@ -424,14 +434,16 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
     const T dj = metric<DIM>(gs + el * NG, xi, Sm);
     if (MODE == 0) {
       T v[3];
+      const T gel = A.ep ? gfe[el] : gfac;
+      const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsu) {
         const T* vc = reinterpret_cast<const T*>(A.vsu) + (e0 + el) * DIM * NU + i;
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) v[c] = gfac * vc[c * NU];
+        for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
       } else {
         T x[3];
         map_point<S::ET_, T>(gs + el * NG, xi, x);
-        velocity<DIM, T>(BC.vel, x, gfac, v);
+        velocity<DIM, T>(BC.vel, x, gel, v);
       }
       T qp[3], qs[3], v2 = 0, g2 = 0;
 #pragma unroll
@@ -448,7 +460,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       T f0[3], f1[3];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
-        f0[c] = ph * v[c] - M * (P.eps * qp[c] - sharp * qs[c]);
+        f0[c] = ph * v[c] - M * (epsel * qp[c] - sharp * qs[c]);
         f1[c] = ps * v[c];
       }
 #pragma unroll
@@ -599,6 +611,14 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   __syncthreads();
 
   double sq = 0.0;
+  // RK constants: one set, or one per element for batched instances
+  __shared__ RKConstF rks[ET];
+  const RKConstF rk0 = rk_const(A.dt);
+  if (A.ep) {
+    for (int el = tid; el < ne; el += blockDim.x) rks[el] = rk_const(MODE == 0 ? A.ep[e0 + el].dt : A.ep[e0 + el].dtau);
+    __syncthreads();
+  }
+  auto rkc_el = [&](int el) -> const RKConstF& { return A.ep ? rks[el] : rk0; };
   // mixed path: element flux balances (float-float partial sums per line)
   __shared__ float2 fb[kCons ? 2 * ET * LN : 1];
   __shared__ float2 wb[kCons ? ET * LN : 1];
@@ -647,17 +667,13 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         const int64_t gt = e0 * 2 + t;
         if (stage == 1) A.tacc[gt] = Te;
         else if (stage < 4) A.tacc[gt] += 2.0 * Te;
-        else tgt[t] = A.dt / 6.0 * (A.tacc[gt] + Te);
+        else tgt[t] = rkc_el(t / 2).ddt / 6.0 * (A.tacc[gt] + Te);
       }
     }
     // ---- du/dt and the RK4 register update
-    RKConstF rkc;
-    rkc.half_dt = (float)(0.5 * A.dt);
-    rkc.dt = (float)A.dt;
-    rkc.dt6 = (float)(A.dt / 6.0);
-    rkc.rdt = 1.0 / A.dt;
     for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
       const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+      const RKConstF& rkc = rkc_el(el);
       T xi[3], Sm[3][3];
       upt_xi<DIM, N>(i, O.x, xi);
       const T dj = metric<DIM>(gs + el * NG, xi, Sm);
@@ -672,7 +688,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         float2* U = reinterpret_cast<float2*>(A.u);
         const float* Acc = reinterpret_cast<const float*>(A.acc);
         const float2 u = U[g];
-        const float inc = rkc.dt6 * (Acc[g] + (float)R);
+        const float inc = rkc_el(el).dt6 * (Acc[g] + (float)R);
         const float s2 = u.x + inc;
         const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
         const float hi = s2 + e2;
@@ -762,6 +778,8 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   }
   if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)
     A.dstate[DS_TIME] = A.dstate[DS_TIME] + A.dt;
+  if (MODE == 0 && stage == 4 && A.use_dev_time && A.ep)
+    for (int el = tid; el < ne; el += blockDim.x) A.ep[e0 + el].t += A.ep[e0 + el].dt;
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
 }
 

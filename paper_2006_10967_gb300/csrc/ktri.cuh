@@ -371,11 +371,7 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   }
   __syncthreads();
   double sq = 0.0;
-  RKConstF rkc;
-  rkc.half_dt = (float)(0.5 * A.dt);
-  rkc.dt = (float)A.dt;
-  rkc.dt6 = (float)(A.dt / 6.0);
-  rkc.rdt = 1.0 / A.dt;
+  const RKConstF rkc = rk_const(A.dt);
   if (stage != 0) {
     for (int el = tid; el < ne; el += blockDim.x) {
       TriMet<T> m;

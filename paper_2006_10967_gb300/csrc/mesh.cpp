@@ -362,4 +362,52 @@ extern "C" int fr_mesh_quadrature(const fr_mesh* m, double* out) {
   return FR_OK;
 }
 
+extern "C" int fr_mesh_concat(const fr_mesh* const* meshes, int n, fr_mesh** out) {
+  if (!meshes || n < 1 || !out) return FR_EINVAL;
+  *out = nullptr;
+  const fr_mesh* m0 = meshes[0];
+  if (!m0) return FR_EINVAL;
+  int64_t E = 0;
+  for (int i = 0; i < n; ++i) {
+    const fr_mesh* mi = meshes[i];
+    if (!mi || mi->etype != m0->etype || mi->order != m0->order || mi->dim != m0->dim) return FR_EINVAL;
+    E += mi->E;
+  }
+  if (E * m0->nf >= (int64_t(1) << 30)) return FR_EUNSUPPORTED;
+  fr_mesh* u = new (std::nothrow) fr_mesh();
+  if (!u) return FR_ENOMEM;
+  try {
+    *u = *m0;
+    u->E = E;
+    u->geo.clear();
+    u->fnbr.clear();
+    u->xu.clear();
+    u->wdet.clear();
+    u->volume = 0.0;
+    u->n_boundary = 0;
+    double hsum = 0.0;
+    int64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      const fr_mesh* mi = meshes[i];
+      u->geo.insert(u->geo.end(), mi->geo.begin(), mi->geo.end());
+      u->xu.insert(u->xu.end(), mi->xu.begin(), mi->xu.end());
+      u->wdet.insert(u->wdet.end(), mi->wdet.begin(), mi->wdet.end());
+      for (int32_t w : mi->fnbr) {
+        const int64_t g = (int64_t)(w >> 1) + off * mi->nf;
+        u->fnbr.push_back((int32_t)((g << 1) | (w & 1)));
+      }
+      u->volume += mi->volume;
+      u->n_boundary += mi->n_boundary;
+      hsum += mi->h * mi->E;
+      off += mi->E;
+    }
+    u->h = hsum / E;
+  } catch (const std::bad_alloc&) {
+    delete u;
+    return FR_ENOMEM;
+  }
+  *out = u;
+  return FR_OK;
+}
+
 extern "C" void fr_mesh_destroy(fr_mesh* m) { delete m; }
