@@ -251,6 +251,7 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
       KArgs a = f->args;
       a.use_dev_time = 1;
       a.dt = dt;
+      a.rk = rk_const(dt);
       for (int st = 1; st <= 4; ++st) {
         char* U = R.ws + R.off_stage + ((size_t)(n - s0) * 4 + (st - 1)) * z.stage_slot;
         CK(cudaMemcpyAsync(U, f->args.ustg, ubytes, cudaMemcpyDeviceToDevice, s));

@@ -310,6 +310,7 @@ int run_precondition(fr_field* f, cudaStream_t s) {
   KArgs a = f->args;
   a.stage = 0;
   a.dt = f->prm.pseudo_dtau;
+  a.rk = rk_const(a.dt);
   a.use_dev_time = 0;
   f->ks.ka[1](a, s);
   for (int k = 0; k < f->prm.pseudo_kmax; ++k)
@@ -331,6 +332,7 @@ int run_step(fr_field* f, cudaStream_t s) {
   KArgs a = f->args;
   a.use_dev_time = 1;
   a.dt = f->prm.dt;
+  a.rk = rk_const(a.dt);
   for (int st = 1; st <= 4; ++st) {
     a.stage = st;
     timed(f, 0, f->ks.kb[0], a, s);
@@ -456,6 +458,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.use_dev_time = 0;
   A.t = 0.0;
   A.dt = prm->dt;
+  A.rk = rk_const(prm->dt);
   A.prm.gamma = prm->gamma;
   A.prm.eps = prm->eps;
   A.prm.tau = prm->tau;
@@ -739,6 +742,7 @@ extern "C" int fr_rhs(fr_field* f, double t, double* dev_out, void* stream) {
   a.t = t;
   a.stage = 1;
   a.dt = f->prm.dt;
+  a.rk = rk_const(a.dt);
   f->ks.kb[0](a, s);
   a.stage = -1;
   a.out = dev_out;
@@ -755,6 +759,7 @@ extern "C" int fr_rhs_pseudo(fr_field* f, double* dev_out, void* stream) {
   a.use_dev_time = 0;
   a.stage = 1;
   a.dt = f->prm.pseudo_dtau;
+  a.rk = rk_const(a.dt);
   f->ks.kb[1](a, s);
   a.stage = -1;
   a.out = dev_out;

@@ -69,6 +69,23 @@ struct TriOpsT {
   const uint8_t* high;
 };
 
+// RK4 step constants (filled on the host for uniform fields; per element for
+// batched instances)
+struct RKConstF {
+  float half_dt, dt, dt6;
+  double rdt, ddt;
+};
+
+__host__ __device__ __forceinline__ RKConstF rk_const(double dt) {
+  RKConstF c;
+  c.half_dt = (float)(0.5 * dt);
+  c.dt = (float)dt;
+  c.dt6 = (float)(dt / 6.0);
+  c.rdt = 1.0 / dt;
+  c.ddt = dt;
+  return c;
+}
+
 // Per-element parameters of a batch of independent instances (one union
 // mesh): each instance keeps its own time step, time, eps and nu_max.
 struct ElemPar {
@@ -103,6 +120,7 @@ struct KArgs {
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
   double t;              // KB: stage time when !use_dev_time
   double dt;             // physical dt or pseudo dtau
+  RKConstF rk;           // rk_const(dt), set on the host with dt
   PhysPrm prm;
   BulkConst<double> cd;
   BulkConst<float> cf;
@@ -228,20 +246,7 @@ __device__ __forceinline__ double rk_apply_d(const KArgs& A, int stage, int64_t 
 // Mixed path: the solution u is a float-float pair (hi, lo) (48-bit
 // significand) so that float stage increments accumulate without FP64
 // instructions; acc = sum_s b_s k_s and the stage values are float.
-struct RKConstF {
-  float half_dt, dt, dt6;
-  double rdt, ddt;
-};
 
-__device__ __forceinline__ RKConstF rk_const(double dt) {
-  RKConstF c;
-  c.half_dt = (float)(0.5 * dt);
-  c.dt = (float)dt;
-  c.dt6 = (float)(dt / 6.0);
-  c.rdt = 1.0 / dt;
-  c.ddt = dt;
-  return c;
-}
 
 __device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
   const float bb = s - a;

@@ -128,7 +128,7 @@ struct KBLayout {
   static constexpr int LN = S::NFP;  // lines per axis per element
   static constexpr int PER_EL_T = NFLD * S::NU          // u, later the divergence
                                   + NFLD * DIM * S::NU  // q~ -> q -> f~
-                                  + 3 * NFLD * S::NF    // uf, uo, cor
+                                  + 2 * NFLD * S::NF    // uo, cor
                                   + S::NG               // geometry
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
@@ -154,8 +154,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);  // [ET][NFLD][NU]
   T* qt = us + ET * NFLD * NU;             // [ET][NFLD][DIM][NU]
-  T* uf = qt + ET * NFLD * DIM * NU;       // [ET][NFLD][NF]
-  T* uo = uf + ET * NFLD * NF;             // [ET][NFLD][NF]
+  T* uo = qt + ET * NFLD * DIM * NU;       // [ET][NFLD][NF] partner traces (own trace at R points)
   T* cor = uo + ET * NFLD * NF;            // [ET][NFLD][NF]
   T* gs = cor + ET * NFLD * NF;            // [ET][NG]
   T* chi = gs + ET * NG;                   // MODE 1: [ET][2][NU]
@@ -252,8 +251,6 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
         const T o0 = (w0 & 1) ? opre[a][0][fld] : f0;
         const T o1 = (w1 & 1) ? opre[a][1][fld] : f1;
         const int fo = (lel * NFLD + fld) * NF;
-        uf[fo + k0] = f0;
-        uf[fo + k1] = f1;
         uo[fo + k0] = o0;
         uo[fo + k1] = o1;
         const T jm = o0 - f0, jp = o1 - f1;
@@ -394,8 +391,14 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       }
       const T M = fmax(sqrt_(v2), P.gamma);
       const T gm = fmax(sqrt_(g2), P.delta);
-      const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
-      const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
+      T pL = 0, sL = 0;  // own traces at this L point (Step 1, recomputed)
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const T lw = s ? O.lend[1][j] : O.lend[0][j];
+        pL += lw * us[(el * 2 + 0) * NU + b0 + j * st];
+        sL += lw * us[(el * 2 + 1) * NU + b0 + j * st];
+      }
+      const T pR = uo[(el * 2 + 0) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
       const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
@@ -419,7 +422,10 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
         for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
         gn += nh[c] * acc;
       }
-      const T F = pm * (-nus[el] * gn + P.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]));
+      T L_ = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) L_ += (s ? O.lend[1][j] : O.lend[0][j]) * us[el * NU + b0 + j * st];
+      const T F = pm * (-nus[el] * gn + P.tau_pseudo * (L_ - uo[el * NF + k]));
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       cor[el * NF + k] = F;
     }
@@ -586,7 +592,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   // the mixed path's flux balance, this element's own L-end fluxes
   constexpr bool kCons = sizeof(T) == 4 && MODE == 0;
   const bool cons = kCons && A.tacc != nullptr && stage >= 1;
-  T fpre[DIM][2][NFLD], fown[kCons ? DIM : 1][2][NFLD];
+  T fpre[DIM][2][NFLD];
   if (stage != 0 && lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -598,7 +604,6 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
 #pragma unroll
         for (int fld = 0; fld < NFLD; ++fld) {
           fpre[a][sd][fld] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fld) * NF + p % NF];
-          if (kCons) fown[kCons ? a : 0][sd][fld] = (cons && (w & 1)) ? fc[((e0 + lel) * 2 + F0 + fld) * NF + k] : (T)0;
         }
       }
   }
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   double sq = 0.0;
   // RK constants: one set, or one per element for batched instances
   __shared__ RKConstF rks[ET];
-  const RKConstF rk0 = rk_const(A.dt);
+  const RKConstF& rk0 = A.rk;
   if (A.ep) {
     for (int el = tid; el < ne; el += blockDim.x) rks[el] = rk_const(MODE == 0 ? A.ep[e0 + el].dt : A.ep[e0 + el].dtau);
     __syncthreads();
@@ -639,11 +644,13 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         for (int fld = 0; fld < NFLD; ++fld) {
           const T c0 = -fpre[a][0][fld], c1 = -fpre[a][1][fld];
           if (cons) {
-            // outward transformed flux at both ends: own F~ (L) or -partner F~ (R)
-            // (one of own / partner flux is zero at each end, so each sum is exact)
+            // outward transformed flux at both ends: own F~ (L ends, c = 0) or
+            // -partner F~ (R ends)
             const float2 wf = O.wff[ll];
-            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)(fown[kCons ? a : 0][0][fld] + c0)));
-            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)(fown[kCons ? a : 0][1][fld] + c1)));
+            const T* fco = fc + ((e0 + lel) * 2 + F0 + fld) * NF + (2 * a) * NFP + ll;
+            const T o0 = c0 == (T)0 ? fco[0] : c0, o1 = c1 == (T)0 ? fco[NFP] : c1;
+            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o0));
+            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o1));
           }
           if (c0 == (T)0 && c1 == (T)0) continue;
           T* yl = ys + (lel * NFLD + fld) * NU + base;

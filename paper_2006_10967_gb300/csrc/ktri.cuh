@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   }
   __syncthreads();
   double sq = 0.0;
-  const RKConstF rkc = rk_const(A.dt);
+  const RKConstF& rkc = A.rk;
   if (stage != 0) {
     for (int el = tid; el < ne; el += blockDim.x) {
       TriMet<T> m;
