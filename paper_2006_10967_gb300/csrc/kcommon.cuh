@@ -150,6 +150,11 @@ __device__ __forceinline__ double cpi(double x) { return cospi(x); }
 __device__ __forceinline__ float cpi(float x) { return cospif(x); }
 __device__ __forceinline__ void scpi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void scpi(float x, float* s, float* c) { sincospif(x, s, c); }
+// Velocity sin/cos of pi*x: the FP64 path keeps sincospi; the float path uses
+// the special-function unit (__sincosf of pi*x, absolute error ~4e-7 for the
+// coordinates of the unit domain).
+__device__ __forceinline__ void vscpi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void vscpi(float x, float* s, float* c) { __sincosf(3.14159265358979f * x, s, c); }
 __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
 __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
@@ -164,8 +169,8 @@ __device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, 
       break;
     case 1: {  // Rider-Kothe; sin(2 pi a) = 2 sin(pi a) cos(pi a)
       R sx, cx, sy, cy;
-      scpi(x[0], &sx, &cx);
-      scpi(x[1], &sy, &cy);
+      vscpi(x[0], &sx, &cx);
+      vscpi(x[1], &sy, &cy);
       v[0] = -sx * sx * ((R)2 * sy * cy) * g;
       v[1] = ((R)2 * sx * cx) * sy * sy * g;
       if (DIM == 3) v[DIM - 1] = 0;
@@ -174,9 +179,9 @@ __device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, 
     case 2: {  // LeVeque 3D deformation
       if (DIM == 3) {
         R sx, cx, sy, cy, sz, cz;
-        scpi(x[0], &sx, &cx);
-        scpi(x[1], &sy, &cy);
-        scpi(x[DIM - 1], &sz, &cz);
+        vscpi(x[0], &sx, &cx);
+        vscpi(x[1], &sy, &cy);
+        vscpi(x[DIM - 1], &sz, &cz);
         const R s2x = (R)2 * sx * cx, s2y = (R)2 * sy * cy, s2z = (R)2 * sz * cz;
         v[0] = (R)2 * sx * sx * s2y * s2z * g;
         v[1] = -s2x * sy * sy * s2z * g;

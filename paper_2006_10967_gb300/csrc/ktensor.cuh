@@ -99,6 +99,47 @@ __device__ __forceinline__ T metric(const T* g, const T* xi, T S[3][3]) {
   return adjugate<DIM, T>(J, S);
 }
 
+// Affine elements (no cross terms in the map) have one metric per element;
+// kernels cache it per tile: mc[el] = {S (3x3), det J}, aff[el] = 1.
+template <int DIM, typename T>
+__device__ __forceinline__ bool is_affine(const T* g) {
+  constexpr int NC = DIM == 2 ? 4 : 8;
+  bool aff = true;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int k = DIM + 1; k < NC; ++k) aff = aff && g[c * NC + k] == (T)0;
+  return aff;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], bool aff, const T* mc) {
+  if (aff) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) S[a][b] = mc[a * 3 + b];
+    return mc[9];
+  }
+  return metric<DIM>(g, xi, S);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void fill_affine(const T* gs, int ne, int NG, unsigned char* aff, T* mc) {
+  for (int el = threadIdx.x; el < ne; el += blockDim.x) {
+    const T* g = gs + el * NG;
+    const bool a = is_affine<DIM>(g);
+    aff[el] = a;
+    if (a) {
+      T xi[3] = {0, 0, 0}, S[3][3];
+      const T dj = metric<DIM>(g, xi, S);
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) mc[el * 10 + p * 3 + q] = (p < DIM && q < DIM) ? S[p][q] : (T)0;
+      mc[el * 10 + 9] = dj;
+    }
+  }
+}
+
 // Lines: along axis a, line l runs through the solution points whose other
 // coordinates (in increasing axis order, lowest fastest) encode l; it ends
 // at flux point l of faces (a, -) and (a, +).
@@ -214,6 +255,10 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   }
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
   __syncthreads();
+  __shared__ T mcs[ET * 10];
+  __shared__ unsigned char affs[ET];
+  fill_affine<DIM, T>(gs, ne, NG, affs, mcs);
+  __syncthreads();
   const T gfac = gfac_s;
 
   // ---- Steps 1-3, one pass per axis: traces at the line ends, partner
@@ -285,7 +330,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           const int i = base + j * st;
           T xi[3], Sm[3][3];
           upt_xi<DIM, N>(i, O.x, xi);
-          const T rdj = (T)1 / metric<DIM>(gs + lel * NG, xi, Sm);
+          const T rdj = (T)1 / metric_c<DIM>(gs + lel * NG, xi, Sm, affs[lel], mcs + lel * 10);
 #pragma unroll
           for (int fld = 0; fld < NFLD; ++fld) {
             T* q = qt + (lel * NFLD + fld) * DIM * NU + i;
@@ -340,7 +385,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
     fline<DIM, N>(k, a, s, b0);
     T xi[3], Sm[3][3];
     fpt_xi<DIM, N>(k, O.x, xi);
-    metric<DIM>(gs + el * NG, xi, Sm);
+    metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
     const T sg = s ? (T)1 : (T)-1;
     T pn[3], pm = 0;
 #pragma unroll
@@ -437,7 +482,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
     upt_xi<DIM, N>(i, O.x, xi);
-    const T dj = metric<DIM>(gs + el * NG, xi, Sm);
+    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
     if (MODE == 0) {
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
@@ -614,6 +659,12 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
     ys[idx] = stage == 0 ? ustg[g] : rp[g];
   }
   __syncthreads();
+  __shared__ T mcs[ET * 10];
+  __shared__ unsigned char affs[ET];
+  if (stage != 0) {
+    fill_affine<DIM, T>(gs, ne, NG, affs, mcs);
+    __syncthreads();
+  }
 
   double sq = 0.0;
   // RK constants: one set, or one per element for batched instances
@@ -683,7 +734,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
       const RKConstF& rkc = rkc_el(el);
       T xi[3], Sm[3][3];
       upt_xi<DIM, N>(i, O.x, xi);
-      const T dj = metric<DIM>(gs + el * NG, xi, Sm);
+      const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
       const T R = -ys[idx] / dj;
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
