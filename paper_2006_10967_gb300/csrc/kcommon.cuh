@@ -273,22 +273,23 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float b) {
   return make_float2(hi, e - (hi - p));
 }
 
-__device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, float R, const RKConstF& c,
-                                          double* sq) {
-  float2* U = reinterpret_cast<float2*>(A.u);
+// Float-float register update with the state u and the accumulator value
+// already at hand (acc is read only from stage 2 on).  Writes the accumulator
+// and, at stage 4, the state to global memory unless keep_u is set.
+__device__ __forceinline__ float rk_apply_v(const KArgs& A, int stage, int64_t g, float R, const RKConstF& c,
+                                            float2 u, float acc, double* sq, float2* unew) {
   float* Acc = reinterpret_cast<float*>(A.acc);
-  const float2 u = U[g];
   switch (stage) {
     case 1: Acc[g] = R; return u.x + fmaf(c.half_dt, R, u.y);
-    case 2: Acc[g] = fmaf(2.0f, R, Acc[g]); return u.x + fmaf(c.half_dt, R, u.y);
-    case 3: Acc[g] = fmaf(2.0f, R, Acc[g]); return u.x + fmaf(c.dt, R, u.y);
+    case 2: Acc[g] = fmaf(2.0f, R, acc); return u.x + fmaf(c.half_dt, R, u.y);
+    case 3: Acc[g] = fmaf(2.0f, R, acc); return u.x + fmaf(c.dt, R, u.y);
     default: {
-      const float inc = c.dt6 * (Acc[g] + R);
+      const float inc = c.dt6 * (acc + R);
       const float s = u.x + inc;
       const float e = two_sum_lo(u.x, inc, s) + u.y;
       const float hi = s + e;
       const float lo = e - (hi - s);
-      U[g] = make_float2(hi, lo);
+      *unew = make_float2(hi, lo);
       if (sq) {
         const double d = (((double)hi - (double)u.x) + ((double)lo - (double)u.y)) * c.rdt;
         *sq += d * d;
@@ -298,10 +299,58 @@ __device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, 
   }
 }
 
+__device__ __forceinline__ float rk_apply(const KArgs& A, int stage, int64_t g, float R, const RKConstF& c,
+                                          double* sq) {
+  float2* U = reinterpret_cast<float2*>(A.u);
+  const float acc = stage > 1 ? reinterpret_cast<const float*>(A.acc)[g] : 0.f;
+  float2 un;
+  const float y = rk_apply_v(A, stage, g, R, c, U[g], acc, sq, &un);
+  if (stage >= 4) U[g] = un;
+  return y;
+}
+
 __device__ __forceinline__ double rk_apply(const KArgs& A, int stage, int64_t g, double R, const RKConstF& c,
                                            double* sq) {
   return rk_apply_d(A, stage, g, R, c.ddt, sq);
 }
+
+// ---- asynchronous global -> shared copies (cp.async; completed by
+//      cp_async_wait_all followed by a block barrier) -------------------------
+__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Block-wide copy of nbytes (a multiple of 4) of contiguous global memory into
+// shared memory, issued without waiting: 16-byte granules when both ends are
+// 16-byte aligned, 4-byte granules otherwise.
+__device__ __forceinline__ void tile_async(void* sdst, const void* gsrc, int nbytes) {
+  const char* s = static_cast<const char*>(gsrc);
+  char* d = static_cast<char*>(sdst);
+  int done = 0;
+  if (((reinterpret_cast<uintptr_t>(s) | (uintptr_t)__cvta_generic_to_shared(d)) & 15) == 0) {
+    const int n16 = nbytes >> 4;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) cp_async_16(d + 16 * i, s + 16 * i);
+    done = n16 << 4;
+  }
+  for (int i = (done >> 2) + threadIdx.x; i < (nbytes >> 2); i += blockDim.x) cp_async_4(d + 4 * i, s + 4 * i);
+}
+
+// Carves 16-byte aligned regions out of dynamic shared memory.
+struct SmemCarve {
+  unsigned char* p;
+  template <typename U>
+  __device__ __forceinline__ U* take(int count) {
+    U* r = reinterpret_cast<U*>(p);
+    p += ((size_t)count * sizeof(U) + 15) & ~(size_t)15;
+    return r;
+  }
+};
 
 // Block-wide sum of one double (all threads get the result).
 __device__ __forceinline__ double block_sum(double v, double* sh) {

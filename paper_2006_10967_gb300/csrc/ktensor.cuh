@@ -171,13 +171,14 @@ struct KBLayout {
                                   + NFLD * DIM * S::NU  // q~ -> q -> f~
                                   + 2 * NFLD * S::NF    // uo, cor
                                   + S::NG               // geometry
+                                  + (MODE == 0 ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
-  static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
+  static constexpr int ET_S = 57344 / BYTES_EL < 1 ? 1 : 57344 / BYTES_EL;
   static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
-  static constexpr int THREADS = ET * LN;
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
+  static constexpr int THREADS = (ET * LN + 31) / 32 * 32;  // whole warps; lines >= ET * LN idle
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 12;  // + region alignment
 };
 
 // ============================================================================
@@ -193,15 +194,18 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* us = reinterpret_cast<T*>(smem_raw);  // [ET][NFLD][NU]
-  T* qt = us + ET * NFLD * NU;             // [ET][NFLD][DIM][NU]
-  T* uo = qt + ET * NFLD * DIM * NU;       // [ET][NFLD][NF] partner traces (own trace at R points)
-  T* cor = uo + ET * NFLD * NF;            // [ET][NFLD][NF]
-  T* gs = cor + ET * NFLD * NF;            // [ET][NG]
-  T* chi = gs + ET * NG;                   // MODE 1: [ET][2][NU]
-  T* nus = chi + (MODE == 1 ? ET * 2 * NU : 0);
-  uint16_t* llist = reinterpret_cast<uint16_t*>(nus + (MODE == 1 ? ET : 0));  // [ET*NF] L flux points
-  unsigned char* lm = reinterpret_cast<unsigned char*>(llist + ET * NF);      // [ET][NF]
+  SmemCarve sc{smem_raw};
+  T* us = sc.take<T>(ET * NFLD * NU);         // [ET][NFLD][NU]
+  T* qt = sc.take<T>(ET * NFLD * DIM * NU);   // [ET][NFLD][DIM][NU]
+  T* uo = sc.take<T>(ET * NFLD * NF);         // [ET][NFLD][NF] partner traces (own trace at R points)
+  T* cor = sc.take<T>(ET * NFLD * NF);        // [ET][NFLD][NF]
+  T* gs = sc.take<T>(ET * NG);                // [ET][NG]
+  T* vu = sc.take<T>(MODE == 0 ? ET * DIM * NU : 0);  // MODE 0: velocity cache, solution points
+  T* vf = sc.take<T>(MODE == 0 ? ET * DIM * NF : 0);  // MODE 0: velocity cache, flux points
+  T* chi = sc.take<T>(MODE == 1 ? ET * 2 * NU : 0);   // MODE 1: [ET][2][NU]
+  T* nus = sc.take<T>(MODE == 1 ? ET : 0);
+  uint16_t* llist = sc.take<uint16_t>(ET * NF);       // [ET*NF] L flux points
+  unsigned char* lm = sc.take<unsigned char>(ET * NF);  // [ET][NF]
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       epe[el] = (T)ep.eps;
     }
   const int lel = tid / LN, ll = tid % LN;
-  const bool lact = lel < ne;
+  const bool lact = lel < ne;  // also false on the idle lines of a padded last warp
   // Prefetch this thread's line-end connectivity and partner traces for all
   // axis passes, so that the dependent global loads overlap the tile load.
   int32_t wpre[DIM][2];
@@ -238,6 +242,16 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) wpre[a][sd] = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+  }
+  // contiguous tiles: state (both fields), geometry, velocity cache; all in
+  // flight together with the connectivity loads above
+  if (MODE == 0) tile_async(us, ustg + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
+  tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
+  if (MODE == 0 && A.vsu)
+    tile_async(vu, reinterpret_cast<const T*>(A.vsu) + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
+  if (MODE == 0 && A.vsf)
+    tile_async(vf, reinterpret_cast<const T*>(A.vsf) + e0 * DIM * NF, ne * DIM * NF * (int)sizeof(T));
+  if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -249,11 +263,12 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           opre[a][sd][fld] = (w & 1) ? tr[((p / NF) * 2 + F0 + fld) * NF + p % NF] : (T)0;
       }
   }
-  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
-    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-    us[idx] = ustg[((e0 + el) * 2 + F0 + fld) * NU + i];
-  }
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
+  if (MODE == 1)
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      us[idx] = ustg[((e0 + el) * 2 + F0) * NU + i];
+    }
+  cp_async_wait_all();
   __syncthreads();
   __shared__ T mcs[ET * 10];
   __shared__ unsigned char affs[ET];
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsf) {
-        const T* vc = reinterpret_cast<const T*>(A.vsf) + (e0 + el) * DIM * NF + k;
+        const T* vc = vf + el * DIM * NF + k;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NF];
       } else {
@@ -488,7 +503,7 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsu) {
-        const T* vc = reinterpret_cast<const T*>(A.vsu) + (e0 + el) * DIM * NU + i;
+        const T* vc = vu + el * DIM * NU + i;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
       } else {
@@ -597,12 +612,16 @@ struct KALayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
   static constexpr int LN = S::NFP;
-  static constexpr int BYTES_EL = (NFLD * S::NU + S::NG) * (int)sizeof(T);
+  // mixed path: float-float state, accumulator, w det J, own fluxes and the
+  // step's mass-balance accumulator staged in shared memory as well
+  static constexpr bool PRE = sizeof(T) == 4 && MODE == 0;
+  static constexpr int BYTES_EL = (NFLD * S::NU + S::NG) * (int)sizeof(T) +
+                                  (PRE ? 2 * S::NU * 8 + 2 * S::NU * 4 + S::NU * 8 + 2 * S::NF * 4 + 16 : 0);
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
-  static constexpr int ET_S = 32768 / BYTES_EL < 1 ? 1 : 32768 / BYTES_EL;
+  static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
   static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
-  static constexpr int THREADS = ET * LN;
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
+  static constexpr int THREADS = (ET * LN + 31) / 32 * 32;  // whole warps; lines >= ET * LN idle
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 8;  // + region alignment
 };
 
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
@@ -618,8 +637,15 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sh[32];
-  T* ys = reinterpret_cast<T*>(smem_raw);  // [ET][NFLD][NU]
-  T* gs = ys + ET * NFLD * NU;             // [ET][NG]
+  constexpr bool PRE = LY::PRE;
+  SmemCarve sc{smem_raw};
+  T* ys = sc.take<T>(ET * NFLD * NU);  // [ET][NFLD][NU]
+  T* gs = sc.take<T>(ET * NG);         // [ET][NG]
+  float2* u2s = sc.take<float2>(PRE ? ET * 2 * NU : 0);  // float-float state, tile order
+  float* acs = sc.take<float>(PRE ? ET * 2 * NU : 0);    // RK accumulator
+  float2* wds = sc.take<float2>(PRE ? ET * NU : 0);      // w det J (float-float)
+  float* fcs = sc.take<float>(PRE ? ET * 2 * NF : 0);    // own transformed fluxes
+  double* tas = sc.take<double>(PRE ? ET * 2 : 0);       // mass-balance accumulator
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -631,20 +657,46 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   const int stage = A.stage;
   const TensorOpsT<T>& O = bulk<T>(A).ops;
   const int lel = tid / LN, ll = tid % LN;
-  const bool lact = lel < ne;
+  const bool lact = lel < ne;  // also false on the idle lines of a padded last warp
 
   // prefetch the partner fluxes of this line's R ends (0 on L ends) and, for
   // the mixed path's flux balance, this element's own L-end fluxes
   constexpr bool kCons = sizeof(T) == 4 && MODE == 0;
   const bool cons = kCons && A.tacc != nullptr && stage >= 1;
   T fpre[DIM][2][NFLD];
+  int32_t wpre[DIM][2];
+  if (stage != 0 && lact) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) wpre[a][sd] = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+  }
+  // contiguous tiles, all in flight together with the connectivity loads
+  if (MODE == 0) {
+    tile_async(ys, (stage == 0 ? ustg : rp) + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
+  } else {
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      const int64_t g = ((e0 + el) * 2 + F0) * NU + i;
+      ys[idx] = stage == 0 ? ustg[g] : rp[g];
+    }
+  }
+  if (stage != 0) tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
+  if (PRE && stage >= 1) {
+    tile_async(u2s, reinterpret_cast<const float2*>(A.u) + e0 * 2 * NU, ne * 2 * NU * 8);
+    if (stage >= 2) tile_async(acs, reinterpret_cast<const float*>(A.acc) + e0 * 2 * NU, ne * 2 * NU * 4);
+    if (cons) {
+      tile_async(fcs, reinterpret_cast<const float*>(A.fc) + e0 * 2 * NF, ne * 2 * NF * 4);
+      if (stage >= 2) tile_async(tas, A.tacc + e0 * 2, ne * 2 * 8);
+      if (stage == 4) tile_async(wds, A.wdetf + e0 * NU, ne * NU * 8);
+    }
+  }
   if (stage != 0 && lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        const int k = (2 * a + sd) * NFP + ll;
-        const int32_t w = A.fnbr[(e0 + lel) * NF + k];
+        const int32_t w = wpre[a][sd];
         const int64_t p = (int64_t)(w >> 1);
 #pragma unroll
         for (int fld = 0; fld < NFLD; ++fld) {
@@ -652,12 +704,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         }
       }
   }
-  for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = geo_of<T>(A)[e0 * NG + idx];
-  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
-    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-    const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
-    ys[idx] = stage == 0 ? ustg[g] : rp[g];
-  }
+  cp_async_wait_all();
   __syncthreads();
   __shared__ T mcs[ET * 10];
   __shared__ unsigned char affs[ET];
@@ -698,7 +745,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
             // outward transformed flux at both ends: own F~ (L ends, c = 0) or
             // -partner F~ (R ends)
             const float2 wf = O.wff[ll];
-            const T* fco = fc + ((e0 + lel) * 2 + F0 + fld) * NF + (2 * a) * NFP + ll;
+            const float* fco = fcs + (lel * 2 + fld) * NF + (2 * a) * NFP + ll;
             const T o0 = c0 == (T)0 ? fco[0] : c0, o1 = c1 == (T)0 ? fco[NFP] : c1;
             bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o0));
             bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o1));
@@ -724,8 +771,8 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         const double Te = -((double)sm.x + (double)sm.y);
         const int64_t gt = e0 * 2 + t;
         if (stage == 1) A.tacc[gt] = Te;
-        else if (stage < 4) A.tacc[gt] += 2.0 * Te;
-        else tgt[t] = rkc_el(t / 2).ddt / 6.0 * (A.tacc[gt] + Te);
+        else if (stage < 4) A.tacc[gt] = tas[t] + 2.0 * Te;
+        else tgt[t] = rkc_el(t / 2).ddt / 6.0 * (tas[t] + Te);
       }
     }
     // ---- du/dt and the RK4 register update
@@ -742,19 +789,25 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         continue;
       }
       if (kCons && cons && stage == 4) {
-        // float-float update now, the element's uniform correction below
-        float2* U = reinterpret_cast<float2*>(A.u);
-        const float* Acc = reinterpret_cast<const float*>(A.acc);
-        const float2 u = U[g];
-        const float inc = rkc_el(el).dt6 * (Acc[g] + (float)R);
+        // float-float update now (kept in shared memory), the element's
+        // uniform correction below
+        const float2 u = u2s[idx];
+        const float inc = rkc_el(el).dt6 * (acs[idx] + (float)R);
         const float s2 = u.x + inc;
         const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
         const float hi = s2 + e2;
-        U[g] = make_float2(hi, e2 - (hi - s2));
+        u2s[idx] = make_float2(hi, e2 - (hi - s2));
         ys[idx] = (T)inc;
         continue;
       }
-      const T yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
+      T yt;
+      if constexpr (PRE) {
+        float2 un;
+        yt = rk_apply_v(A, stage, g, R, rkc, u2s[idx], stage >= 2 ? acs[idx] : 0.f, nullptr, &un);
+        if (stage == 4) reinterpret_cast<float2*>(A.u)[g] = un;
+      } else {
+        yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
+      }
       if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
       ustg[g] = yt;
       ys[idx] = yt;
@@ -764,7 +817,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
       // per line: sum of w det J * increment (and of w det J), float-float
       if (lact) {
         const int base = line_base<DIM, N>(0, ll);
-        const float2* wd = A.wdetf + (e0 + lel) * NU + base;
+        const float2* wd = wds + lel * NU + base;
         float2 wsl = make_float2(0.f, 0.f);
 #pragma unroll
         for (int fld = 0; fld < NFLD; ++fld) {
@@ -798,7 +851,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
         const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
         float2* U = reinterpret_cast<float2*>(A.u);
-        const float2 u = U[g];
+        const float2 u = u2s[idx];
         const float dh = dlt[2 * (el * 2 + fld)], dl = dlt[2 * (el * 2 + fld) + 1];
         const float s2 = u.x + dh;
         const float e2 = two_sum_lo(u.x, dh, s2) + (u.y + dl);
