@@ -1,6 +1,7 @@
 // C ABI of libfrpcpf: field life cycle, RK4 march, preconditioning schedule,
 // mass integral and state transfer.  Device memory is a caller-provided
 // workspace; the library never allocates device memory.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -301,7 +302,10 @@ int stage_and_traces(fr_field* f, cudaStream_t s) {
   return FR_OK;
 }
 
-int run_precondition(fr_field* f, cudaStream_t s) {
+// The launch sequence of one preconditioning: reset psi0/psi, traces, then
+// k_max pseudo-time RK4 iterations (iterations after the stop rule holds
+// exit at once on the device).
+int launch_precondition(fr_field* f, cudaStream_t s) {
   CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
   int grid;
   launch_elementwise_grid(f->E * f->nu, &grid);
@@ -320,15 +324,11 @@ int run_precondition(fr_field* f, cudaStream_t s) {
       timed(f, 3, f->ks.ka[1], a, s);
     }
   CK(cudaGetLastError());
-  f->n_precond_done++;
   return FR_OK;
 }
 
-int run_step(fr_field* f, cudaStream_t s) {
-  if (f->nstep > 0 && f->nstep % f->prm.n_precond == 0) {
-    const int rc = run_precondition(f, s);
-    if (rc) return rc;
-  }
+// The launch sequence of one physical RK4 step (the time lives on the device).
+int launch_rk_step(fr_field* f, cudaStream_t s) {
   KArgs a = f->args;
   a.use_dev_time = 1;
   a.dt = f->prm.dt;
@@ -339,9 +339,101 @@ int run_step(fr_field* f, cudaStream_t s) {
     timed(f, 1, f->ks.ka[0], a, s);
   }
   CK(cudaGetLastError());
-  f->nstep++;
   return FR_OK;
 }
+
+bool graphs_on(const fr_field* f) { return f->use_graphs && !f->profiling; }
+
+// Records body(stream) on the field's capture stream and instantiates it.
+// The launch arguments are fixed for the life of a field, so a graph stays
+// valid until the field is destroyed.
+template <typename Body>
+int capture_graph(fr_field* f, cudaGraphExec_t* out, Body body) {
+  if (!f->cap) CK(cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = body(f->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(f->cap, &g);
+  if (rc != FR_OK || ec != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != FR_OK ? rc : FR_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    *out = nullptr;
+    return FR_ECUDA;
+  }
+  return FR_OK;
+}
+
+int run_precondition(fr_field* f, cudaStream_t s) {
+  if (graphs_on(f)) {
+    if (!f->g_pre) {
+      const int rc = capture_graph(f, &f->g_pre, [f](cudaStream_t c) { return launch_precondition(f, c); });
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(f->g_pre, s));
+  } else {
+    const int rc = launch_precondition(f, s);
+    if (rc) return rc;
+  }
+  f->n_precond_done++;
+  return FR_OK;
+}
+
+constexpr int kGraphSteps = 16;  // RK steps per replay of the step graph
+
+// n physical RK steps with no preconditioning due among them.
+int launch_rk_steps(fr_field* f, int n, cudaStream_t s) {
+  if (!graphs_on(f)) {
+    for (int i = 0; i < n; ++i) {
+      const int rc = launch_rk_step(f, s);
+      if (rc) return rc;
+    }
+    return FR_OK;
+  }
+  if (n >= kGraphSteps && !f->g_steps) {
+    const int rc = capture_graph(f, &f->g_steps, [f](cudaStream_t c) {
+      for (int i = 0; i < kGraphSteps; ++i) {
+        const int r = launch_rk_step(f, c);
+        if (r) return r;
+      }
+      return (int)FR_OK;
+    });
+    if (rc) return rc;
+  }
+  if (n % kGraphSteps && !f->g_step1) {
+    const int rc = capture_graph(f, &f->g_step1, [f](cudaStream_t c) { return launch_rk_step(f, c); });
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n / kGraphSteps; ++i) CK(cudaGraphLaunch(f->g_steps, s));
+  for (int i = 0; i < n % kGraphSteps; ++i) CK(cudaGraphLaunch(f->g_step1, s));
+  return FR_OK;
+}
+
+// n_steps physical steps; a preconditioning runs before every step whose
+// index is a positive multiple of n_precond.
+int run_steps(fr_field* f, int n_steps, cudaStream_t s) {
+  const int64_t np = f->prm.n_precond;
+  int done = 0;
+  while (done < n_steps) {
+    if (f->nstep > 0 && f->nstep % np == 0) {
+      const int rc = run_precondition(f, s);
+      if (rc) return rc;
+    }
+    const int64_t next = (f->nstep / np + 1) * np;
+    const int chunk = (int)std::min<int64_t>(n_steps - done, next - f->nstep);
+    const int rc = launch_rk_steps(f, chunk, s);
+    if (rc) return rc;
+    f->nstep += chunk;
+    done += chunk;
+  }
+  return FR_OK;
+}
+
+int run_step(fr_field* f, cudaStream_t s) { return run_steps(f, 1, s); }
 
 }  // namespace
 
@@ -387,6 +479,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return FR_EINVAL;
   KernelSet ks;
   if (!get_kernels(*m, prm->precision, &ks)) return FR_EUNSUPPORTED;
+  if (!ks.prepared) return FR_ECUDA;
   int mg;
   launch_elementwise_grid(m->E * m->nu, &mg);
   const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
@@ -625,11 +718,8 @@ extern "C" int fr_field_init_batch(const fr_mesh* m, const fr_params* prm, int n
 
 extern "C" int fr_step(fr_field* f, int n_steps, void* stream) {
   if (!f || n_steps < 0) return FR_EINVAL;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int n = 0; n < n_steps; ++n) {
-    const int rc = run_step(f, s);
-    if (rc) return rc;
-  }
+  const int rc = run_steps(f, n_steps, reinterpret_cast<cudaStream_t>(stream));
+  if (rc) return rc;
   return f->sticky;
 }
 
@@ -795,6 +885,9 @@ extern "C" int fr_profile_read(fr_field* f, void* stream, double* total_ms, int6
 
 extern "C" void fr_field_destroy(fr_field* f) {
   if (!f) return;
+  for (cudaGraphExec_t g : {f->g_steps, f->g_step1, f->g_pre})
+    if (g) cudaGraphExecDestroy(g);
+  if (f->cap) cudaStreamDestroy(f->cap);
   for (int c = 0; c < 4; ++c)
     for (auto& pr : f->prof[c]) {
       cudaEventDestroy(pr.first);

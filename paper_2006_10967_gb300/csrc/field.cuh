@@ -31,6 +31,12 @@ struct fr_field {
   double* xfer = nullptr;  // E*nu doubles, staging for get/set in the mixed path
   AdjRecord rec;
   frp::ElemPar* ep_region = nullptr;  // per-element parameters (used by batch fields)
+  // CUDA graphs of the launch sequences (captured on a private stream on
+  // first use, replayed on the caller's stream): kGraphSteps RK steps, one
+  // RK step, one preconditioning
+  int use_graphs = 1;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_steps = nullptr, g_step1 = nullptr, g_pre = nullptr;
   // optional per-launch CUDA-event timing: [class] -> (start, stop) pairs
   int profiling = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];

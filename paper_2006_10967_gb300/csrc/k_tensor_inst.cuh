@@ -8,22 +8,12 @@ namespace frp {
 template <int DIM, int N, typename T, int MODE>
 void launch_kb_tensor(const KArgs& A, cudaStream_t s) {
   using LY = KBLayout<DIM, N, T, MODE>;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
-    init = true;
-  }
   launch_kernel(kb_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
 }
 
 template <int DIM, int N, typename T, int MODE>
 void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
   using LY = KALayout<DIM, N, T, MODE>;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
-    init = true;
-  }
   launch_kernel(ka_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
 }
 
@@ -32,8 +22,19 @@ void launch_vcache(const KArgs& A, cudaStream_t s) {
   k_vel_cache<DIM, N, T><<<152 * 8, kThreads, 0, s>>>(A);
 }
 
+// Shared-memory opt-in of one (kb, ka) pair; done when the kernel table is
+// filled, so that no launch (and no graph capture) has to do it.
+template <int DIM, int N, typename T, int MODE>
+bool prepare_tensor() {
+  return cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KBLayout<DIM, N, T, MODE>::SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KALayout<DIM, N, T, MODE>::SMEM) == cudaSuccess;
+}
+
 template <int DIM, int N, typename T>
 void fill_tensor(int64_t E, KernelSet* ks) {
+  ks->prepared = prepare_tensor<DIM, N, T, 0>() && prepare_tensor<DIM, N, T, 1>();
   ks->vcache = launch_vcache<DIM, N, T>;
   ks->kb[0] = launch_kb_tensor<DIM, N, T, 0>;
   ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;

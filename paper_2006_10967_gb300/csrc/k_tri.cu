@@ -7,27 +7,26 @@ namespace frp {
 template <int P, typename T, int MODE>
 void launch_kb_tri(const KArgs& A, cudaStream_t s) {
   using LY = KBTriLayout<P, T, MODE>;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(kb_tri<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
-    init = true;
-  }
   launch_kernel(kb_tri<P, T, MODE>, LY::SMEM, LY::ET, A, s);
 }
 
 template <int P, typename T, int MODE>
 void launch_ka_tri(const KArgs& A, cudaStream_t s) {
   using LY = KATriLayout<P, T, MODE>;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(ka_tri<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
-    init = true;
-  }
   launch_kernel(ka_tri<P, T, MODE>, LY::SMEM, LY::ET, A, s);
+}
+
+template <int P, typename T, int MODE>
+bool prepare_tri() {
+  return cudaFuncSetAttribute(kb_tri<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KBTriLayout<P, T, MODE>::SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(ka_tri<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KATriLayout<P, T, MODE>::SMEM) == cudaSuccess;
 }
 
 template <int P, typename T>
 void fill_tri(int64_t E, KernelSet* ks) {
+  ks->prepared = prepare_tri<P, T, 0>() && prepare_tri<P, T, 1>();
   ks->kb[0] = launch_kb_tri<P, T, 0>;
   ks->kb[1] = launch_kb_tri<P, T, 1>;
   ks->ka[0] = launch_ka_tri<P, T, 0>;

@@ -162,6 +162,18 @@ __host__ __device__ constexpr int warp_tile(int cap, int ln) {
   return (cap / (32 / gcd_(ln, 32))) > 0 ? (cap / (32 / gcd_(ln, 32))) * (32 / gcd_(ln, 32)) : cap;
 }
 
+// Field split: on the physical step (two fields) the line passes give each
+// thread one line of one field, in separate warps, so that twice the warps
+// are in flight; MINB asks the compiler for registers that let MINB blocks
+// share an SM.
+#ifndef FRP_FIELD_SPLIT
+#define FRP_FIELD_SPLIT 0
+#endif
+template <int THREADS, typename T>
+struct MinBlocks {
+  static constexpr int v = sizeof(T) == 8 ? 1 : (1280 / THREADS < 1 ? 1 : (1280 / THREADS > 8 ? 8 : 1280 / THREADS));
+};
+
 template <int DIM, int N, typename T, int MODE>
 struct KBLayout {
   using S = TS<DIM, N>;
@@ -177,7 +189,10 @@ struct KBLayout {
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 57344 / BYTES_EL < 1 ? 1 : 57344 / BYTES_EL;
   static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
-  static constexpr int THREADS = (ET * LN + 31) / 32 * 32;  // whole warps; lines >= ET * LN idle
+  static constexpr int FS = FRP_FIELD_SPLIT ? NFLD : 1;  // fields split across threads
+  static constexpr int LINES = ET * LN;
+  static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
+  static constexpr int MINB = MinBlocks<THREADS, T>::v;
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 12;  // + region alignment
 };
 
@@ -186,10 +201,12 @@ struct KBLayout {
 // thread one solution-point line; the 1D operators are read from the kernel
 // parameters (constant bank) with compile-time indices.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
+__global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<DIM, N, T, MODE>::MINB)
+    kb_tensor(const KArgs A) {
   using S = TS<DIM, N>;
   using LY = KBLayout<DIM, N, T, MODE>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
+  constexpr int FS = LY::FS, NQ = NFLD / FS;  // fields per thread in the line passes
   constexpr int F0 = MODE == 0 ? 0 : 1;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
@@ -231,12 +248,14 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       gfe[el] = A.prm.T > 0.0 ? cpi((T)((ep.t + rk_c(A.stage) * ep.dt) / A.prm.T)) : (T)1;
       epe[el] = (T)ep.eps;
     }
-  const int lel = tid / LN, ll = tid % LN;
-  const bool lact = lel < ne;  // also false on the idle lines of a padded last warp
+  // line-pass role: line (lel, ll) of the fields fsel + q FS, q < NQ
+  const int fsel = tid / LY::LINES, lin = tid % LY::LINES;
+  const int lel = lin / LN, ll = lin % LN;
+  const bool lact = lel < ne && fsel < FS;  // false on the idle lanes of a padded last warp
   // Prefetch this thread's line-end connectivity and partner traces for all
   // axis passes, so that the dependent global loads overlap the tile load.
   int32_t wpre[DIM][2];
-  T opre[DIM][2][NFLD];
+  T opre[DIM][2][NQ];
   if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -259,8 +278,8 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
         const int32_t w = wpre[a][sd];
         const int64_t p = (int64_t)(w >> 1);
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld)
-          opre[a][sd][fld] = (w & 1) ? tr[((p / NF) * 2 + F0 + fld) * NF + p % NF] : (T)0;
+        for (int q = 0; q < NQ; ++q)
+          opre[a][sd][q] = (w & 1) ? tr[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF] : (T)0;
       }
   }
   if (MODE == 1)
@@ -286,18 +305,22 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const int base = line_base<DIM, N>(a, ll);
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
       const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
-      lm[lel * NF + k0] = (unsigned char)(w0 & 1);
-      lm[lel * NF + k1] = (unsigned char)(w1 & 1);
-      // L points go to the compacted list of Step 5; R points get no flux here
-      if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k0);
-      if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k1);
+      if (fsel == 0) {
+        lm[lel * NF + k0] = (unsigned char)(w0 & 1);
+        lm[lel * NF + k1] = (unsigned char)(w1 & 1);
+        // L points go to the compacted list of Step 5; R points get no flux here
+        if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k0);
+        if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k1);
+      }
 #pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld) {
+      for (int q = 0; q < NQ; ++q) {
+        const int fld = fsel + q * FS;
         if (!(w0 & 1)) cor[(lel * NFLD + fld) * NF + k0] = 0;
         if (!(w1 & 1)) cor[(lel * NFLD + fld) * NF + k1] = 0;
       }
 #pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld) {
+      for (int q = 0; q < NQ; ++q) {
+        const int fld = fsel + q * FS;
         const T* ul = us + (lel * NFLD + fld) * NU + base;
         T v[N];
 #pragma unroll
@@ -308,8 +331,8 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           f0 += O.lend[0][j] * v[j];
           f1 += O.lend[1][j] * v[j];
         }
-        const T o0 = (w0 & 1) ? opre[a][0][fld] : f0;
-        const T o1 = (w1 & 1) ? opre[a][1][fld] : f1;
+        const T o0 = (w0 & 1) ? opre[a][0][q] : f0;
+        const T o1 = (w1 & 1) ? opre[a][1][q] : f1;
         const int fo = (lel * NFLD + fld) * NF;
         uo[fo + k0] = o0;
         uo[fo + k1] = o1;
@@ -347,17 +370,17 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
           upt_xi<DIM, N>(i, O.x, xi);
           const T rdj = (T)1 / metric_c<DIM>(gs + lel * NG, xi, Sm, affs[lel], mcs + lel * 10);
 #pragma unroll
-          for (int fld = 0; fld < NFLD; ++fld) {
-            T* q = qt + (lel * NFLD + fld) * DIM * NU + i;
+          for (int q = 0; q < NQ; ++q) {
+            T* qp = qt + (lel * NFLD + fsel + q * FS) * DIM * NU + i;
             T qv[3];
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) qv[c] = q[c * NU];
+            for (int c = 0; c < DIM; ++c) qv[c] = qp[c * NU];
 #pragma unroll
             for (int b = 0; b < DIM; ++b) {
               T r = 0;
 #pragma unroll
               for (int c = 0; c < DIM; ++c) r += Sm[c][b] * qv[c];
-              q[b * NU] = r * rdj;
+              qp[b * NU] = r * rdj;
             }
           }
         }
@@ -571,7 +594,8 @@ __global__ void __launch_bounds__(256) kb_tensor(const KArgs A) {
       const int base = line_base<DIM, N>(a, ll);
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
 #pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld) {
+      for (int q = 0; q < NQ; ++q) {
+        const int fld = fsel + q * FS;
         const T* fl = qt + ((lel * NFLD + fld) * DIM + a) * NU + base;
         T v[N];
 #pragma unroll
@@ -620,7 +644,10 @@ struct KALayout {
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
   static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
-  static constexpr int THREADS = (ET * LN + 31) / 32 * 32;  // whole warps; lines >= ET * LN idle
+  static constexpr int FS = FRP_FIELD_SPLIT ? NFLD : 1;  // fields split across threads
+  static constexpr int LINES = ET * LN;
+  static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
+  static constexpr int MINB = MinBlocks<THREADS, T>::v;
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 8;  // + region alignment
 };
 
@@ -628,10 +655,12 @@ struct KALayout {
 // as in kb_tensor.  stage -1 writes du/dt to A.out (fp64) and leaves the
 // state alone; stage 0 only recomputes the traces of ustg.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
+__global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<DIM, N, T, MODE>::MINB)
+    ka_tensor(const KArgs A) {
   using S = TS<DIM, N>;
   using LY = KALayout<DIM, N, T, MODE>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
+  constexpr int FS = LY::FS, NQ = NFLD / FS;
   constexpr int F0 = MODE == 0 ? 0 : 1;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
@@ -656,14 +685,16 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   const int tid = threadIdx.x;
   const int stage = A.stage;
   const TensorOpsT<T>& O = bulk<T>(A).ops;
-  const int lel = tid / LN, ll = tid % LN;
-  const bool lact = lel < ne;  // also false on the idle lines of a padded last warp
+  // line-pass role: line (lel, ll) of the fields fsel + q FS, q < NQ
+  const int fsel = tid / LY::LINES, lin = tid % LY::LINES;
+  const int lel = lin / LN, ll = lin % LN;
+  const bool lact = lel < ne && fsel < FS;  // false on the idle lanes of a padded last warp
 
   // prefetch the partner fluxes of this line's R ends (0 on L ends) and, for
   // the mixed path's flux balance, this element's own L-end fluxes
   constexpr bool kCons = sizeof(T) == 4 && MODE == 0;
   const bool cons = kCons && A.tacc != nullptr && stage >= 1;
-  T fpre[DIM][2][NFLD];
+  T fpre[DIM][2][NQ];
   int32_t wpre[DIM][2];
   if (stage != 0 && lact) {
 #pragma unroll
@@ -699,9 +730,8 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         const int32_t w = wpre[a][sd];
         const int64_t p = (int64_t)(w >> 1);
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld) {
-          fpre[a][sd][fld] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fld) * NF + p % NF];
-        }
+        for (int q = 0; q < NQ; ++q)
+          fpre[a][sd][q] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF];
       }
   }
   cp_async_wait_all();
@@ -730,25 +760,26 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
   if (stage != 0) {
     // ---- lift of the R-side common fluxes: minus L's transformed flux, one
     //      pass per axis
-    float2 bal[NFLD];
+    float2 bal[NQ];
 #pragma unroll
-    for (int fld = 0; fld < NFLD; ++fld) bal[fld] = make_float2(0.f, 0.f);
+    for (int q = 0; q < NQ; ++q) bal[q] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (lact) {
         const int st = ipow(N, a);
         const int base = line_base<DIM, N>(a, ll);
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld) {
-          const T c0 = -fpre[a][0][fld], c1 = -fpre[a][1][fld];
+        for (int q = 0; q < NQ; ++q) {
+          const int fld = fsel + q * FS;
+          const T c0 = -fpre[a][0][q], c1 = -fpre[a][1][q];
           if (cons) {
             // outward transformed flux at both ends: own F~ (L ends, c = 0) or
             // -partner F~ (R ends)
             const float2 wf = O.wff[ll];
             const float* fco = fcs + (lel * 2 + fld) * NF + (2 * a) * NFP + ll;
             const T o0 = c0 == (T)0 ? fco[0] : c0, o1 = c1 == (T)0 ? fco[NFP] : c1;
-            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o0));
-            bal[fld] = ff_add(bal[fld], ff_mul(wf, (float)o1));
+            bal[q] = ff_add(bal[q], ff_mul(wf, (float)o0));
+            bal[q] = ff_add(bal[q], ff_mul(wf, (float)o1));
           }
           if (c0 == (T)0 && c1 == (T)0) continue;
           T* yl = ys + (lel * NFLD + fld) * NU + base;
@@ -761,7 +792,7 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
     if (cons) {
       if (lact)
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld) fb[(lel * 2 + fld) * LN + ll] = bal[fld];
+        for (int q = 0; q < NQ; ++q) fb[(lel * 2 + fsel + q * FS) * LN + ll] = bal[q];
       __syncthreads();
       // element mass rate = -sum_k w_f F~_out,k, accumulated with the RK4
       // weights; stage 4 turns it into the step's target mass change
@@ -820,17 +851,18 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
         const float2* wd = wds + lel * NU + base;
         float2 wsl = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int fld = 0; fld < NFLD; ++fld) {
+        for (int q = 0; q < NQ; ++q) {
+          const int fld = fsel + q * FS;
           float2 sl = make_float2(0.f, 0.f);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
             const float2 w2 = wd[j];
             sl = ff_add(sl, ff_mul(w2, (float)ys[(lel * NFLD + fld) * NU + base + j]));
-            if (fld == 0) wsl = ff_add(wsl, w2);
+            if (q == 0) wsl = ff_add(wsl, w2);
           }
           fb[(lel * 2 + fld) * LN + ll] = sl;
         }
-        wb[lel * LN + ll] = wsl;
+        if (fsel == 0) wb[lel * LN + ll] = wsl;
       }
       __syncthreads();
       for (int t = tid; t < 2 * ne; t += blockDim.x) {
@@ -872,7 +904,8 @@ __global__ void __launch_bounds__(256) ka_tensor(const KArgs A) {
       const int base = line_base<DIM, N>(a, ll);
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
 #pragma unroll
-      for (int fld = 0; fld < NFLD; ++fld) {
+      for (int q = 0; q < NQ; ++q) {
+        const int fld = fsel + q * FS;
         const T* yl = ys + (lel * NFLD + fld) * NU + base;
         T t0 = 0, t1 = 0;
 #pragma unroll

@@ -153,6 +153,28 @@ def test_rk_steps_and_preconditioning_parity_fp64(G, case):
     assert st["t"] == pytest.approx(sol.t, rel=1e-15)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(G, precision):
+    """fr_step replays captured CUDA graphs (16-step chunks, single steps, the
+    preconditioning sequence); with profiling on it launches every kernel
+    directly.  Both must produce the same bits, preconditionings included."""
+    w = CASES["quad_periodic_jitter_p3"]()
+    w.n_precond = 10
+    w.pseudo_kmax = 3
+    _, Fg = _pair(G, w, precision=precision, precondition=True)
+    _, Fd = _pair(G, w, precision=precision, precondition=True)
+    Fd.profile(True)
+    for n in (37, 5):
+        Fg.step(n)
+        Fd.step(n)
+    for which in (0, 1, 2):
+        assert np.array_equal(Fg.get(which), Fd.get(which)), which
+    sg, sd = Fg.stats(), Fd.stats()
+    assert sg["n_steps"] == sd["n_steps"] == 42
+    assert sg["n_preconditions"] == sd["n_preconditions"] == 5
+    assert sg["t"] == sd["t"]
+
+
 def test_pseudo_stop_rule_matches_oracle(G):
     w = CASES["quad_periodic_jitter_p3"]()
     w.pseudo_kmax = 20
