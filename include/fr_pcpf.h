@@ -313,6 +313,16 @@ int fr_adjoint_step(fr_field* field, const double* dJ_dphiT, const double* dJ_dp
 int fr_profile(fr_field* field, int enable);
 int fr_profile_read(fr_field* field, void* stream, double* total_ms, int64_t* launches);
 
+/* Steady-state duration of one kernel class (not part of the method): n
+ * back-to-back launches of the class on the field's current state, replayed
+ * as one CUDA graph on `stream` after one untimed replay, bracketed by CUDA
+ * events; *ms_per_launch receives the mean milliseconds per launch.  kernel 0
+ * is the physical residual + common flux kernel (Steps 1-6 of Section 3.1) at
+ * RK stage 1.  The state is unchanged; the partial residual and common-flux
+ * scratch is overwritten (every step rewrites it).  FR_EINVAL for another
+ * class, n < 1 or a NULL pointer.  Synchronises `stream`. */
+int fr_profile_kernel(fr_field* field, int kernel, int n, void* stream, double* ms_per_launch);
+
 void fr_field_destroy(fr_field* field);
 
 const char* fr_strerror(int code);

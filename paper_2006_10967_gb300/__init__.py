@@ -293,6 +293,14 @@ class Field:
         names = ("kb_phys", "ka_phys", "kb_pseudo", "ka_pseudo")
         return {k: (ms[i], n[i]) for i, k in enumerate(names)}
 
+    def profile_kernel(self, kernel=0, n=400, stream=None):
+        """Mean milliseconds per launch of kernel class `kernel` (0: physical
+        residual + common flux), n launches replayed as one CUDA graph."""
+        ms = C.c_double()
+        check(lib().fr_profile_kernel(self.handle, int(kernel), int(n), self._stream(stream), C.byref(ms)),
+              "fr_profile_kernel")
+        return ms.value
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

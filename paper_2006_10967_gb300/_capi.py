@@ -94,6 +94,7 @@ _SIGS = {
     "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fr_profile": (C.c_int, [_vp, C.c_int]),
     "fr_profile_read": (C.c_int, [_vp, _vp, _dp, C.POINTER(C.c_int64)]),
+    "fr_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _dp]),
     "fr_field_destroy": (None, [_vp]),
     "fr_strerror": (C.c_char_p, [C.c_int]),
     "fr_version": (C.c_int, []),

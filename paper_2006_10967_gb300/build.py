@@ -21,6 +21,11 @@ NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC"]
 
 CU = ["api.cu", "k_quad.cu", "k_hex.cu", "k_tri.cu", "noalloc.cu", "adjoint.cu"]
+# The residual/update kernels' float arithmetic (the mixed path) uses the
+# approximate reciprocal, division and square root (2 ulp) and flushes
+# denormals; FP64 arithmetic is unaffected by these flags.
+FAST_FLOAT = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FAST_FLOAT_TU = {"k_quad.cu", "k_hex.cu", "k_tri.cu"}
 CPP = ["mesh.cpp", "refel.cpp"]
 
 
@@ -43,7 +48,8 @@ def stale():
 def _compile(src):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
-        cmd = [NVCC] + NVFLAGS + ["-c", src, "-o", obj]
+        extra = FAST_FLOAT if os.path.basename(src) in FAST_FLOAT_TU else []
+        cmd = [NVCC] + NVFLAGS + extra + ["-c", src, "-o", obj]
     else:
         cmd = ["g++"] + CXXFLAGS + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

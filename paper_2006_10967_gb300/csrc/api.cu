@@ -18,7 +18,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf, ep;
+  size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf, ep, mcg;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t total;
 };
@@ -132,6 +132,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   L.tacc = take(E * 2 * sizeof(double));
   L.wdetf = take(E * NU * 2 * sizeof(float));
   L.ep = take(E * sizeof(ElemPar));
+  L.mcg = m.etype != FR_TRI ? take(E * 12 * tb) : 0;  // per-element metric records
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -344,6 +345,15 @@ int launch_rk_step(fr_field* f, cudaStream_t s) {
 
 bool graphs_on(const fr_field* f) { return f->use_graphs && !f->profiling; }
 
+// Releases the captured graphs (they hold the launch arguments by value).
+void drop_graphs(fr_field* f) {
+  for (cudaGraphExec_t* g : {&f->g_steps, &f->g_step1, &f->g_pre})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+}
+
 // Records body(stream) on the field's capture stream and instantiates it.
 // The launch arguments are fixed for the life of a field, so a graph stays
 // valid until the field is destroyed.
@@ -545,6 +555,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.tacc = (prm->precision == FR_MIXED && m->etype != FR_TRI) ? reinterpret_cast<double*>(b + L.tacc) : nullptr;
   A.wdetf = reinterpret_cast<const float2*>(b + L.wdetf);
   A.ep = nullptr;
+  A.mcg = L.mcg ? b + L.mcg : nullptr;
   f->ep_region = reinterpret_cast<ElemPar*>(b + L.ep);
   A.out = nullptr;
   A.stage = 0;
@@ -621,6 +632,10 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   if (err == FR_OK && cudaMemsetAsync(b + L.dstate, 0, DS_WORDS * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaMemsetAsync(b + L.acc, 0, m->E * 2 * m->nu * sizeof(double), s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaMemsetAsync(b + L.fc, 0, L.psi0 - L.fc, s) != cudaSuccess) err = FR_ECUDA;
+  if (err == FR_OK && A.mcg) {
+    if (!f->ks.mconst) err = FR_EUNSUPPORTED;
+    else f->ks.mconst(A, s);
+  }
   if (err == FR_OK && A.vsu) {
     if (!f->ks.vcache) err = FR_EUNSUPPORTED;
     else f->ks.vcache(A, s);
@@ -630,7 +645,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   if (err == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaGetLastError() != cudaSuccess) err = FR_ECUDA;
   if (err != FR_OK) {
-    delete f;
+    fr_field_destroy(f);
     return err;
   }
   err = read_status(f, s);
@@ -699,17 +714,18 @@ extern "C" int fr_field_init_batch(const fr_mesh* m, const fr_params* prm, int n
   }
   if (cudaMemcpyAsync(f->ep_region, ep.data(), ep.size() * sizeof(ElemPar), cudaMemcpyHostToDevice, s) !=
       cudaSuccess) {
-    delete f;
+    fr_field_destroy(f);
     return FR_ECUDA;
   }
   f->args.ep = f->ep_region;
+  drop_graphs(f);  // the launch arguments changed
   // the batch's pseudo step for the launch arguments is per element; keep a positive value
   rc = FR_OK;
   if (precondition) rc = run_precondition(f, s);
   if (rc == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FR_ECUDA;
   if (rc == FR_OK) rc = read_status(f, s);
   if (rc != FR_OK && rc != FR_ENONFINITE) {
-    delete f;
+    fr_field_destroy(f);
     return rc;
   }
   *out = f;
@@ -883,10 +899,40 @@ extern "C" int fr_profile_read(fr_field* f, void* stream, double* total_ms, int6
   return FR_OK;
 }
 
+extern "C" int fr_profile_kernel(fr_field* f, int kernel, int n, void* stream, double* ms_per_launch) {
+  if (!f || !ms_per_launch || kernel != 0 || n < 1) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KArgs a = f->args;
+  a.use_dev_time = 1;
+  a.dt = f->prm.dt;
+  a.rk = rk_const(a.dt);
+  a.stage = 1;
+  cudaGraphExec_t ge = nullptr;
+  int rc = capture_graph(f, &ge, [&](cudaStream_t c) {
+    for (int i = 0; i < n; ++i) f->ks.kb[0](a, c);
+    CK(cudaGetLastError());
+    return (int)FR_OK;
+  });
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  rc = FR_ECUDA;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+      cudaGraphLaunch(ge, s) == cudaSuccess && cudaEventRecord(e0, s) == cudaSuccess &&
+      cudaGraphLaunch(ge, s) == cudaSuccess && cudaEventRecord(e1, s) == cudaSuccess &&
+      cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+    *ms_per_launch = (double)ms / n;
+    rc = FR_OK;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  return rc;
+}
+
 extern "C" void fr_field_destroy(fr_field* f) {
   if (!f) return;
-  for (cudaGraphExec_t g : {f->g_steps, f->g_step1, f->g_pre})
-    if (g) cudaGraphExecDestroy(g);
+  drop_graphs(f);
   if (f->cap) cudaStreamDestroy(f->cap);
   for (int c = 0; c < 4; ++c)
     for (auto& pr : f->prof[c]) {

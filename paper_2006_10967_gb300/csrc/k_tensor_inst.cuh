@@ -18,6 +18,12 @@ void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
 }
 
 template <int DIM, int N, typename T>
+void launch_mconst(const KArgs& A, cudaStream_t s) {
+  const int64_t g = (A.E + kThreads - 1) / kThreads;
+  k_metric_const<DIM, T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kThreads, 0, s>>>(A, TS<DIM, N>::NG);
+}
+
+template <int DIM, int N, typename T>
 void launch_vcache(const KArgs& A, cudaStream_t s) {
   k_vel_cache<DIM, N, T><<<152 * 8, kThreads, 0, s>>>(A);
 }
@@ -36,6 +42,7 @@ template <int DIM, int N, typename T>
 void fill_tensor(int64_t E, KernelSet* ks) {
   ks->prepared = prepare_tensor<DIM, N, T, 0>() && prepare_tensor<DIM, N, T, 1>();
   ks->vcache = launch_vcache<DIM, N, T>;
+  ks->mconst = launch_mconst<DIM, N, T>;
   ks->kb[0] = launch_kb_tensor<DIM, N, T, 0>;
   ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;
   ks->ka[0] = launch_ka_tensor<DIM, N, T, 0>;

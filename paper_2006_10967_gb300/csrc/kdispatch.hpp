@@ -13,6 +13,7 @@ struct KernelSet {
   LaunchFn ka[2] = {nullptr, nullptr};
   int max_blocks = 0;                   // upper bound on blocks of any launch (per element count)
   LaunchFn vcache = nullptr;            // fills the spatial velocity cache (nullptr: not supported)
+  LaunchFn mconst = nullptr;            // fills the per-element metric records (tensor elements)
   bool prepared = false;                // shared-memory limits set for every kernel of the set
 };
 

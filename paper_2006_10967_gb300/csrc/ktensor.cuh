@@ -112,31 +112,43 @@ __device__ __forceinline__ bool is_affine(const T* g) {
   return aff;
 }
 
+// Metric terms at xi: from the element's precomputed record when the element
+// is affine (mc: adj J row-major, det J, 1/det J, affine flag; see
+// k_metric_const), else from its geometry.  Returns det J; rdj, when given,
+// receives 1/det J.
+constexpr int kMetricRec = 12;
 template <int DIM, typename T>
-__device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], bool aff, const T* mc) {
-  if (aff) {
+__device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], const T* mc, T* rdj = nullptr) {
+  if (mc[11] != (T)0) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int b = 0; b < DIM; ++b) S[a][b] = mc[a * 3 + b];
+    if (rdj) *rdj = mc[10];
     return mc[9];
   }
-  return metric<DIM>(g, xi, S);
+  const T dj = metric<DIM>(g, xi, S);
+  if (rdj) *rdj = (T)1 / dj;
+  return dj;
 }
 
+// Per-element metric record (kMetricRec values of the bulk type), computed
+// once per field from the element geometry: the metric at the reference
+// centre, its determinant and reciprocal, and whether the map is affine
+// (then the record holds the metric everywhere in the element).
 template <int DIM, typename T>
-__device__ __forceinline__ void fill_affine(const T* gs, int ne, int NG, unsigned char* aff, T* mc) {
-  for (int el = threadIdx.x; el < ne; el += blockDim.x) {
-    const T* g = gs + el * NG;
-    const bool a = is_affine<DIM>(g);
-    aff[el] = a;
-    if (a) {
-      T xi[3] = {0, 0, 0}, S[3][3];
-      const T dj = metric<DIM>(g, xi, S);
-      for (int p = 0; p < 3; ++p)
-        for (int q = 0; q < 3; ++q) mc[el * 10 + p * 3 + q] = (p < DIM && q < DIM) ? S[p][q] : (T)0;
-      mc[el * 10 + 9] = dj;
-    }
+__global__ void k_metric_const(const KArgs A, int NG) {
+  T* mc = reinterpret_cast<T*>(A.mcg);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const T* g = geo_of<T>(A) + e * NG;
+    T xi[3] = {0, 0, 0}, S[3][3];
+    const T dj = metric<DIM>(g, xi, S);
+    T* o = mc + e * kMetricRec;
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) o[p * 3 + q] = (p < DIM && q < DIM) ? S[p][q] : (T)0;
+    o[9] = dj;
+    o[10] = (T)1 / dj;
+    o[11] = is_affine<DIM>(g) ? (T)1 : (T)0;
   }
 }
 
@@ -182,7 +194,7 @@ struct KBLayout {
   static constexpr int PER_EL_T = NFLD * S::NU          // u, later the divergence
                                   + NFLD * DIM * S::NU  // q~ -> q -> f~
                                   + 2 * NFLD * S::NF    // uo, cor
-                                  + S::NG               // geometry
+                                  + S::NG + kMetricRec  // geometry, metric record
                                   + (MODE == 0 ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
@@ -193,7 +205,7 @@ struct KBLayout {
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
   static constexpr int MINB = MinBlocks<THREADS, T>::v;
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 12;  // + region alignment
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 13;  // + region alignment
 };
 
 // ============================================================================
@@ -217,6 +229,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   T* uo = sc.take<T>(ET * NFLD * NF);         // [ET][NFLD][NF] partner traces (own trace at R points)
   T* cor = sc.take<T>(ET * NFLD * NF);        // [ET][NFLD][NF]
   T* gs = sc.take<T>(ET * NG);                // [ET][NG]
+  T* mcs = sc.take<T>(ET * kMetricRec);       // [ET][kMetricRec] metric records
   T* vu = sc.take<T>(MODE == 0 ? ET * DIM * NU : 0);  // MODE 0: velocity cache, solution points
   T* vf = sc.take<T>(MODE == 0 ? ET * DIM * NF : 0);  // MODE 0: velocity cache, flux points
   T* chi = sc.take<T>(MODE == 1 ? ET * 2 * NU : 0);   // MODE 1: [ET][2][NU]
@@ -266,6 +279,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   // flight together with the connectivity loads above
   if (MODE == 0) tile_async(us, ustg + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
   tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
+  tile_async(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne * kMetricRec * (int)sizeof(T));
   if (MODE == 0 && A.vsu)
     tile_async(vu, reinterpret_cast<const T*>(A.vsu) + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
   if (MODE == 0 && A.vsf)
@@ -288,10 +302,6 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       us[idx] = ustg[((e0 + el) * 2 + F0) * NU + i];
     }
   cp_async_wait_all();
-  __syncthreads();
-  __shared__ T mcs[ET * 10];
-  __shared__ unsigned char affs[ET];
-  fill_affine<DIM, T>(gs, ne, NG, affs, mcs);
   __syncthreads();
   const T gfac = gfac_s;
 
@@ -368,7 +378,8 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
           const int i = base + j * st;
           T xi[3], Sm[3][3];
           upt_xi<DIM, N>(i, O.x, xi);
-          const T rdj = (T)1 / metric_c<DIM>(gs + lel * NG, xi, Sm, affs[lel], mcs + lel * 10);
+          T rdj;
+          metric_c<DIM>(gs + lel * NG, xi, Sm, mcs + lel * kMetricRec, &rdj);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             T* qp = qt + (lel * NFLD + fsel + q * FS) * DIM * NU + i;
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     fline<DIM, N>(k, a, s, b0);
     T xi[3], Sm[3][3];
     fpt_xi<DIM, N>(k, O.x, xi);
-    metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
+    metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec);
     const T sg = s ? (T)1 : (T)-1;
     T pn[3], pm = 0;
 #pragma unroll
@@ -520,7 +531,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
     upt_xi<DIM, N>(i, O.x, xi);
-    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
+    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec);
     if (MODE == 0) {
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
@@ -639,7 +650,7 @@ struct KALayout {
   // mixed path: float-float state, accumulator, w det J, own fluxes and the
   // step's mass-balance accumulator staged in shared memory as well
   static constexpr bool PRE = sizeof(T) == 4 && MODE == 0;
-  static constexpr int BYTES_EL = (NFLD * S::NU + S::NG) * (int)sizeof(T) +
+  static constexpr int BYTES_EL = (NFLD * S::NU + S::NG + kMetricRec) * (int)sizeof(T) +
                                   (PRE ? 2 * S::NU * 8 + 2 * S::NU * 4 + S::NU * 8 + 2 * S::NF * 4 + 16 : 0);
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
@@ -648,7 +659,7 @@ struct KALayout {
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
   static constexpr int MINB = MinBlocks<THREADS, T>::v;
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 8;  // + region alignment
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 9;  // + region alignment
 };
 
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
@@ -670,6 +681,7 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   SmemCarve sc{smem_raw};
   T* ys = sc.take<T>(ET * NFLD * NU);  // [ET][NFLD][NU]
   T* gs = sc.take<T>(ET * NG);         // [ET][NG]
+  T* mcs = sc.take<T>(ET * kMetricRec);  // metric records
   float2* u2s = sc.take<float2>(PRE ? ET * 2 * NU : 0);  // float-float state, tile order
   float* acs = sc.take<float>(PRE ? ET * 2 * NU : 0);    // RK accumulator
   float2* wds = sc.take<float2>(PRE ? ET * NU : 0);      // w det J (float-float)
@@ -712,7 +724,10 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
       ys[idx] = stage == 0 ? ustg[g] : rp[g];
     }
   }
-  if (stage != 0) tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
+  if (stage != 0) {
+    tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
+    tile_async(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne * kMetricRec * (int)sizeof(T));
+  }
   if (PRE && stage >= 1) {
     tile_async(u2s, reinterpret_cast<const float2*>(A.u) + e0 * 2 * NU, ne * 2 * NU * 8);
     if (stage >= 2) tile_async(acs, reinterpret_cast<const float*>(A.acc) + e0 * 2 * NU, ne * 2 * NU * 4);
@@ -736,12 +751,6 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   }
   cp_async_wait_all();
   __syncthreads();
-  __shared__ T mcs[ET * 10];
-  __shared__ unsigned char affs[ET];
-  if (stage != 0) {
-    fill_affine<DIM, T>(gs, ne, NG, affs, mcs);
-    __syncthreads();
-  }
 
   double sq = 0.0;
   // RK constants: one set, or one per element for batched instances
@@ -812,8 +821,9 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
       const RKConstF& rkc = rkc_el(el);
       T xi[3], Sm[3][3];
       upt_xi<DIM, N>(i, O.x, xi);
-      const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, affs[el], mcs + el * 10);
-      const T R = -ys[idx] / dj;
+      T rdj;
+      metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec, &rdj);
+      const T R = -ys[idx] * rdj;
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
         A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;

@@ -175,6 +175,23 @@ def test_graph_replay_matches_direct_launches(G, precision):
     assert sg["t"] == sd["t"]
 
 
+def test_profile_kernel_leaves_the_state(G):
+    """fr_profile_kernel replays residual launches on the current state: the
+    march that follows is bit-identical to one without it."""
+    w = CASES["quad_periodic_jitter_p3"]()
+    _, Fa = _pair(G, w, precision="mixed")
+    _, Fb = _pair(G, w, precision="mixed")
+    Fa.step(3)
+    Fb.step(3)
+    assert Fa.profile_kernel(0, 10) > 0.0
+    Fa.step(3)
+    Fb.step(3)
+    for which in (0, 1):
+        assert np.array_equal(Fa.get(which), Fb.get(which))
+    with pytest.raises(G.FRError):
+        Fa.profile_kernel(1, 10)
+
+
 def test_pseudo_stop_rule_matches_oracle(G):
     w = CASES["quad_periodic_jitter_p3"]()
     w.pseudo_kmax = 20
