@@ -132,7 +132,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   L.tacc = take(E * 2 * sizeof(double));
   L.wdetf = take(E * NU * 2 * sizeof(float));
   L.ep = take(E * sizeof(ElemPar));
-  L.mcg = m.etype != FR_TRI ? take(E * 12 * tb) : 0;  // per-element metric records
+  L.mcg = m.etype != FR_TRI ? take(E * kMetricRec * tb) : 0;  // per-element metric records
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -575,6 +575,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.prm.pseudo_tol = prm->pseudo_tol;
   A.prm.pseudo_fixed = prm->pseudo_fixed;
   A.prm.T = prm->vel.T;
+  A.prm.rT = prm->vel.T > 0.0 ? 1.0 / prm->vel.T : 0.0;
   fill_bulk<double>(prm, m, A.cd);
   fill_bulk<float>(prm, m, A.cf);
 
@@ -701,6 +702,8 @@ extern "C" int fr_field_init_batch(const fr_mesh* m, const fr_params* prm, int n
       ep[e].t = 0.0;
       ep[e].eps = I.eps;
       ep[e].nu_max = I.nu_max;
+      ep[e].rk = rk_const(I.dt);
+      ep[e].rkp = rk_const(I.pseudo_dtau > 0.0 ? I.pseudo_dtau : I.dt);
     }
     // this instance's velocity factor at its points
     KArgs a = f->args;

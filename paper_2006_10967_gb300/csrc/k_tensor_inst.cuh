@@ -20,7 +20,7 @@ void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
 template <int DIM, int N, typename T>
 void launch_mconst(const KArgs& A, cudaStream_t s) {
   const int64_t g = (A.E + kThreads - 1) / kThreads;
-  k_metric_const<DIM, T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kThreads, 0, s>>>(A, TS<DIM, N>::NG);
+  k_metric_const<DIM, T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kThreads, 0, s>>>(A, TS<DIM, N>::NG, TS<DIM, N>::NU);
 }
 
 template <int DIM, int N, typename T>

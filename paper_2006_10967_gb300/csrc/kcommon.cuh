@@ -36,7 +36,8 @@ struct PrmT {
 struct PhysPrm {
   double gamma, eps, tau, tau_psi, tau_pseudo, delta, s0, kappa, nu_max, pseudo_tol;
   int pseudo_fixed;
-  double T;  // period of the velocity time factor (<= 0: none)
+  double T;   // period of the velocity time factor (<= 0: none)
+  double rT;  // 1 / T (0 when T <= 0)
 };
 
 // 1D tensor operators; kernels stage them into shared memory.
@@ -71,9 +72,12 @@ struct TriOpsT {
 
 // RK4 step constants (filled on the host for uniform fields; per element for
 // batched instances)
+// Values per element in the tensor kernels' metric records (bulk type).
+constexpr int kMetricRec = 16;
+
 struct RKConstF {
   float half_dt, dt, dt6;
-  double rdt, ddt;
+  double rdt, ddt, ddt6;
 };
 
 __host__ __device__ __forceinline__ RKConstF rk_const(double dt) {
@@ -83,6 +87,7 @@ __host__ __device__ __forceinline__ RKConstF rk_const(double dt) {
   c.dt6 = (float)(dt / 6.0);
   c.rdt = 1.0 / dt;
   c.ddt = dt;
+  c.ddt6 = dt / 6.0;
   return c;
 }
 
@@ -92,6 +97,7 @@ struct ElemPar {
   double dt, dtau;  // physical and pseudo time steps
   double t;         // physical time at the start of the current step
   double eps, nu_max;
+  RKConstF rk, rkp;  // RK4 constants of dt and dtau
 };
 
 struct KArgs {
@@ -142,6 +148,16 @@ template <> __device__ __forceinline__ const float* geo_of<float>(const KArgs& A
 // Time factor g(t) = cos(pi t / T) of the modulated velocity fields, in double.
 __device__ __forceinline__ double time_factor(const KArgs& A, double t) {
   return A.prm.T > 0.0 ? cospi(t / A.prm.T) : 1.0;
+}
+// The bulk-precision time factor: the FP64 path as above; the float path
+// evaluates cos(pi t / T) in float from t / T rounded to float (the time
+// itself stays FP64), which keeps the slow FP64 pipe out of the kernels.
+template <typename T> __device__ __forceinline__ T time_factor_t(const KArgs& A, double t);
+template <> __device__ __forceinline__ double time_factor_t<double>(const KArgs& A, double t) {
+  return time_factor(A, t);
+}
+template <> __device__ __forceinline__ float time_factor_t<float>(const KArgs& A, double t) {
+  return A.prm.T > 0.0 ? cospif((float)(t * A.prm.rT)) : 1.0f;
 }
 
 // ---------------------------------------------------------------------------

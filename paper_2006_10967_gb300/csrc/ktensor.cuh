@@ -113,10 +113,9 @@ __device__ __forceinline__ bool is_affine(const T* g) {
 }
 
 // Metric terms at xi: from the element's precomputed record when the element
-// is affine (mc: adj J row-major, det J, 1/det J, affine flag; see
+// is affine (mc: adj J row-major, det J, 1/det J, affine flag, ...; see
 // k_metric_const), else from its geometry.  Returns det J; rdj, when given,
 // receives 1/det J.
-constexpr int kMetricRec = 12;
 template <int DIM, typename T>
 __device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], const T* mc, T* rdj = nullptr) {
   if (mc[11] != (T)0) {
@@ -133,11 +132,13 @@ __device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], const 
 }
 
 // Per-element metric record (kMetricRec values of the bulk type), computed
-// once per field from the element geometry: the metric at the reference
-// centre, its determinant and reciprocal, and whether the map is affine
-// (then the record holds the metric everywhere in the element).
+// once per field from the element geometry: [0..8] the metric at the
+// reference centre, [9] its determinant, [10] the reciprocal, [11] whether
+// the map is affine (then [0..10] hold everywhere in the element), [12..13]
+// 1/W with W = sum_i w_i det J_i the element's quadrature area (FP64 value
+// split into two bulk-type parts).
 template <int DIM, typename T>
-__global__ void k_metric_const(const KArgs A, int NG) {
+__global__ void k_metric_const(const KArgs A, int NG, int NU) {
   T* mc = reinterpret_cast<T*>(A.mcg);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.E; e += (int64_t)gridDim.x * blockDim.x) {
     const T* g = geo_of<T>(A) + e * NG;
@@ -149,6 +150,12 @@ __global__ void k_metric_const(const KArgs A, int NG) {
     o[9] = dj;
     o[10] = (T)1 / dj;
     o[11] = is_affine<DIM>(g) ? (T)1 : (T)0;
+    double W = 0.0;
+    for (int i = 0; i < NU; ++i) W += A.wdet[e * NU + i];
+    const double rW = 1.0 / W;
+    o[12] = (T)rW;
+    o[13] = (T)(rW - (double)o[12]);
+    o[14] = o[15] = (T)0;
   }
 }
 
@@ -253,12 +260,12 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   if (tid == 0) {
     nL = 0;
     const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
-    gfac_s = (T)time_factor(A, tstage);
+    gfac_s = time_factor_t<T>(A, tstage);
   }
   if (A.ep)
     for (int el = tid; el < ne; el += blockDim.x) {
       const ElemPar& ep = A.ep[e0 + el];
-      gfe[el] = A.prm.T > 0.0 ? cpi((T)((ep.t + rk_c(A.stage) * ep.dt) / A.prm.T)) : (T)1;
+      gfe[el] = time_factor_t<T>(A, ep.t + rk_c(A.stage) * ep.dt);
       epe[el] = (T)ep.eps;
     }
   // line-pass role: line (lel, ll) of the fields fsel + q FS, q < NQ
@@ -757,13 +764,12 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   __shared__ RKConstF rks[ET];
   const RKConstF& rk0 = A.rk;
   if (A.ep) {
-    for (int el = tid; el < ne; el += blockDim.x) rks[el] = rk_const(MODE == 0 ? A.ep[e0 + el].dt : A.ep[e0 + el].dtau);
+    for (int el = tid; el < ne; el += blockDim.x) rks[el] = MODE == 0 ? A.ep[e0 + el].rk : A.ep[e0 + el].rkp;
     __syncthreads();
   }
   auto rkc_el = [&](int el) -> const RKConstF& { return A.ep ? rks[el] : rk0; };
   // mixed path: element flux balances (float-float partial sums per line)
   __shared__ float2 fb[kCons ? 2 * ET * LN : 1];
-  __shared__ float2 wb[kCons ? ET * LN : 1];
   __shared__ double tgt[kCons ? 2 * ET : 1];
   __shared__ float dlt[kCons ? 4 * ET : 1];
   if (stage != 0) {
@@ -812,7 +818,7 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
         const int64_t gt = e0 * 2 + t;
         if (stage == 1) A.tacc[gt] = Te;
         else if (stage < 4) A.tacc[gt] = tas[t] + 2.0 * Te;
-        else tgt[t] = rkc_el(t / 2).ddt / 6.0 * (tas[t] + Te);
+        else tgt[t] = rkc_el(t / 2).ddt6 * (tas[t] + Te);
       }
     }
     // ---- du/dt and the RK4 register update
@@ -859,31 +865,24 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
       if (lact) {
         const int base = line_base<DIM, N>(0, ll);
         const float2* wd = wds + lel * NU + base;
-        float2 wsl = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const int fld = fsel + q * FS;
           float2 sl = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const float2 w2 = wd[j];
-            sl = ff_add(sl, ff_mul(w2, (float)ys[(lel * NFLD + fld) * NU + base + j]));
-            if (q == 0) wsl = ff_add(wsl, w2);
-          }
+          for (int j = 0; j < N; ++j)
+            sl = ff_add(sl, ff_mul(wd[j], (float)ys[(lel * NFLD + fld) * NU + base + j]));
           fb[(lel * 2 + fld) * LN + ll] = sl;
         }
-        if (fsel == 0) wb[lel * LN + ll] = wsl;
       }
       __syncthreads();
       for (int t = tid; t < 2 * ne; t += blockDim.x) {
         const int el = t / 2;
-        float2 S2 = make_float2(0.f, 0.f), W2 = make_float2(0.f, 0.f);
-        for (int l = 0; l < LN; ++l) {
-          S2 = ff_add(S2, fb[t * LN + l]);
-          W2 = ff_add(W2, wb[el * LN + l]);
-        }
-        const double S = (double)S2.x + (double)S2.y, W = (double)W2.x + (double)W2.y;
-        const double d = (tgt[t] - S) / W;
+        float2 S2 = make_float2(0.f, 0.f);
+        for (int l = 0; l < LN; ++l) S2 = ff_add(S2, fb[t * LN + l]);
+        const T* mc = mcs + el * kMetricRec;
+        const double S = (double)S2.x + (double)S2.y, rW = (double)mc[12] + (double)mc[13];
+        const double d = (tgt[t] - S) * rW;
         const float dh = (float)d;
         dlt[2 * t] = dh;
         dlt[2 * t + 1] = (float)(d - (double)dh);

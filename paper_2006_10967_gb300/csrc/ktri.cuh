@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   __shared__ T gfac_s;
   if (tid == 0) {
     const double tstage = A.use_dev_time ? A.dstate[DS_TIME] + rk_c(A.stage) * A.dt : A.t;
-    gfac_s = (T)time_factor(A, tstage);
+    gfac_s = time_factor_t<T>(A, tstage);
   }
 
   load_tri_ops<P, T>(tri_of<T>(A), op);
