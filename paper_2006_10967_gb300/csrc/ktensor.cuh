@@ -670,7 +670,7 @@ struct KALayout {
 };
 
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
-// as in kb_tensor.  stage -1 writes du/dt to A.out (fp64) and leaves the
+// as in kb_tensor, the last of which also applies the update to its line.  stage -1 writes du/dt to A.out (fp64) and leaves the
 // state alone; stage 0 only recomputes the traces of ustg.
 template <int DIM, int N, typename T, int MODE>
 __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<DIM, N, T, MODE>::MINB)
@@ -801,6 +801,53 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
 #pragma unroll
           for (int j = 0; j < N; ++j) yl[j * st] += -O.gLd[j] * c0 + O.gRd[j] * c1;
         }
+        if (a == DIM - 1) {
+          // every contribution to this line's points is in: du/dt and the
+          // RK4 register update, by the line's own thread
+          const RKConstF& rkc = rkc_el(lel);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const int i = base + j * st;
+            T xi[3], Sm[3][3];
+            upt_xi<DIM, N>(i, O.x, xi);
+            T rdj;
+            metric_c<DIM>(gs + lel * NG, xi, Sm, mcs + lel * kMetricRec, &rdj);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              const int fld = fsel + q * FS;
+              const int li = (lel * NFLD + fld) * NU + i;  // tile index
+              const T R = -ys[li] * rdj;
+              const int64_t g = ((e0 + lel) * 2 + F0 + fld) * NU + i;
+              if (stage < 0) {
+                A.out[(int64_t)fld * A.E * NU + (e0 + lel) * NU + i] = (double)R;
+                continue;
+              }
+              if (kCons && cons && stage == 4) {
+                // float-float update now (kept in shared memory), the
+                // element's uniform correction below
+                const float2 u = u2s[li];
+                const float inc = rkc.dt6 * (acs[li] + (float)R);
+                const float s2 = u.x + inc;
+                const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
+                const float hi = s2 + e2;
+                u2s[li] = make_float2(hi, e2 - (hi - s2));
+                ys[li] = (T)inc;
+                continue;
+              }
+              T yt;
+              if constexpr (PRE) {
+                float2 un;
+                yt = rk_apply_v(A, stage, g, R, rkc, u2s[li], stage >= 2 ? acs[li] : 0.f, nullptr, &un);
+                if (stage == 4) reinterpret_cast<float2*>(A.u)[g] = un;
+              } else {
+                yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
+              }
+              if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
+              ustg[g] = yt;
+              ys[li] = yt;
+            }
+          }
+        }
       }
       __syncthreads();
     }
@@ -821,47 +868,9 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
         else tgt[t] = rkc_el(t / 2).ddt6 * (tas[t] + Te);
       }
     }
-    // ---- du/dt and the RK4 register update
-    for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
-      const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-      const RKConstF& rkc = rkc_el(el);
-      T xi[3], Sm[3][3];
-      upt_xi<DIM, N>(i, O.x, xi);
-      T rdj;
-      metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec, &rdj);
-      const T R = -ys[idx] * rdj;
-      const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
-      if (stage < 0) {
-        A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
-        continue;
-      }
-      if (kCons && cons && stage == 4) {
-        // float-float update now (kept in shared memory), the element's
-        // uniform correction below
-        const float2 u = u2s[idx];
-        const float inc = rkc_el(el).dt6 * (acs[idx] + (float)R);
-        const float s2 = u.x + inc;
-        const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
-        const float hi = s2 + e2;
-        u2s[idx] = make_float2(hi, e2 - (hi - s2));
-        ys[idx] = (T)inc;
-        continue;
-      }
-      T yt;
-      if constexpr (PRE) {
-        float2 un;
-        yt = rk_apply_v(A, stage, g, R, rkc, u2s[idx], stage >= 2 ? acs[idx] : 0.f, nullptr, &un);
-        if (stage == 4) reinterpret_cast<float2*>(A.u)[g] = un;
-      } else {
-        yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
-      }
-      if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
-      ustg[g] = yt;
-      ys[idx] = yt;
-    }
-    __syncthreads();
     if (kCons && cons && stage == 4) {
-      // per line: sum of w det J * increment (and of w det J), float-float
+      __syncthreads();  // the element sums above have read fb
+      // per line: sum of w det J * increment, float-float
       if (lact) {
         const int base = line_base<DIM, N>(0, ll);
         const float2* wd = wds + lel * NU + base;
