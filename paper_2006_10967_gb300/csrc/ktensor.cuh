@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
   constexpr int FS = LY::FS, NQ = NFLD / FS;  // fields per thread in the line passes
   constexpr int F0 = MODE == 0 ? 0 : 1;
+  constexpr bool kFuse4 = (N % 2) == 1;  // Step 4 inside the axis-0 pass of Step 6
+  static_assert(FS == 1, "the line passes assume one thread per line for all fields");
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -533,7 +535,8 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   }
   __syncthreads();
 
-  // ---- Step 4: transformed flux at solution points (in place of q) ---------
+  // ---- Step 4 (even N): transformed flux at solution points (in place of q)
+  if constexpr (!kFuse4) {
   for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
@@ -602,22 +605,111 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     }
   }
   __syncthreads();
+  }
 
-  // ---- Steps 4/6 by axis: normal flux at the line ends, flux jumps, the
-  //      line derivative and the two end lifts, summed into us
+  // ---- Steps 4 and 6 by axis.  With N odd, axis 0 first computes Step 4
+  //      (the transformed flux f~ = det J J^-1 f) at its own line's points:
+  //      the axis-0 component stays in registers, the others go to qt for the
+  //      later axes (with N even the lanes' stride N would make that pass's
+  //      shared-memory accesses conflict, so Step 4 runs above instead).  Each
+  //      pass then takes the normal flux at the line ends, the flux jumps,
+  //      the line derivative and the two end lifts into us.
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     if (lact) {
       const int st = ipow(N, a);
       const int base = line_base<DIM, N>(a, ll);
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
+      T fa[NFLD][N];  // axis-a transformed flux along this line
+      if (kFuse4 && a == 0) {
+        const int el = lel;
+        const T* mc = mcs + el * kMetricRec;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int i = base + j;  // axis-0 lines are contiguous
+          T xi[3], Sm[3][3];
+          upt_xi<DIM, N>(i, O.x, xi);
+          const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mc);
+          if (MODE == 0) {
+            T v[3];
+            const T gel = A.ep ? gfe[el] : gfac;
+            const T epsel = A.ep ? epe[el] : P.eps;
+            if (A.vsu) {
+              const T* vc = vu + el * DIM * NU + i;
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
+            } else {
+              T x[3];
+              map_point<S::ET_, T>(gs + el * NG, xi, x);
+              velocity<DIM, T>(BC.vel, x, gel, v);
+            }
+            T qp[3], qs[3], v2 = 0, g2 = 0;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              qp[c] = qt[((el * 2 + 0) * DIM + c) * NU + i];
+              qs[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
+              v2 += v[c] * v[c];
+              g2 += qs[c] * qs[c];
+            }
+            const T M = fmax(sqrt_(v2), P.gamma);
+            const T gm = fmax(sqrt_(g2), P.delta);
+            const T ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];
+            const T sharp = P.gamma * ph * ((T)1 - ph) / gm;
+            T f0[3], f1[3];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              f0[c] = ph * v[c] - M * (epsel * qp[c] - sharp * qs[c]);
+              f1[c] = ps * v[c];
+            }
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) {
+              T t0 = 0, t1 = 0;
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) {
+                t0 += Sm[b][c] * f0[c];
+                t1 += Sm[b][c] * f1[c];
+              }
+              if (b == 0) {
+                fa[0][j] = t0;
+                fa[NFLD - 1][j] = t1;
+              } else {
+                qt[((el * 2 + 0) * DIM + b) * NU + i] = t0;
+                qt[((el * 2 + 1) * DIM + b) * NU + i] = t1;
+              }
+            }
+          } else {
+            T qs[3], g2 = 0;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              qs[c] = qt[(el * DIM + c) * NU + i];
+              g2 += qs[c] * qs[c];
+            }
+            const T nu = nus[el];
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) {
+              T t0 = 0;
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) t0 += Sm[b][c] * (-nu * qs[c]);
+              if (b == 0) fa[0][j] = t0;
+              else qt[(el * DIM + b) * NU + i] = t0;
+            }
+            const T qm = sqrt_(g2);
+            const T p0 = (T)A.psi0[(e0 + el) * NU + i];
+            chi[el * 2 * NU + i] = tanh_(p0 / fmax(qm, P.delta)) * ((T)1 - qm) * dj;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const T* fl = qt + ((lel * NFLD + q) * DIM + a) * NU + base;
+#pragma unroll
+          for (int j = 0; j < N; ++j) fa[q][j] = fl[j * st];
+        }
+      }
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        const int fld = fsel + q * FS;
-        const T* fl = qt + ((lel * NFLD + fld) * DIM + a) * NU + base;
-        T v[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = fl[j * st];
+        const int fld = q;
+        const T* v = fa[q];
         T fp0 = 0, fp1 = 0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
