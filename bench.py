@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison (0: skip)")
     ap.add_argument("--cpu-steps", type=int, default=25, help="oracle RK4 steps for cpu_baseline (0: skip)")
-    ap.add_argument("--mesh-n", type=int, default=128, help="elements per side (128 is the benchmark workload)")
+    ap.add_argument("--mesh-n", type=int, default=None,
+                    help="elements per side (c2q: 128, the benchmark workload; c3: 64)")
     ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
     ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3", "c4"],
@@ -396,14 +397,16 @@ def main():
             print(json.dumps(line))
         return
     if args.workload == "c2q":
-        w = S.workload("c2q", n=args.mesh_n)
-        wname = f"rider_kothe_quad{args.mesh_n}_jitter_p4"
+        n = args.mesh_n or 128
+        w = S.workload("c2q", n=n)
+        wname = f"rider_kothe_quad{n}_jitter_p4"
     elif args.workload == "c2t":
         w = S.workload("c2t")
         wname = "rider_kothe_tri_delaunay_p3"
     else:
-        w = S.workload("c3")
-        wname = "leveque_hex64_p3"
+        n = args.mesh_n or 64
+        w = S.workload("c3", n=n)
+        wname = f"leveque_hex{n}_p3"
     mesh = w.mesh()
     nu_el = {"quad": (w.order + 1) ** 2, "tri": (w.order + 1) * (w.order + 2) // 2, "hex": (w.order + 1) ** 3}[mesh.etype]
     workload_cfg = {"workload": wname, "elements": mesh.n_elems, "order": w.order,
