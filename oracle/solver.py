@@ -27,6 +27,12 @@ Readings of points the paper leaves open (each is a parameter):
   * Resolution indicator on psi with an orthonormal modal basis; the
     truncation drops modes of (tensor) max degree p or (triangle) total degree p;
     an element with zero energy or zero truncated energy gets nu_s = 0.
+
+Params.normal selects the interface normal of the sharpening term: "psi"
+(the preconditioned method, n = grad psi/|grad psi|, Section 2) or "phi"
+(the unpreconditioned conservative phase field of Eq. altconservativephasefieldeq,
+n = grad phi/|grad phi| from phi's own corrected gradient, with no psi reset
+and no preconditioning; psi is still advected but feeds nothing).
 """
 from dataclasses import dataclass
 import math
@@ -56,6 +62,7 @@ class Params:
     kappa: float = 5.0
     nu_max: float = 0.0
     delta: float = 1e-12
+    normal: str = "psi"  # "psi": preconditioned (Section 2); "phi": unpreconditioned CPF
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -198,7 +205,8 @@ class Solver:
         # Step 4: flux at solution points, transformed
         v = velocity(self.vel, self.xu, t, A, B)
         M = torch.clamp(torch.sqrt((v * v).sum(-1)), min=prm.gamma)
-        qpsi = q[:, 1]
+        kn = 1 if prm.normal == "psi" else 0                          # field the normal comes from
+        qpsi = q[:, kn]
         nvec = qpsi / torch.clamp(torch.sqrt((qpsi * qpsi).sum(-1)), min=prm.delta)[..., None]
         fvis = M[..., None] * (prm.eps * q[:, 0] - prm.gamma * (phi * (1 - phi))[..., None] * nvec)
         f = torch.stack([phi[..., None] * v - fvis, psi[..., None] * v], 1)
@@ -207,7 +215,7 @@ class Solver:
         vf = velocity(self.vel, self.xf, t, A, B)
         vn = (vf * self.nhat).sum(-1)
         Mf = torch.clamp(torch.sqrt((vf * vf).sum(-1)), min=prm.gamma)
-        qpsif = qf[:, 1]
+        qpsif = qf[:, kn]
         nvecf = qpsif / torch.clamp(torch.sqrt((qpsif * qpsif).sum(-1)), min=prm.delta)[..., None]
         phif = Uf[:, 0]
         fvisf = Mf[..., None] * (prm.eps * qf[:, 0] - prm.gamma * (phif * (1 - phif))[..., None] * nvecf)
@@ -285,7 +293,7 @@ class Solver:
         self.psi0 = self.psi.clone()
         self.t = 0.0
         self.nstep = 0
-        if precondition:
+        if precondition and self.prm.normal == "psi":
             self.precondition()
 
     def rk4_step(self, A=None, B=None):
@@ -301,9 +309,10 @@ class Solver:
         self.nstep += 1
 
     def step(self, n=1, A=None, B=None):
-        """n physical steps; psi is reset and preconditioned every n_precond steps."""
+        """n physical steps; psi is reset and preconditioned every n_precond steps
+        (the preconditioned method only)."""
         for _ in range(n):
-            if self.nstep > 0 and self.nstep % self.prm.n_precond == 0:
+            if self.prm.normal == "psi" and self.nstep > 0 and self.nstep % self.prm.n_precond == 0:
                 self.precondition()
             self.rk4_step(A, B)
 

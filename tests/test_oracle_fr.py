@@ -175,6 +175,59 @@ def test_equilibrium_profile_and_sharpening_sign():
     assert res[1] < res[0] / 4
 
 
+def test_unpreconditioned_normal_comes_from_phi_alone():
+    """Unpreconditioned CPF (Eq. altconservativephasefieldeq, n = grad phi/|grad phi|):
+    phi's residual does not depend on psi at all, while the preconditioned
+    method's does; with psi = phi - 1/2 the two normals coincide."""
+    mesh = S.quad_grid(6, jitter=0.1, seed=2)
+    vel = S.Velocity("rider_kothe", T=8.0)
+    sp = _solver(mesh, 3, vel, gamma=0.09, eps=0.09 * 0.05)
+    sc = _solver(mesh, 3, vel, gamma=0.09, eps=0.09 * 0.05, normal="phi")
+    x = sc.xu
+    r = torch.sqrt((x[..., 0] - 0.45) ** 2 + (x[..., 1] - 0.55) ** 2)
+    phi = 0.5 * (1 + torch.tanh(8.0 * (0.25 - r)))
+    other = 0.3 * torch.sin(5 * x[..., 0]) * torch.cos(3 * x[..., 1]) + (x[..., 1] - 0.5)
+    Rc1, _ = sc.rhs(phi, phi - 0.5, 0.3)
+    Rc2, _ = sc.rhs(phi, other, 0.3)
+    assert torch.equal(Rc1, Rc2)
+    Rp1, _ = sp.rhs(phi, phi - 0.5, 0.3)
+    Rp2, _ = sp.rhs(phi, other, 0.3)
+    assert float((Rp1 - Rp2).abs().max()) > 1e-3 * float(Rp1.abs().max())
+    assert float((Rc1 - Rp1).abs().max()) <= 1e-12 * float(Rp1.abs().max())
+
+
+def test_unpreconditioned_equilibrium_profile():
+    """u = 0, unpreconditioned CPF: the planar tanh of width eps/gamma is
+    stationary up to a residual that falls with h, whatever psi holds."""
+    gamma, eps = 0.09, 0.09 * 0.06
+    res = []
+    for n in (16, 32):
+        mesh = S.quad_grid(n, periodic=(False, True))
+        s = _solver(mesh, 4, S.Velocity("uniform", a=(0.0, 0.0)), gamma=gamma, eps=eps, normal="phi")
+        phi = _planar(s, eps / gamma)
+        junk = torch.cos(7 * s.xu[..., 1]) * s.xu[..., 0]
+        Rphi, _ = s.rhs(phi, junk, 0.0)
+        res.append(float(Rphi.abs().max()))
+    assert res[1] < res[0] / 4
+
+
+def test_unpreconditioned_march_skips_preconditioning():
+    """No psi reset or pseudo-time iterations in the unpreconditioned method."""
+    mesh = S.quad_grid(4)
+    runs = []
+    for n_precond in (2, 10 ** 6):
+        s = _solver(mesh, 2, S.Velocity("uniform", a=(1.0, 0.5)), gamma=0.09, eps=0.01, dt=1e-3,
+                    normal="phi", n_precond=n_precond, pseudo_kmax=3, pseudo_dtau=1e-3, nu_max=0.01)
+        it0 = s.pseudo_iters
+        s.initialize(S.Circle((0.5, 0.5), 0.25, 6.0), precondition=True)
+        psi_before = s.psi.clone()
+        s.step(5)
+        assert s.pseudo_iters == it0
+        assert not torch.equal(psi_before, s.psi)
+        runs.append((s.phi, s.psi))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+
+
 def test_paper_parameters_make_the_initial_profile_an_equilibrium():
     """gamma = 0.09, eps = 0.06 h/p (Section 2) and beta = 3p/(4h) (Section 4):
     the initial width 1/(2 beta) equals eps/gamma."""
