@@ -48,6 +48,8 @@ def parse():
                     help="elements per side (c2q: 128, the benchmark workload; c3: 64)")
     ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
+    ap.add_argument("--normal", default="psi", choices=["psi", "phi"],
+                    help="interface normal: psi (preconditioned method) or phi (unpreconditioned CPF)")
     ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3", "c4"],
                     help="c2q: 128^2 jittered quads p=4 (the benchmark); c2t: ~30k Delaunay triangles p=3; "
                          "c3: 64^3 hexes p=3 (LeVeque); c4: 256-instance quad ensemble (200 steps per step)")
@@ -407,9 +409,14 @@ def main():
         n = args.mesh_n or 64
         w = S.workload("c3", n=n)
         wname = f"leveque_hex{n}_p3"
+    w.normal = args.normal
+    if args.normal == "phi":
+        wname += "_unpreconditioned"
     mesh = w.mesh()
     nu_el = {"quad": (w.order + 1) ** 2, "tri": (w.order + 1) * (w.order + 2) // 2, "hex": (w.order + 1) ** 3}[mesh.etype]
-    workload_cfg = {"workload": wname, "elements": mesh.n_elems, "order": w.order,
+    workload_cfg = {"workload": wname, "normal": {"psi": "grad psi (preconditioned)",
+                                                  "phi": "grad phi (unpreconditioned CPF)"}[args.normal],
+                    "elements": mesh.n_elems, "order": w.order,
                     "solution_points": mesh.n_elems * nu_el, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
                     "stages_per_rk_step": 4, "precondition_every": w.n_precond, "pseudo_kmax": w.pseudo_kmax,
                     "l2": "flushed before each timed step (512 MiB write); working set L2-resident within a step",

@@ -135,8 +135,15 @@ typedef struct fr_params {
                             at every solution and flux point at init (quad/hex; dim x (nu+nf)
                             values per element in the stage precision) instead of evaluating
                             v(x) every stage; 0: evaluate in the kernels */
-  int32_t reserved0;
+  int32_t normal;        /* interface normal of the sharpening term: FR_NORMAL_PSI (the
+                            preconditioned method, n = grad psi/|grad psi|, Section 2) or
+                            FR_NORMAL_PHI (the unpreconditioned conservative phase field,
+                            Eq. altconservativephasefieldeq with n = grad phi/|grad phi|;
+                            fr_step and set-up then never reset or precondition psi, which
+                            is still advected but feeds nothing).  Other values: FR_EINVAL */
 } fr_params;
+
+enum { FR_NORMAL_PSI = 0, FR_NORMAL_PHI = 1 };
 
 typedef struct fr_ic {
   int32_t kind;          /* FR_IC_CIRCLE or FR_IC_ARRAY */
@@ -291,6 +298,8 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  * fr_adjoint_record: advance n_steps from the current state (as fr_step),
  *   keeping checkpoints in `workspace` (device, caller-owned, 256-byte
  *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
+ *   FR_EUNSUPPORTED for a field whose normal is FR_NORMAL_PHI (the adjoint
+ *   covers the preconditioned method).
  * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
  *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,
  *   2 * n_dof: phi then psi) and, for a stream-function velocity,

@@ -70,7 +70,7 @@ class Params:
                  tau_pseudo=w.tau_pseudo, dt=w.dt, n_precond=w.n_precond,
                  pseudo_kmax=w.pseudo_kmax, pseudo_dtau=w.pseudo_dtau,
                  pseudo_tol=w.pseudo_tol, s0=w.s0, kappa=w.kappa, nu_max=w.nu_max,
-                 delta=w.delta)
+                 delta=w.delta, normal=getattr(w, "normal", "psi"))
         d.update(kw)
         return cls(**d)
 

@@ -111,6 +111,11 @@ def make_params(w, precision="fp64", **kw):
     p.nu_max = g("nu_max")
     p.delta = g("delta")
     p.vel_cache = int(bool(kw.get("vel_cache", True)))
+    # interface normal: "psi" (preconditioned method) or "phi" (unpreconditioned CPF)
+    normal = kw.get("normal", getattr(w, "normal", "psi"))
+    if normal not in ("psi", "phi"):
+        raise ValueError(f"normal must be 'psi' or 'phi', not {normal!r}")
+    p.normal = 1 if normal == "phi" else 0
     vel = kw.get("velocity", w.velocity)
     p.vel.kind = VELS[vel.kind]
     p.vel.T = float(vel.T)

@@ -78,6 +78,7 @@ void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
   b.prm.tau_psi = (R)prm->tau_psi;
   b.prm.tau_pseudo = (R)prm->tau_pseudo;
   b.prm.delta = (R)prm->delta;
+  b.prm.nphi = prm->normal == FR_NORMAL_PHI;
   if (m->etype != FR_TRI) {
     const Tensor1D& t = m->t1;
     for (int i = 0; i < t.n; ++i) {
@@ -153,6 +154,7 @@ int check_params(const fr_params* p) {
   if (!p) return FR_EINVAL;
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return FR_EINVAL;
   if (p->n_precond < 1 || p->pseudo_kmax < 0) return FR_EINVAL;
+  if (p->normal != FR_NORMAL_PSI && p->normal != FR_NORMAL_PHI) return FR_EINVAL;
   if (p->pseudo_kmax > 0 && !(p->pseudo_dtau > 0.0)) return FR_EINVAL;
   if (p->precision != FR_FP64 && p->precision != FR_MIXED) return FR_EINVAL;
   if (!(p->gamma >= 0.0) || !(p->eps >= 0.0) || !(p->delta > 0.0) || !(p->kappa > 0.0)) return FR_EINVAL;
@@ -429,7 +431,7 @@ int run_steps(fr_field* f, int n_steps, cudaStream_t s) {
   const int64_t np = f->prm.n_precond;
   int done = 0;
   while (done < n_steps) {
-    if (f->nstep > 0 && f->nstep % np == 0) {
+    if (f->prm.normal == FR_NORMAL_PSI && f->nstep > 0 && f->nstep % np == 0) {
       const int rc = run_precondition(f, s);
       if (rc) return rc;
     }
@@ -642,7 +644,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
     else f->ks.vcache(A, s);
   }
   if (err == FR_OK) err = stage_and_traces(f, s);
-  if (err == FR_OK && ic->precondition) err = run_precondition(f, s);
+  if (err == FR_OK && ic->precondition && prm->normal == FR_NORMAL_PSI) err = run_precondition(f, s);
   if (err == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) err = FR_ECUDA;
   if (err == FR_OK && cudaGetLastError() != cudaSuccess) err = FR_ECUDA;
   if (err != FR_OK) {
@@ -724,7 +726,7 @@ extern "C" int fr_field_init_batch(const fr_mesh* m, const fr_params* prm, int n
   drop_graphs(f);  // the launch arguments changed
   // the batch's pseudo step for the launch arguments is per element; keep a positive value
   rc = FR_OK;
-  if (precondition) rc = run_precondition(f, s);
+  if (precondition && prm->normal == FR_NORMAL_PSI) rc = run_precondition(f, s);
   if (rc == FR_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FR_ECUDA;
   if (rc == FR_OK) rc = read_status(f, s);
   if (rc != FR_OK && rc != FR_ENONFINITE) {

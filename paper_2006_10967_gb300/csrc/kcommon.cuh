@@ -31,6 +31,7 @@ struct VelDescT {
 template <typename R>
 struct PrmT {
   R gamma, eps, tau, tau_psi, tau_pseudo, delta;
+  int nphi;  // 1: the sharpening normal comes from phi's gradient (unpreconditioned CPF)
 };
 
 struct PhysPrm {

@@ -485,12 +485,13 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
         map_point<S::ET_, T>(gs + el * NG, xi, x);
         velocity<DIM, T>(BC.vel, x, gel, v);
       }
-      T vn = 0, v2 = 0, g2 = 0;
+      T vn = 0, v2 = 0, g2 = 0, qn[3];  // qn: gradient giving the interface normal
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
+        qn[c] = P.nphi ? qf[0][c] : qf[1][c];
         vn += v[c] * nh[c];
         v2 += v[c] * v[c];
-        g2 += qf[1][c] * qf[1][c];
+        g2 += qn[c] * qn[c];
       }
       const T M = fmax(sqrt_(v2), P.gamma);
       const T gm = fmax(sqrt_(g2), P.delta);
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) fvn += nh[c] * (epsel * qf[0][c] - sharp * qf[1][c]);
+      for (int c = 0; c < DIM; ++c) fvn += nh[c] * (epsel * qf[0][c] - sharp * qn[c]);
       const T Fp = (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
       const T Fs = (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
       // the transformed common flux F~ = |pn| F out of L; the R side uses -F~
@@ -561,6 +562,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
         qp[c] = qt[((el * 2 + 0) * DIM + c) * NU + i];
         qs[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
         v2 += v[c] * v[c];
+        qs[c] = P.nphi ? qp[c] : qs[c];  // gradient giving the interface normal
         g2 += qs[c] * qs[c];
       }
       const T M = fmax(sqrt_(v2), P.gamma);
@@ -649,6 +651,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
               qp[c] = qt[((el * 2 + 0) * DIM + c) * NU + i];
               qs[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
               v2 += v[c] * v[c];
+              qs[c] = P.nphi ? qp[c] : qs[c];  // gradient giving the interface normal
               g2 += qs[c] * qs[c];
             }
             const T M = fmax(sqrt_(v2), P.gamma);

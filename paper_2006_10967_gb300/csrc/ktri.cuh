@@ -225,13 +225,14 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       velocity<2, T>(BC.vel, x, gfac, v);
       const T vn = v[0] * nh[0] + v[1] * nh[1];
       const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
-      const T gm = fmax(sqrt_(qf[1][0] * qf[1][0] + qf[1][1] * qf[1][1]), Pm.delta);
+      const int kn = Pm.nphi ? 0 : 1;  // field whose gradient gives the interface normal
+      const T gm = fmax(sqrt_(qf[kn][0] * qf[kn][0] + qf[kn][1] * qf[kn][1]), Pm.delta);
       const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
       const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
       const T sharp = Pm.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qf[0][c] - sharp * qf[1][c]);
+      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qf[0][c] - sharp * qf[kn][c]);
       const T Fp = (T)0.5 * (pL + pR) * vn - fvn + Pm.tau * (pL - pR);
       const T Fs = (T)0.5 * (sL + sR) * vn + Pm.tau_psi * (sL - sR);
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       map_point<ET_TRI, T>(gs + el * NG, xi, x);
       velocity<2, T>(BC.vel, x, gfac, v);
       const T qp0 = q[((el * 2 + 0) * 2 + 0) * NU + i], qp1 = q[((el * 2 + 0) * 2 + 1) * NU + i];
-      const T qs0 = q[((el * 2 + 1) * 2 + 0) * NU + i], qs1 = q[((el * 2 + 1) * 2 + 1) * NU + i];
+      const int kn = Pm.nphi ? 0 : 1;  // field whose gradient gives the interface normal
+      const T qs0 = q[((el * 2 + kn) * 2 + 0) * NU + i], qs1 = q[((el * 2 + kn) * 2 + 1) * NU + i];
       const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
       const T gm = fmax(sqrt_(qs0 * qs0 + qs1 * qs1), Pm.delta);
       const T ph = us[(el * 2 + 0) * NU + i], ps = us[(el * 2 + 1) * NU + i];

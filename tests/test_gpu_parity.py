@@ -271,3 +271,54 @@ def test_nonfinite_state_is_reported(G):
     F.set(0, phi)
     F.step(1)
     assert F.sync() == -4
+
+
+# ---------------------------------------------------------------------------
+# Unpreconditioned conservative phase field (normal from phi's gradient)
+
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_periodic_jitter_p3", "tri_delaunay_p3",
+                                  "hex_walls_p3", "hex_periodic_jitter_p2"])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
+def test_unpreconditioned_rhs_parity(G, case, precision, tol):
+    """Eq. altconservativephasefieldeq with n = grad phi / |grad phi|, odd and
+    even orders (the residual kernel fuses Step 4 differently), with a psi
+    that is not phi - 1/2 so that the choice of normal matters."""
+    w = CASES[case]()
+    sol, F = _pair(G, w, precision=precision, normal="phi")
+    _perturb(sol, F)
+    R = F.rhs(0.3).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.3)
+    assert _rel(R[0], Ro[0].numpy()) < tol, case
+    assert _rel(R[1], Ro[1].numpy()) < tol, case
+    # the preconditioned residual of the same state is a different one
+    Rpc = sol.__class__(w.mesh(), w.order, Params.from_workload(w), w.velocity)
+    Rp = Rpc.rhs(sol.phi, sol.psi, 0.3)[0].numpy()
+    gap = _rel(Ro[0].numpy(), Rp)
+    assert gap > 1e-3
+    assert _rel(R[0], Rp) > 0.5 * gap
+
+
+def test_unpreconditioned_march_parity_without_preconditioning(G):
+    w = CASES["quad_walls_jitter_p4"]()
+    w.n_precond = 2
+    w.pseudo_kmax = 3
+    sol, F = _pair(G, w, precondition=True, normal="phi")
+    for nsteps in (1, 4):
+        F.step(nsteps)
+        sol.step(nsteps)
+        assert _rel(F.get(0), sol.phi.numpy()) < TOL64
+        assert _rel(F.get(1), sol.psi.numpy()) < TOL64
+    st = F.stats()
+    assert st["n_steps"] == 5 and st["n_preconditions"] == 0
+
+
+def test_unpreconditioned_mixed_conserves_mass_and_has_no_adjoint(G):
+    w = CASES["quad_periodic_jitter_p3"]()
+    _, F = _pair(G, w, precision="mixed", normal="phi")
+    m0 = F.mass(0)
+    F.step(20)
+    assert F.sync() == 0
+    assert abs(F.mass(0) - m0) < 1e-12 * abs(m0)
+    _, F64 = _pair(G, w, normal="phi")
+    with pytest.raises(G.FRError):
+        F64.adjoint_record(4, 2)
