@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
     ap.add_argument("--normal", default="psi", choices=["psi", "phi"],
                     help="interface normal: psi (preconditioned method) or phi (unpreconditioned CPF)")
-    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3", "c4"],
+    ap.add_argument("--order", type=int, default=None, help="zalesak/rudman: polynomial order (default 4)")
+    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3", "c4", "zalesak", "rudman"],
                     help="c2q: 128^2 jittered quads p=4 (the benchmark); c2t: ~30k Delaunay triangles p=3; "
-                         "c3: 64^3 hexes p=3 (LeVeque); c4: 256-instance quad ensemble (200 steps per step)")
+                         "c3: 64^3 hexes p=3 (LeVeque); c4: 256-instance quad ensemble (200 steps per step); "
+                         "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     return ap.parse_args()
 
@@ -187,12 +189,29 @@ def peaks():
     return d
 
 
+def make_field(G, S, M, P, w, precondition=True):
+    """The workload's field: the disk through the library's circle initial
+    condition, a slotted disk through its phi0 array at the solution points."""
+    if isinstance(w.circle, S.SlottedDisk):
+        return G.Field(M, P, phi0=S.initial_phi(w, M.solution_points()), precondition=precondition)
+    return G.Field(M, P, ic=w.circle, precondition=precondition)
+
+
+def oracle_init(sol, S, w):
+    """The oracle's initial state for the workload (no preconditioning)."""
+    import torch
+    if isinstance(w.circle, S.SlottedDisk):
+        sol.initialize(phi=torch.from_numpy(S.initial_phi(w, sol.xu.numpy())), precondition=False)
+    else:
+        sol.initialize(w.circle, precondition=False)
+
+
 # ---------------------------------------------------------------------------
 def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False, vel_cache=True):
     import torch
     M = G.Mesh.from_synthetic(mesh, w.order)
     P = G.make_params(w, precision, vel_cache=vel_cache)
-    F = G.Field(M, P, ic=w.circle, precondition=True)
+    F = make_field(G, S, M, P, w, precondition=True)
     ndof = M.info.n_dof
     stream = torch.cuda.current_stream()
     for _ in range(W):
@@ -337,7 +356,7 @@ def cpu_baseline(S, w, mesh, nsteps):
     import torch
     from oracle import Params, Solver
     sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
-    sol.initialize(w.circle, precondition=False)
+    oracle_init(sol, S, w)
     t0 = time.perf_counter()
     for _ in range(nsteps):
         sol.rk4_step()
@@ -345,22 +364,22 @@ def cpu_baseline(S, w, mesh, nsteps):
     ndof = sol.E * sol.Nu
     return {"value": ndof * 4 * nsteps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": f"{nsteps} RK4 step(s) (4 residual stages) of the full 128^2 p=4 workload, "
+            "sample": f"{nsteps} RK4 step(s) (4 residual stages) of the full workload ({w.name}), "
                       f"FP64 torch-CPU oracle, {dt:.1f} s"}
 
 
 def accuracy(G, S, w, mesh):
-    """Run both precisions to t = T and report E_L1 / E_m against the initial disk
-    (the Rider-Kothe flow returns it at t = T)."""
+    """Run both precisions to t = T and report E_L1, E_r and E_m (Section 4)
+    against the initial shape, which the flows return at t = T (Rider-Kothe
+    reversal, one solid-body revolution)."""
     import numpy as np
     res = {}
     M = G.Mesh.from_synthetic(mesh, w.order)
     xu = M.solution_points()
-    c = np.array(w.circle.centre)
-    phi_e = 0.5 * (1 + np.tanh(w.circle.beta * (w.circle.radius - np.sqrt(((xu - c) ** 2).sum(-1)))))
+    phi_e = S.initial_phi(w, xu)
     wq = M.quadrature()
     for prec in ("fp64", "mixed"):
-        F = G.Field(M, G.make_params(w, prec), ic=w.circle, precondition=True)
+        F = make_field(G, S, M, G.make_params(w, prec), w, precondition=True)
         m0 = F.mass(0)
         t0 = time.perf_counter()
         F.step(w.n_steps)
@@ -368,6 +387,7 @@ def accuracy(G, S, w, mesh):
         el = time.perf_counter() - t0
         phi = F.get(0)
         res[prec] = {"E_L1": float((wq * np.abs(phi - phi_e)).sum()),
+                     "E_r": float((wq * np.abs(phi - phi_e)).sum() / (wq * phi_e).sum()),
                      "E_m": float((F.mass(0) - m0) / (wq * phi_e).sum()),
                      "steps": w.n_steps, "wall_s": el}
     res["ratio_L1_mixed_over_fp64"] = res["mixed"]["E_L1"] / res["fp64"]["E_L1"]
@@ -405,6 +425,10 @@ def main():
     elif args.workload == "c2t":
         w = S.workload("c2t")
         wname = "rider_kothe_tri_delaunay_p3"
+    elif args.workload in ("zalesak", "rudman"):
+        n = args.mesh_n or (100 if args.workload == "zalesak" else 200)
+        w = S.workload(args.workload, n=n, p=args.order or 4)
+        wname = w.name
     else:
         n = args.mesh_n or 64
         w = S.workload("c3", n=n)
@@ -428,7 +452,7 @@ def main():
         import torch
         from oracle import Params, Solver
         sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
-        sol.initialize(w.circle, precondition=False)
+        oracle_init(sol, S, w)
         for _ in range(args.warmup):
             sol.rk4_step()
         t0 = time.perf_counter()

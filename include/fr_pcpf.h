@@ -72,7 +72,8 @@ extern "C" {
 #define FR_VEL_LEVEQUE 2     /* Section 4.3 field times g(t) */
 #define FR_VEL_STREAM 3      /* u = dPsi/dy, v = -dPsi/dx,
                                 Psi = g(t) sum_m A_m sin(2 pi k_m.x) + B_m cos(2 pi k_m.x) */
-#define FR_VEL_ROTATION 4    /* (0.5 - y, x - 0.5), Section 4.1 */
+#define FR_VEL_ROTATION 4    /* solid-body rotation about (a[0], a[1]): (a[1] - y, x - a[0]),
+                                Section 4.1 (Zalesak: centre (0.5, 0.5); Rudman: (2, 2)) */
 #define FR_MAX_MODES 32
 
 #define FR_IC_CIRCLE 0 /* phi = (1 + tanh(beta (r - |x - c|)))/2, Eqs. initialCond, discEq */
@@ -108,7 +109,7 @@ typedef struct fr_velocity {
   int32_t kind;          /* FR_VEL_* */
   int32_t n_modes;       /* FR_VEL_STREAM: 1..FR_MAX_MODES */
   double T;              /* g(t) = cos(pi t / T) if T > 0, else 1 */
-  double a[3];           /* FR_VEL_UNIFORM */
+  double a[3];           /* FR_VEL_UNIFORM: the velocity; FR_VEL_ROTATION: the centre */
   const double* kx;      /* host, n_modes each (FR_VEL_STREAM), copied */
   const double* ky;
   const double* A;

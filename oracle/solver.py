@@ -88,8 +88,8 @@ def velocity(vel, x, t, A=None, B=None):
         u = -torch.sin(pi * X) ** 2 * torch.sin(2 * pi * Y) * g
         v = torch.sin(2 * pi * X) * torch.sin(pi * Y) ** 2 * g
         return torch.stack([u, v], -1)
-    if vel.kind == "rotation":
-        return torch.stack([0.5 - Y, X - 0.5], -1)
+    if vel.kind == "rotation":  # solid-body rotation about (a[0], a[1])
+        return torch.stack([vel.a[1] - Y, X - vel.a[0]], -1)
     if vel.kind == "leveque":
         Z = x[..., 2]
         s = torch.sin

@@ -223,9 +223,9 @@ __device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, 
       if (DIM == 3) v[DIM - 1] = 0;
       break;
     }
-    default:  // solid-body rotation
-      v[0] = (R)0.5 - x[1];
-      v[1] = x[0] - (R)0.5;
+    default:  // solid-body rotation about (a[0], a[1])
+      v[0] = V.a[1] - x[1];
+      v[1] = x[0] - V.a[0];
       if (DIM == 3) v[DIM - 1] = 0;
   }
 }

@@ -8,9 +8,9 @@ operators, no fluxes. Both the CPU oracle and the CUDA path consume what it
 produces and each evaluates the method on its own.
 """
 from .meshes import (Mesh, quad_grid, tri_delaunay, tri_split, hex_grid)
-from .workloads import (Velocity, Circle, Workload, workload, WORKLOADS,
-                        stream_coefficients, ensemble_instances)
+from .workloads import (Velocity, Circle, SlottedDisk, Workload, workload, WORKLOADS,
+                        stream_coefficients, ensemble_instances, initial_phi)
 
 __all__ = ["Mesh", "quad_grid", "tri_delaunay", "tri_split", "hex_grid",
-           "Velocity", "Circle", "Workload", "workload", "WORKLOADS",
-           "stream_coefficients", "ensemble_instances"]
+           "Velocity", "Circle", "SlottedDisk", "Workload", "workload", "WORKLOADS",
+           "stream_coefficients", "ensemble_instances", "initial_phi"]

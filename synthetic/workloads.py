@@ -23,7 +23,8 @@ class Velocity:
           'leveque'     3D deformation field of Section 4.3 times g(t)
           'stream'      u = dPsi/dy, v = -dPsi/dx with
                         Psi = g(t) sum_m A_m sin(2 pi k_m.x) + B_m cos(2 pi k_m.x)
-          'rotation'    solid-body rotation (0.5 - y, x - 0.5) (Section 4.1)
+          'rotation'    solid-body rotation about (a[0], a[1]): (a[1] - y, x - a[0])
+                        (Section 4.1: Zalesak about (0.5, 0.5), Rudman about (2, 2))
     g(t) = cos(pi t / T) when T > 0, else 1.
     """
     kind: str
@@ -41,6 +42,39 @@ class Circle:
     centre: tuple
     radius: float
     beta: float
+
+
+@dataclass
+class SlottedDisk:
+    """Initial interface of the solid-body rotation tests (Section 4.1): the disk
+    |x - c| <= r with the slot |x - c_x| <= half_width, y <= top removed.
+
+    The initial field is phi = (1 + tanh(beta d)) / 2 (Eq. initialCond) with d
+    the signed distance of the slotted disk, positive inside, taken as the set
+    difference min(r - |x - c|, -d_slot) where d_slot is the signed distance
+    of the slot strip (positive inside it); this is exact at the interface and
+    inside the shape, and saturates the tanh elsewhere."""
+    centre: tuple
+    radius: float
+    half_width: float
+    top: float
+    beta: float
+
+    def signed_distance(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        dx = x[..., 0] - self.centre[0]
+        dy = x[..., 1] - self.centre[1]
+        d_disk = self.radius - np.sqrt(dx * dx + dy * dy)
+        ax = np.abs(dx) - self.half_width            # > 0: beside the strip
+        ay = x[..., 1] - self.top                    # > 0: above the strip
+        inside = (ax <= 0) & (ay <= 0)
+        d_slot = np.where(inside, np.minimum(-ax, -ay),
+                          -np.sqrt(np.maximum(ax, 0.0) ** 2 + np.maximum(ay, 0.0) ** 2))
+        return np.minimum(d_disk, -d_slot)
+
+    def phi(self, x):
+        """Initial phase field at the points x (..., 2)."""
+        return 0.5 * (1.0 + np.tanh(self.beta * self.signed_distance(x)))
 
 
 @dataclass
@@ -77,9 +111,10 @@ class Workload:
         return replace(self, **kw)
 
 
-def _umax(vel, dim, n=257):
-    """Max |u| at t = 0 on a fine lattice (used only to size the time step)."""
-    g = np.linspace(0.0, 1.0, n)
+def _umax(vel, dim, n=257, length=1.0):
+    """Max |u| at t = 0 on a fine lattice of [0, length]^dim (used only to size
+    the time step)."""
+    g = np.linspace(0.0, length, n)
     if dim == 2:
         x, y = np.meshgrid(g, g, indexing="ij")
         if vel.kind == "uniform":
@@ -88,7 +123,7 @@ def _umax(vel, dim, n=257):
             u = -np.sin(np.pi * x) ** 2 * np.sin(2 * np.pi * y)
             v = np.sin(2 * np.pi * x) * np.sin(np.pi * y) ** 2
         elif vel.kind == "rotation":
-            u, v = 0.5 - y, x - 0.5
+            u, v = vel.a[1] - y, x - vel.a[0]
         elif vel.kind == "stream":
             u = np.zeros_like(x)
             v = np.zeros_like(x)
@@ -123,7 +158,7 @@ def _finish(w, dim, cfl=0.1):
         w.eps = 0.06 * h / p
     w.nu_max = 0.15 * h / p
     w.pseudo_dtau = 0.1 * h / (p + 1)
-    umax = _umax(w.velocity, dim)
+    umax = _umax(w.velocity, dim, length=w.extra.get("length", 1.0))
     w.dt, w.n_steps = time_step(w.t_end, h, p, umax, cfl)
     w.extra.setdefault("umax", umax)
     return w
@@ -252,7 +287,50 @@ def _c5():
     return w
 
 
+def _zalesak(n=100, p=4):
+    """Zalesak's slotted disk (Section 4.1): r = 0.15 at (0.5, 0.75), slot
+    |x - 0.5| <= 0.025, y <= 0.85, solid-body rotation about (0.5, 0.5) for one
+    revolution (t = 2 pi) on n x n uniform quads.
+
+    The domain is periodic: the rotation crosses the unit square's edges, and
+    with copy ghost states and the central inviscid flux an inflow edge
+    amplifies round-off until the march fails; across opposite edges the
+    rotation's normal component is the same, and the disk stays far from them."""
+    h = 1.0 / n
+    w = Workload(f"zalesak_quad{n}_p{p}",
+                 lambda: meshes.quad_grid(n, periodic=(True, True), name=f"quadper{n}"), p,
+                 Velocity("rotation", a=(0.5, 0.5, 0.0)),
+                 SlottedDisk((0.5, 0.75), 0.15, 0.025, 0.85, 3 * p / (4 * h)), t_end=2 * math.pi, h=h)
+    return _finish(w, 2)
+
+
+def _rudman(n=200, p=4):
+    """Rudman's slotted disk (Section 4.1): r = 0.5 at (2, 2.75) in [0, 4]^2,
+    slot |x - 2| <= 0.06, y <= 2.65, rotation about (2, 2) for one revolution
+    on n x n uniform quads (periodic, as for Zalesak's disk)."""
+    h = 4.0 / n
+    w = Workload(f"rudman_quad{n}_p{p}",
+                 lambda: meshes.quad_grid(n, lengths=(4.0, 4.0), periodic=(True, True), name=f"quadper{n}L4"), p,
+                 Velocity("rotation", a=(2.0, 2.0, 0.0)),
+                 SlottedDisk((2.0, 2.75), 0.5, 0.06, 2.65, 3 * p / (4 * h)), t_end=2 * math.pi, h=h)
+    w.extra["length"] = 4.0
+    return _finish(w, 2)
+
+
+def initial_phi(w, x):
+    """The workload's initial phase field at the points x: the disk of Eq.
+    discEq for a Circle, the slotted disk for a SlottedDisk."""
+    c = w.circle
+    if isinstance(c, SlottedDisk):
+        return c.phi(x)
+    x = np.asarray(x, dtype=np.float64)
+    r = np.sqrt(((x - np.asarray(c.centre)[: x.shape[-1]]) ** 2).sum(-1))
+    return 0.5 * (1.0 + np.tanh(c.beta * (c.radius - r)))
+
+
 WORKLOADS = {
+    "zalesak": _zalesak,
+    "rudman": _rudman,
     "c1": _c1,
     "c2q": _c2q,
     "c2t": _c2t,

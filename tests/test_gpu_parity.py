@@ -86,7 +86,7 @@ CASES = {
         S.Velocity("rider_kothe", T=8.0), S.Circle((0.5, 0.6), 0.25, 3 * 3 / (4 / 8)), 1 / 8),
     "tri_split_periodic_p2": lambda: _workload(
         lambda: S.tri_split(5, shuffle_seed=1), 2,
-        S.Velocity("rotation"), S.Circle((0.5, 0.6), 0.25, 3 * 2 / (4 / 5)), 1 / 5),
+        S.Velocity("rotation", a=(0.5, 0.5)), S.Circle((0.5, 0.6), 0.25, 3 * 2 / (4 / 5)), 1 / 5),
     "hex_walls_p3": lambda: _workload(
         lambda: S.hex_grid(3, shuffle_seed=2), 3,
         S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 3 / (4 / 3)), 1 / 3),
@@ -322,3 +322,40 @@ def test_unpreconditioned_mixed_conserves_mass_and_has_no_adjoint(G):
     _, F64 = _pair(G, w, normal="phi")
     with pytest.raises(G.FRError):
         F64.adjoint_record(4, 2)
+
+
+# ---------------------------------------------------------------------------
+# Slotted disk in solid-body rotation (Section 4.1), rotation about (2, 2)
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", 1e-5)])
+def test_rudman_slotted_disk_parity(G, precision, tol):
+    """Rudman's problem on a coarse [0,4]^2 mesh (p = 3): the slotted disk's
+    initial field (an array input), preconditioning, and RK4 steps of the
+    rotation about (2, 2), against the oracle on the same phi0."""
+    n, p = 8, 3
+    h = 4.0 / n
+    w = _workload(lambda: S.quad_grid(n, lengths=(4.0, 4.0), periodic=(False, False)), p,
+                  S.Velocity("rotation", a=(2.0, 2.0, 0.0)),
+                  S.SlottedDisk((2.0, 2.75), 0.5, 0.06, 2.65, 3 * p / (4 * h)), h)
+    w.n_precond = 2
+    w.pseudo_kmax = 3
+    mesh = w.mesh()
+    sol = Solver(mesh, p, Params.from_workload(w, pseudo_fixed=True), w.velocity)
+    phi0 = S.initial_phi(w, sol.xu.numpy())
+    sol.initialize(phi=torch.from_numpy(phi0), precondition=True)
+    M = G.Mesh.from_synthetic(mesh, p)
+    F = G.Field(M, G.make_params(w, precision, pseudo_fixed=True), phi0=phi0, precondition=True)
+    assert _rel(F.get(1), sol.psi.numpy()) < tol
+    R = F.rhs(0.0).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.0)
+    assert _rel(R[0], Ro[0].numpy()) < (TOL64 if precision == "fp64" else TOL32)
+    F.step(3)
+    sol.step(3)
+    assert _rel(F.get(0), sol.phi.numpy()) < tol
+    assert F.stats()["n_preconditions"] == sol_preconditions(3, w.n_precond)
+
+
+def sol_preconditions(n_steps, n_precond):
+    """Preconditionings in n_steps steps from set-up (one at set-up, then one
+    before every step whose index is a positive multiple of n_precond)."""
+    return 1 + sum(1 for k in range(1, n_steps) if k % n_precond == 0)
