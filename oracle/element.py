@@ -20,10 +20,15 @@ orthonormal Psi) and E[i,k] = int l_i lambda_k ds, evaluated exactly by the
 face Gauss-Legendre rule at the flux points.  The tests check that on tensor
 elements this equals the Radau closed form g_L'(xi) along each line.
 
-Triangle solution points: the Williams-Shunn tables are not available, so the
-triangle uses the interior principal lattice with barycentric coordinates
-((i+1)/(p+3), (j+1)/(p+3), ...): symmetric, interior and unisolvent (an affine
-image of the equispaced lattice).
+Triangle solution points: the Williams-Shunn tables are not available.  The
+triangle uses the Blyth-Pozrikidis map of the 1D Gauss-Legendre nodes
+v_0 < ... < v_p on [0, 1]: lattice index (i, j, k), i + j + k = p, goes to the
+barycentric point l_a = (1 + 2 v_a - v_b - v_c)/3.  The set is symmetric,
+interior and unisolvent, its interpolatory weights int l_i are positive for
+p <= 4, and the central-flux advection operator on it is close to energy
+neutral (the tests bound the largest real part of its spectrum); the same
+map of equispaced nodes (the principal lattice) gives negative weights and
+advection modes that grow by e^29 over one Rider-Kothe period at p = 3.
 """
 import math
 from dataclasses import dataclass
@@ -200,10 +205,18 @@ def ref_element(etype, p):
         high = np.array([max(d) == p for d in degrees])
         modal = lambda x: _modal_tensor(p, dim, x)[:2]
     else:
+        # Blyth-Pozrikidis map of the 1D Gauss-Legendre nodes v on [0, 1]:
+        # lattice index (i, j, k), i + j + k = p, goes to the barycentric point
+        # l_a = (1 + 2 v_a - v_b - v_c) / 3 (equispaced v would give the lattice)
+        v = (g + 1.0) / 2.0
         pts = []
         for j in range(p + 1):
             for i in range(p + 1 - j):
-                pts.append([2.0 * (i + 1) / (p + 3) - 1.0, 2.0 * (j + 1) / (p + 3) - 1.0])
+                k = p - i - j
+                l1 = (1.0 + 2.0 * v[i] - v[j] - v[k]) / 3.0
+                l2 = (1.0 + 2.0 * v[j] - v[i] - v[k]) / 3.0
+                l0 = 1.0 - l1 - l2
+                pts.append([l1 - l0 - l2, l2 - l0 - l1])   # vertices (-1,-1), (1,-1), (-1,1)
         xu = np.array(pts)
         P, Gm, degrees = _modal_tri(p, xu)
         high = np.array([i + j == p for (i, j) in degrees])

@@ -261,15 +261,9 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     const T* mt = met + el * 5;
     if (MODE == 0) {
       T xi[2], x[3], v[3];
-      // solution point reference coordinates are those of the lattice
-      {
-        int c = 0, jj = 0, ii = 0;
-        for (int j = 0; j <= P; ++j)
-          for (int i2 = 0; i2 <= P - j; ++i2, ++c)
-            if (c == i) { jj = j; ii = i2; }
-        xi[0] = (T)(2.0 * (ii + 1) / (P + 3) - 1.0);
-        xi[1] = (T)(2.0 * (jj + 1) / (P + 3) - 1.0);
-      }
+      const T* xr = tri_of<T>(A).xu + 2 * i;  // solution point i in the reference triangle
+      xi[0] = xr[0];
+      xi[1] = xr[1];
       map_point<ET_TRI, T>(gs + el * NG, xi, x);
       velocity<2, T>(BC.vel, x, gfac, v);
       const T qp0 = q[((el * 2 + 0) * 2 + 0) * NU + i], qp1 = q[((el * 2 + 0) * 2 + 1) * NU + i];

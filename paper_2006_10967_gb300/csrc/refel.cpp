@@ -187,15 +187,24 @@ void build_tri(int p, TriRef& t) {
   t.p = p;
   t.nu = nu;
   t.nf = nf;
+  double g[kMaxN], w[kMaxN];
+  gauss_legendre(n, g, w);
+  // Solution points: the Blyth-Pozrikidis map of the Gauss-Legendre nodes
+  // v = (g + 1)/2: lattice index (i, j, k), i + j + k = p, goes to the
+  // barycentric point l_a = (1 + 2 v_a - v_b - v_c)/3 (symmetric, interior,
+  // positive interpolatory weights for p <= 4)
   t.xu.resize(nu * 2);
   int c = 0;
   for (int j = 0; j <= p; ++j)
     for (int i = 0; i <= p - j; ++i, ++c) {
-      t.xu[2 * c] = 2.0 * (i + 1) / (p + 3) - 1.0;
-      t.xu[2 * c + 1] = 2.0 * (j + 1) / (p + 3) - 1.0;
+      const int k = p - i - j;
+      const double vi = 0.5 * (g[i] + 1.0), vj = 0.5 * (g[j] + 1.0), vk = 0.5 * (g[k] + 1.0);
+      const double l1 = (1.0 + 2.0 * vi - vj - vk) / 3.0;
+      const double l2 = (1.0 + 2.0 * vj - vi - vk) / 3.0;
+      const double l0 = 1.0 - l1 - l2;
+      t.xu[2 * c] = l1 - l0 - l2;  // vertices (-1,-1), (1,-1), (-1,1)
+      t.xu[2 * c + 1] = l2 - l0 - l1;
     }
-  double g[kMaxN], w[kMaxN];
-  gauss_legendre(n, g, w);
   const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
   const double s2 = std::sqrt(2.0);
   const double nrm[3][2] = {{0, -1}, {1 / s2, 1 / s2}, {-1, 0}};

@@ -136,3 +136,23 @@ def test_flux_points_on_boundary_and_normals_unit(etype, p):
     # face weights add up to the reference boundary measure
     meas = {"quad": 8.0, "hex": 24.0, "tri": 4.0 + 2.0 * math.sqrt(2.0)}[etype]
     assert el.wf.sum() == pytest.approx(meas, rel=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_triangle_points_symmetric_interior_positive(p):
+    """The triangle's solution points (Blyth-Pozrikidis map of the 1D
+    Gauss-Legendre nodes): the set is invariant under the vertex permutations,
+    interior, and its interpolatory weights int l_i are positive."""
+    el = ref_element("tri", p)
+    x = el.xu
+    lam = np.stack([-(x[:, 0] + x[:, 1]) / 2, (1 + x[:, 0]) / 2, (1 + x[:, 1]) / 2], 1)
+    assert lam.min() > 0.0
+    key = lambda L: sorted(tuple(np.round(r, 12)) for r in L)
+    for perm in itertools.permutations(range(3)):
+        assert key(lam[:, perm]) == key(lam)
+    assert el.wq.min() > 0.0 and el.wq.sum() == pytest.approx(2.0, rel=1e-14)
+    # the smallest barycentric coordinate is the one of lattice index (0, 0, p):
+    # (1 + 2 v_0 - v_0 - v_p) / 3 with v the Gauss-Legendre nodes on [0, 1]
+    g, _ = gauss_legendre(p + 1)
+    v = (g + 1) / 2
+    assert lam.min() == pytest.approx((1 + v[0] - v[p]) / 3, abs=1e-14)

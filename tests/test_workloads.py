@@ -103,3 +103,15 @@ def test_rotation_velocity_about_a_centre():
     v = velocity(vel, x, 0.7)
     expect = torch.tensor([[0.0, 0.0], [0.0, 1.0], [-1.5, 0.0], [1.0, -1.5]], dtype=torch.float64)
     assert torch.equal(v, expect)
+
+
+def test_split_triangle_family():
+    """Section 4.2's "c" meshes: n x n squares split along a diagonal, h = 1/n
+    (sqrt(2 |Omega| / E))."""
+    for n in (32, 64):
+        w = S.workload("c2s", n=n, p=4)
+        m = w.mesh()
+        assert m.etype == "tri" and m.n_elems == 2 * n * n
+        assert w.h == pytest.approx(math.sqrt(2.0 / m.n_elems))
+        assert w.circle.beta == pytest.approx(GOLD["ic_beta_times_h_per_p"]["value"] * w.order / w.h)
+        assert tuple(w.circle.centre) == tuple(GOLD["rider_kothe_centre"]["value"])
