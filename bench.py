@@ -52,11 +52,13 @@ def parse():
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
     ap.add_argument("--normal", default="psi", choices=["psi", "phi"],
                     help="interface normal: psi (preconditioned method) or phi (unpreconditioned CPF)")
-    ap.add_argument("--order", type=int, default=None, help="zalesak/rudman: polynomial order (default 4)")
-    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c3", "c4", "zalesak", "rudman"],
+    ap.add_argument("--order", type=int, default=None,
+                    help="zalesak/rudman: polynomial order (default 4); c2s: (default 3)")
+    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c2s", "c3", "c4", "zalesak", "rudman"],
                     help="c2q: 128^2 jittered quads p=4 (the benchmark); c2t: ~30k Delaunay triangles p=3; "
                          "c3: 64^3 hexes p=3 (LeVeque); c4: 256-instance quad ensemble (200 steps per step); "
-                         "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads)")
+                         "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads); "
+                         "c2s: Rider-Kothe on split-triangle meshes (--mesh-n, --order <= 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     return ap.parse_args()
 
@@ -428,6 +430,10 @@ def main():
     elif args.workload == "c2t":
         w = S.workload("c2t")
         wname = "rider_kothe_tri_delaunay_p3"
+    elif args.workload == "c2s":
+        n = args.mesh_n or 128
+        w = S.workload("c2s", n=n, p=args.order or 3)
+        wname = f"rider_kothe_trisplit{n}_p{w.order}"
     elif args.workload in ("zalesak", "rudman"):
         n = args.mesh_n or (100 if args.workload == "zalesak" else 200)
         w = S.workload(args.workload, n=n, p=args.order or 4)

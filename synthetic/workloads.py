@@ -260,6 +260,18 @@ def _c2t(m=123):
     return _finish(w, 2)
 
 
+def _c2s(n=128, p=3):
+    """Rider-Kothe vortex on the paper's split-triangle family ("c" meshes of
+    Section 4.2): an n x n grid with every square split along a diagonal,
+    walls, element order shuffled (seed 14); h = sqrt(2 |Omega| / E) = 1/n."""
+    h = 1.0 / n
+    w = Workload(f"c2s_trisplit{n}_p{p}_rider_kothe",
+                 lambda: meshes.tri_split(n, periodic=(False, False), shuffle_seed=14, name=f"trisplit{n}"),
+                 p, Velocity("rider_kothe", T=8.0), Circle((0.5, 0.75), 0.15, 3 * p / (4 * h)),
+                 t_end=8.0, h=h)
+    return _finish(w, 2)
+
+
 def _c3(n=64):
     p = 3
     h = 1.0 / n
@@ -334,6 +346,7 @@ WORKLOADS = {
     "c1": _c1,
     "c2q": _c2q,
     "c2t": _c2t,
+    "c2s": _c2s,
     "c3": _c3,
     "c5": _c5,
 }
