@@ -12,6 +12,7 @@
 //   lam = lam' + a4 + a3 + a2 + a1,
 // with the vector-Jacobian products of kadj.cuh, and accumulates the
 // gradient with respect to the stream-function coefficients.
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -30,8 +31,10 @@ namespace {
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 typedef void (*AdjFn)(const AdjArgs&, cudaStream_t);
+typedef void (*TabFn)(const KArgs&, double*, cudaStream_t);
 struct AdjSet {
   AdjFn a = nullptr, b = nullptr, c = nullptr;
+  TabFn tab = nullptr;  // cos/sin table of the stream-function modes at the points
   int et = 1;
 };
 
@@ -56,11 +59,18 @@ void lc(const AdjArgs& B, cudaStream_t s) {
   adj_c<DIM, N><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, 0, s>>>(B);
 }
 template <int DIM, int N>
+void ltab(const KArgs& A, double* cs, cudaStream_t s) {
+  const int64_t n = A.E * (TS<DIM, N>::NU + TS<DIM, N>::NF);
+  const int64_t g = (n + 255) / 256;
+  k_coef_table<DIM, N><<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(A, cs);
+}
+template <int DIM, int N>
 AdjSet make_set() {
   AdjSet a;
   a.a = la<DIM, N>;
   a.b = lb<DIM, N>;
   a.c = lc<DIM, N>;
+  a.tab = ltab<DIM, N>;
   a.et = AdjLayout<DIM, N>::ET;
   return a;
 }
@@ -133,6 +143,11 @@ Sizes sizes(const fr_field* f, int n_steps, int ck, int adj_blocks) {
   t += 2 * al(nf2);
   t += 4 * al(2 * ndof * 8);
   t += al((size_t)adj_blocks * 2 * FR_MAX_MODES * 8);
+  if (f->prm.vel.kind == FR_VEL_STREAM) {  // phase table and per-point velocity adjoint
+    const size_t np = (size_t)f->E * (f->nu + f->nf);
+    t += al(np * (size_t)f->prm.vel.n_modes * 2 * 8);
+    t += al(np * 2 * 8);
+  }
   z.total = t;
   return z;
 }
@@ -192,6 +207,13 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, void*
   R.off_Lk = off;
   off += nd2;
   R.off_coefp = off;
+  off += al((size_t)nb * 2 * FR_MAX_MODES * 8);
+  if (f->prm.vel.kind == FR_VEL_STREAM) {
+    const size_t np = (size_t)f->E * (f->nu + f->nf);
+    R.off_cs = off;
+    off += al(np * (size_t)f->prm.vel.n_modes * 2 * 8);
+    R.off_lv = off;
+  }
   const size_t ubytes = 2 * (size_t)f->E * f->nu * 8;
   for (int n = 0; n < n_steps; ++n) {
     if (n % ckpt_every == 0) {
@@ -235,6 +257,10 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
   if (grid > 152 * 16) grid = 152 * 16;
   k_pack_lam<<<grid, 256, 0, s>>>(Lp, dJ_dphiT, dJ_dpsiT, E, NU);
   if (M2) CK(cudaMemsetAsync(coefp, 0, (size_t)R.adj_blocks * M2 * 8, s));
+  double* cs = M2 ? reinterpret_cast<double*>(R.ws + R.off_cs) : nullptr;
+  double* lv = M2 ? reinterpret_cast<double*>(R.ws + R.off_lv) : nullptr;
+  if (M2) as.tab(f->args, cs, s);
+  const int64_t npts = E * (f->nu + f->nf);
   const int64_t nstep_save = f->nstep;
   std::vector<double> th(R.ckpt_every);
   for (int seg = R.n_ckpt - 1; seg >= 0; --seg) {
@@ -282,6 +308,7 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
         B.lamuo = lamuo;
         B.coefp = coefp;
         B.want_coef = M2 > 0;
+        B.lv = lv;
         B.Lp = Lp;
         B.Lu = Lu;
         B.first = st == 4;
@@ -293,6 +320,11 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
         }
         as.a(B, s);
         as.b(B, s);
+        if (M2) {
+          const double T = f->prm.vel.T;
+          const double gt = T > 0.0 ? std::cos(M_PI * B.K.t / T) : 1.0;  // time factor of this stage
+          k_coef_acc<<<R.adj_blocks, 256, 0, s>>>(lv, cs, npts, f->args.cd.vel, gt, coefp);
+        }
         // adj_c reads Lk (through lamk of the next stage) only after this stage
         // is complete; writing Lk here is safe because stage st consumed it in adj_a/adj_b
         as.c(B, s);

@@ -14,7 +14,7 @@ struct AdjRecord {
   char* ws = nullptr;      // caller workspace
   size_t bytes = 0;
   size_t off_ckpt = 0, off_stage = 0, off_times = 0, off_Y = 0, off_lamuo = 0, off_lamU = 0, off_Lp = 0,
-         off_Lu = 0, off_Lk = 0, off_coefp = 0;
+         off_Lu = 0, off_Lk = 0, off_coefp = 0, off_cs = 0, off_lv = 0;
   int adj_blocks = 0;
 };
 

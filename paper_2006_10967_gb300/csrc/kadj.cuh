@@ -17,6 +17,11 @@
 //           traces (lamuo, global)
 //   adj_c : gathers the partners' lamuo, adds L^T of it, and applies the
 //           RK4 adjoint recurrence.
+// For a stream-function velocity adj_b also stores, per solution and flux
+// point, the adjoint of the velocity there (lv); k_coef_acc contracts it with
+// the derivative of the velocity with respect to each coefficient, from a
+// table of cos/sin(2 pi k_m . x) at the points made once per sweep
+// (k_coef_table), into per-block partial sums.
 #pragma once
 #include "ktensor.cuh"
 
@@ -31,6 +36,7 @@ struct AdjArgs {
   double* lamuo;        // E x 2 x NF
   double* coefp;        // [blocks][2 * n_modes] coefficient gradient partials (accumulated)
   int want_coef;
+  double* lv;           // stream velocity: E x (NU + NF) x 2 adjoint of the velocity at each point
   // adj_c: RK4 recurrence  Lu = (first ? Lp : Lu) + a ;  Lk = c_lp * Lp + c_a * a
   const double* Lp;
   double* Lu;
@@ -59,16 +65,65 @@ struct AdjLayout {
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 64;
 };
 
-// d(v)/d(coefficients) contracted with lv, added to sh[0..2M) (stream field,
-// 2D): v = g * sum_m 2 pi (A_m cos th_m - B_m sin th_m) (ky_m, -kx_m).
-template <typename T>
-__device__ __forceinline__ void coef_vjp(const VelDescT<T>& V, const T* x, T g, const T* lv, double* sh) {
-  for (int m = 0; m < V.n_modes; ++m) {
-    T s, c;
-    scpi((T)2 * (V.kx[m] * x[0] + V.ky[m] * x[1]), &s, &c);
-    const T w = (T)(2.0 * M_PI) * g * (V.ky[m] * lv[0] - V.kx[m] * lv[1]);
-    atomicAdd(&sh[m], (double)(w * c));
-    atomicAdd(&sh[V.n_modes + m], (double)(-w * s));
+// cos/sin(2 pi k_m . x) of every stream-function mode m at every solution
+// and flux point of the mesh: cs[((e (NU + NF) + p) M + m) 2 + {0, 1}].
+template <int DIM, int N>
+__global__ void k_coef_table(const KArgs A, double* cs) {
+  using S = TS<DIM, N>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG;
+  const VelDescT<double>& V = A.cd.vel;
+  const int M = V.n_modes;
+  const int64_t n = A.E * (NU + NF);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / (NU + NF);
+    const int p = (int)(g % (NU + NF));
+    double xi[3], x[3];
+    if (p < NU) upt_xi<DIM, N>(p, A.cd.ops.x, xi);
+    else fpt_xi<DIM, N>(p - NU, A.cd.ops.x, xi);
+    map_point<S::ET_, double>(A.geo + e * NG, xi, x);
+    for (int m = 0; m < M; ++m) {
+      double sn, c;
+      scpi(2.0 * (V.kx[m] * x[0] + V.ky[m] * x[1]), &sn, &c);
+      cs[(g * M + m) * 2 + 0] = c;
+      cs[(g * M + m) * 2 + 1] = sn;
+    }
+  }
+}
+
+// Coefficient gradient of one stage: with v = g sum_m 2 pi (A_m cos th_m -
+// B_m sin th_m)(k_y, -k_x), th_m = 2 pi k_m . x, the stage adds
+//   dA_m += 2 pi g sum_p w_pm cos th_pm,  dB_m -= 2 pi g sum_p w_pm sin th_pm,
+//   w_pm = k_y,m lv0_p - k_x,m lv1_p,
+// over the points p of block b's share, to coefp[b][.] (no atomics).
+// Launch: blocks = the partial slots, 256 threads = 32 mode lanes x 8 groups.
+__global__ void k_coef_acc(const double* lv, const double* cs, int64_t npts, VelDescT<double> V, double g,
+                           double* coefp) {
+  const int M = V.n_modes, M2 = 2 * M;
+  const int m = threadIdx.x & 31, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
+  const int64_t per = (npts + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = (int64_t)blockIdx.x * per, p1 = p0 + per < npts ? p0 + per : npts;
+  double ac = 0.0, as = 0.0;
+  if (m < M) {
+    const double kx = V.kx[m], ky = V.ky[m];
+    for (int64_t p = p0 + grp; p < p1; p += ngrp) {
+      const double w = ky * lv[2 * p] - kx * lv[2 * p + 1];
+      ac += w * cs[(p * M + m) * 2 + 0];
+      as += w * cs[(p * M + m) * 2 + 1];
+    }
+  }
+  __shared__ double red[2][8][32];
+  red[0][grp][m] = ac;
+  red[1][grp][m] = as;
+  __syncthreads();
+  if (grp == 0 && m < M) {
+    double sc = 0.0, ss = 0.0;
+    for (int q = 0; q < ngrp; ++q) {
+      sc += red[0][q][m];
+      ss += red[1][q][m];
+    }
+    const double f = 2.0 * M_PI * g;
+    coefp[(int64_t)blockIdx.x * M2 + m] += f * sc;
+    coefp[(int64_t)blockIdx.x * M2 + M + m] -= f * ss;
   }
 }
 
@@ -135,7 +190,6 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   double* lqf = luo + ET * 2 * NF;                     // [ET][2][DIM][NF]
   double* gs = lqf + ET * 2 * DIM * NF;                // [ET][NG]
   unsigned char* lm = reinterpret_cast<unsigned char*>(gs + ET * NG);
-  __shared__ double csh[2 * kMaxModes];
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -147,8 +201,6 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   const PrmT<double> P = BC.prm;
   const double g = time_factor(A, A.t);
   const bool coef = B.want_coef && BC.vel.kind == 3 && DIM == 2;
-  const int M2 = 2 * BC.vel.n_modes;
-  for (int m = tid; m < 2 * kMaxModes; m += blockDim.x) csh[m] = 0.0;
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) us[idx] = ustg[e0 * 2 * NU + idx];
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = A.geo[e0 * NG + idx];
   __syncthreads();
@@ -311,7 +363,9 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
       const double dM = vm > P.gamma ? 1.0 / vm : 0.0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) lvv[c] = ph * l0[c] + ps * l1[c] - la * v[c] * dM;
-      coef_vjp<double>(BC.vel, x, g, lvv, csh);
+      double* o = B.lv + ((e0 + el) * (NU + NF) + i) * 2;
+      o[0] = lvv[0];
+      o[1] = lvv[1];
     }
   }
   // ---- reverse of Step 5 at L flux points ------------------------------------
@@ -323,6 +377,11 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
       for (int c = 0; c < DIM; ++c) lqf[((el * 2 + fld) * DIM + c) * NF + k] = 0.0;
       luf[(el * 2 + fld) * NF + k] = 0.0;
       luo[(el * 2 + fld) * NF + k] = 0.0;
+    }
+    if (coef) {
+      double* o = B.lv + ((e0 + el) * (NU + NF) + NU + k) * 2;  // R points: no contribution
+      o[0] = 0.0;
+      o[1] = 0.0;
     }
     if (!lm[el * NF + k]) continue;
     const int64_t gk = (e0 + el) * NF + k;
@@ -415,7 +474,9 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
 #pragma unroll
       for (int c = 0; c < DIM; ++c)
         lvv[c] = lF[0] * (0.5 * (pL + pR) * nh[c] - fvn * v[c] * dM) + lF[1] * 0.5 * (sL + sR) * nh[c];
-      coef_vjp<double>(BC.vel, x, g, lvv, csh);
+      double* o = B.lv + ((e0 + el) * (NU + NF) + NU + k) * 2;
+      o[0] = lvv[0];
+      o[1] = lvv[1];
     }
   }
   __syncthreads();
@@ -503,10 +564,6 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   }
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) B.lamU[e0 * 2 * NU + idx] = us[idx];
   for (int idx = tid; idx < ne * 2 * NF; idx += blockDim.x) B.lamuo[e0 * 2 * NF + idx] = luo[idx];
-  if (coef) {
-    __syncthreads();
-    for (int m = tid; m < M2; m += blockDim.x) B.coefp[(int64_t)blockIdx.x * M2 + m] += csh[m];
-  }
 }
 
 // ---------------------------------------------------------------------------
