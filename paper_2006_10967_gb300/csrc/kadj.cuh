@@ -304,8 +304,14 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
     double xi[3], Sm[3][3], x[3], v[3];
     upt_xi<DIM, N>(i, O.x, xi);
     metric<DIM>(gs + el * NG, xi, Sm);
-    map_point<S::ET_, double>(gs + el * NG, xi, x);
-    velocity<DIM, double>(BC.vel, x, g, v);
+    if (A.vsu) {  // the forward kernels' velocity: g(t) times the cached v(x)
+      const double* vc = reinterpret_cast<const double*>(A.vsu) + (e0 + el) * DIM * NU + i;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) v[c] = g * vc[c * NU];
+    } else {
+      map_point<S::ET_, double>(gs + el * NG, xi, x);
+      velocity<DIM, double>(BC.vel, x, g, v);
+    }
     double q0[3], q1[3], l0[3], l1[3], v2 = 0, g2 = 0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -407,8 +413,14 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
     double nh[3];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) nh[c] = pn[c] / pm;
-    map_point<S::ET_, double>(gs + el * NG, xi, x);
-    velocity<DIM, double>(BC.vel, x, g, v);
+    if (A.vsf) {  // the forward kernels' velocity: g(t) times the cached v(x)
+      const double* vc = reinterpret_cast<const double*>(A.vsf) + (e0 + el) * DIM * NF + k;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) v[c] = g * vc[c * NF];
+    } else {
+      map_point<S::ET_, double>(gs + el * NG, xi, x);
+      velocity<DIM, double>(BC.vel, x, g, v);
+    }
     const int st = ipow(N, a);
     double qf0[3], qf1[3];
 #pragma unroll
