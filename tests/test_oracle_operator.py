@@ -117,7 +117,7 @@ def _structured_index(x, n, p, xi):
     return g
 
 
-@pytest.mark.parametrize("n,p", [(2, 2), (3, 3), (3, 4)])
+@pytest.mark.parametrize("n,p", [(1, 1), (1, 3), (2, 1), (2, 2), (3, 3), (3, 4)])
 @pytest.mark.parametrize("tau,eps", [(0.0, 0.0), (0.1, 0.0), (0.1, 0.02)])
 def test_residual_equals_kronecker_sum_of_1d_operators(n, p, tau, eps):
     a = (1.0, 0.5)
@@ -128,7 +128,9 @@ def test_residual_equals_kronecker_sum_of_1d_operators(n, p, tau, eps):
     I = np.eye(n * (p + 1))
     ref = np.kron(I, Ax) + np.kron(Ay, I)
     g = _structured_index(x, n, p, xi)
-    assert np.abs(A - ref[np.ix_(g, g)]).max() < 1e-12 * np.abs(ref).max()
+    # scale: the operator's natural size (2/h)(p+1)^2 (1x1, p = 1 central is exactly 0)
+    scale = max(np.abs(ref).max(), 2.0 * n * (p + 1) ** 2)
+    assert np.abs(A - ref[np.ix_(g, g)]).max() < 1e-13 * scale
 
 
 def test_central_flux_is_energy_neutral_and_penalty_dissipates():
@@ -182,3 +184,144 @@ def test_ldg_1d_null_space_is_constants_and_the_wrap_mode():
         m = np.zeros(n * (p + 1))
         m[:p + 1] = npl.legval(xi, np.eye(p + 1)[p])
         assert np.abs(Ld @ m).max() < 1e-9 * lam[-1]
+
+
+# ---------------------------------------------------------------- triangles
+def _tri_dg_reference(mesh, p, a, tau, mu, xu):
+    """Nodal matrix of du/dt for f = a u - mu grad u on a periodic triangle
+    mesh, from the DG weak form with exact integration (FR with the DG
+    correction reproduces it when a and mu are constant).  Physical monomial
+    basis per element, Duffy-collapsed Gauss rule on the element and Gauss
+    rule on the edges; neighbours found by matching edge midpoints modulo the
+    period; LDG: u_hat from the face's R side, q_hat from its L side (L = lower
+    element index); penalty tau (u_self - u_other) out of each side."""
+    E = mesh.conn.shape[0]
+    per = np.array(mesh.period, dtype=float)
+    X = mesh.nodes[mesh.conn]                                  # (E, 3, 2)
+    pw = [(i, j) for i in range(p + 1) for j in range(p + 1 - i)]
+    Nm = len(pw)
+    cen = X.mean(1)
+
+    def basis(e, x):                                           # x (k, 2) -> (k, Nm), grads (k, Nm, 2)
+        y = (x - cen[e]) * 4.0
+        B = np.stack([y[:, 0] ** i * y[:, 1] ** j for i, j in pw], 1)
+        dx = np.stack([i * y[:, 0] ** max(i - 1, 0) * y[:, 1] ** j * 4.0 for i, j in pw], 1)
+        dy = np.stack([j * y[:, 0] ** i * y[:, 1] ** max(j - 1, 0) * 4.0 for i, j in pw], 1)
+        return B, np.stack([dx, dy], -1)
+
+    g, gw = npl.leggauss(p + 3)
+    g, gw = 0.5 * (g + 1.0), 0.5 * gw
+    def vol_rule(e):
+        v0, v1, v2 = X[e]
+        d1, d2 = v1 - v0, v2 - v0
+        area2 = abs(d1[0] * d2[1] - d1[1] * d2[0])
+        s_, t_ = np.meshgrid(g, g, indexing="ij")
+        ws = np.outer(gw, gw) * (1.0 - t_)
+        ss, tt = s_ * (1.0 - t_), t_
+        pts = v0 + ss.reshape(-1, 1) * (v1 - v0) + tt.reshape(-1, 1) * (v2 - v0)
+        return pts, ws.reshape(-1) * area2
+    eg, egw = npl.leggauss(p + 2)
+    eg = 0.5 * (eg + 1.0)
+
+    # edges: (e, k) -> (neighbour, shift) by midpoint matching modulo the period
+    edges = {}
+    for e in range(E):
+        for k in range(3):
+            a0, a1 = X[e, k], X[e, (k + 1) % 3]
+            edges[(e, k)] = (a0, a1, 0.5 * (a0 + a1))
+    nbr = {}
+    for (e, k), (a0, a1, m) in edges.items():
+        for (e2, k2), (b0, b1, m2) in edges.items():
+            if (e2, k2) == (e, k):
+                continue
+            d = m2 - m
+            sh = per * np.round(d / per)
+            if np.allclose(d, sh, atol=1e-12) and (
+                    np.allclose(a0 + sh, b1) and np.allclose(a1 + sh, b0)):
+                nbr[(e, k)] = (e2, sh)
+    assert len(nbr) == 3 * E
+
+    n = E * Nm
+    Mb = np.zeros((n, n))
+    Gx = np.zeros((2, n, n))                                   # M q = G u
+    Kv = np.zeros((n, n))                                      # advective volume + face terms
+    Dq = np.zeros((2, n, n))                                   # viscous terms acting on q
+    sl = lambda e: slice(e * Nm, (e + 1) * Nm)
+    for e in range(E):
+        pts, w = vol_rule(e)
+        B, dB = basis(e, pts)
+        Mb[sl(e), sl(e)] = (B * w[:, None]).T @ B
+        for c in range(2):
+            Gx[c, sl(e), sl(e)] -= (dB[:, :, c] * w[:, None]).T @ B       # -int u d_c v
+            Kv[sl(e), sl(e)] += a[c] * (dB[:, :, c] * w[:, None]).T @ B   # int a_c u d_c v
+            Dq[c, sl(e), sl(e)] -= mu * (dB[:, :, c] * w[:, None]).T @ B  # -int mu q_c d_c v
+        for k in range(3):
+            a0, a1 = X[e, k], X[e, (k + 1) % 3]
+            L = np.linalg.norm(a1 - a0)
+            t = (a1 - a0) / L
+            nrm = np.array([t[1], -t[0]])                      # outward for CCW vertices
+            xs = a0 + eg[:, None] * (a1 - a0)
+            ws = 0.5 * egw * L
+            e2, sh = nbr[(e, k)]
+            Bs, _ = basis(e, xs)
+            Bo, _ = basis(e2, xs + sh)
+            self_L = e < e2
+            an = a @ nrm
+            for c in range(2):
+                # u_hat = trace of the R side
+                Bh = Bo if self_L else Bs
+                Gx[c, sl(e), sl(e2) if self_L else sl(e)] += nrm[c] * (Bs * ws[:, None]).T @ Bh
+                # q_hat = q of the L side: flux out of e gets -mu q_hat . n
+                Bq = Bs if self_L else Bo
+                Dq[c, sl(e), sl(e) if self_L else sl(e2)] += mu * nrm[c] * (Bs * ws[:, None]).T @ Bq
+            # advective common flux and penalty, out of e: -int F v
+            Kv[sl(e), sl(e)] -= (0.5 * an + tau) * (Bs * ws[:, None]).T @ Bs
+            Kv[sl(e), sl(e2)] -= (0.5 * an - tau) * (Bs * ws[:, None]).T @ Bo
+    Mi = np.linalg.inv(Mb)
+    Amod = Mi @ (Kv + sum(Dq[c] @ Mi @ Gx[c] for c in range(2)))
+    V = np.zeros((n, n))
+    for e in range(E):
+        V[sl(e), sl(e)] = basis(e, xu[e])[0]
+    return V @ Amod @ np.linalg.inv(V)
+
+
+def _oracle_tri_matrix(mesh, p, a, tau, eps):
+    prm = Params(gamma=0.0, eps=eps, tau=tau, tau_psi=tau, dt=1e-3)
+    s = Solver(mesh, p, prm, S.Velocity("uniform", a=(a[0], a[1], 0.0)))
+    s.initialize(S.Circle((0.5, 0.5), 0.25, 4.0), precondition=False)
+    shape, Nd = s.phi.shape, s.phi.numel()
+    A = np.zeros((Nd, Nd))
+    z = torch.zeros(shape, dtype=torch.float64)
+    for k in range(Nd):
+        e = torch.zeros(Nd, dtype=torch.float64)
+        e[k] = 1.0
+        A[:, k] = s.rhs(e.reshape(shape), z, 0.0)[0].reshape(-1).numpy()
+    return A, s.xu.numpy()
+
+
+@pytest.mark.parametrize("nx,p", [(1, 1), (1, 2), (1, 3), (2, 2), (2, 3)])
+@pytest.mark.parametrize("tau,eps", [(0.0, 0.0), (0.1, 0.0), (0.1, 0.02)])
+def test_triangle_residual_equals_dg_weak_form(nx, p, tau, eps):
+    a = (1.0, 0.5)
+    mesh = S.tri_split(nx)
+    A, xu = _oracle_tri_matrix(mesh, p, a, tau, eps)
+    ref = _tri_dg_reference(mesh, p, np.array(a), tau, eps * float(np.hypot(*a)), xu)
+    scale = max(np.abs(ref).max(), 2.0 * nx * (p + 1) ** 2)
+    err = np.abs(A - ref).max() / scale
+    assert err < 1e-13
+
+
+def test_triangle_spectra():
+    mesh, p, a = S.tri_split(2), 3, (1.0, 0.5)
+    A0, _ = _oracle_tri_matrix(mesh, p, a, 0.0, 0.0)
+    ev0 = np.linalg.eigvals(A0)
+    assert np.abs(ev0.real).max() < 1e-9 * np.abs(ev0).max()
+    A1, _ = _oracle_tri_matrix(mesh, p, a, 0.1, 0.0)
+    ev1 = np.linalg.eigvals(A1)
+    assert ev1.real.max() < 1e-10 * np.abs(ev1).max() and ev1.real.min() < -1e-3
+    A2, _ = _oracle_tri_matrix(mesh, p, a, 0.1, 0.05)
+    Ld = (A2 - A1) / (0.05 * float(np.hypot(*a)))
+    ev = np.linalg.eigvals(Ld)
+    scale = np.abs(ev).max()
+    assert np.abs(ev.imag).max() < 1e-8 * scale and ev.real.max() < 1e-10 * scale
+    assert np.allclose(Ld @ np.ones(Ld.shape[0]), 0.0, atol=1e-10 * scale)
