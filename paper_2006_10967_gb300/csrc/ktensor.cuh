@@ -131,6 +131,49 @@ __device__ __forceinline__ T metric_c(const T* g, const T* xi, T S[3][3], const 
   return dj;
 }
 
+// One element's metric for the per-point loops of a line pass, where all of
+// a thread's points lie in one element.  Quads hold the six bilinear Jacobian
+// coefficients in registers (an affine map has a zero cross coefficient), so
+// the per-point metric needs no shared-memory reads; with lanes spanning
+// several elements those reads conflict (element records 8 and 16 words
+// apart share banks).  Hexes, whose kernels have no registers to spare,
+// read the record and geometry per point.
+template <int DIM, typename T>
+struct LineMetric {
+  const T* g;
+  const T* mc;
+  __device__ __forceinline__ void load(const T* g_, const T* mc_) {
+    g = g_;
+    mc = mc_;
+  }
+  __device__ __forceinline__ T at(const T* xi, T S[3][3], T* rdj = nullptr) const {
+    return metric_c<DIM>(g, xi, S, mc, rdj);
+  }
+};
+template <typename T>
+struct LineMetric<2, T> {
+  T k[2][3];  // d x_c / d xi = k[c][0] + k[c][2] eta, d x_c / d eta = k[c][1] + k[c][2] xi
+  __device__ __forceinline__ void load(const T* g, const T*) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      k[c][0] = g[c * 4 + 1];
+      k[c][1] = g[c * 4 + 2];
+      k[c][2] = g[c * 4 + 3];
+    }
+  }
+  __device__ __forceinline__ T at(const T* xi, T S[3][3], T* rdj = nullptr) const {
+    T J[3][3];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      J[c][0] = k[c][0] + k[c][2] * xi[1];
+      J[c][1] = k[c][1] + k[c][2] * xi[0];
+    }
+    const T dj = adjugate<2, T>(J, S);
+    if (rdj) *rdj = (T)1 / dj;
+    return dj;
+  }
+};
+
 // Per-element metric record (kMetricRec values of the bulk type), computed
 // once per field from the element geometry: [0..8] the metric at the
 // reference centre, [9] its determinant, [10] the reciprocal, [11] whether
@@ -382,13 +425,15 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       }
       if (a == DIM - 1) {
         // physical gradient at this line's points (all axes are done)
+        LineMetric<DIM, T> em;
+        em.load(gs + lel * NG, mcs + lel * kMetricRec);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const int i = base + j * st;
           T xi[3], Sm[3][3];
           upt_xi<DIM, N>(i, O.x, xi);
           T rdj;
-          metric_c<DIM>(gs + lel * NG, xi, Sm, mcs + lel * kMetricRec, &rdj);
+          em.at(xi, Sm, &rdj);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             T* qp = qt + (lel * NFLD + fsel + q * FS) * DIM * NU + i;
@@ -625,13 +670,14 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       T fa[NFLD][N];  // axis-a transformed flux along this line
       if (kFuse4 && a == 0) {
         const int el = lel;
-        const T* mc = mcs + el * kMetricRec;
+        LineMetric<DIM, T> em;
+        em.load(gs + el * NG, mcs + el * kMetricRec);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const int i = base + j;  // axis-0 lines are contiguous
           T xi[3], Sm[3][3];
           upt_xi<DIM, N>(i, O.x, xi);
-          const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mc);
+          const T dj = em.at(xi, Sm);
           if (MODE == 0) {
             T v[3];
             const T gel = A.ep ? gfe[el] : gfac;
@@ -900,13 +946,15 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
           // every contribution to this line's points is in: du/dt and the
           // RK4 register update, by the line's own thread
           const RKConstF& rkc = rkc_el(lel);
+          LineMetric<DIM, T> em;
+          em.load(gs + lel * NG, mcs + lel * kMetricRec);
 #pragma unroll
           for (int j = 0; j < N; ++j) {
             const int i = base + j * st;
             T xi[3], Sm[3][3];
             upt_xi<DIM, N>(i, O.x, xi);
             T rdj;
-            metric_c<DIM>(gs + lel * NG, xi, Sm, mcs + lel * kMetricRec, &rdj);
+            em.at(xi, Sm, &rdj);
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
               const int fld = fsel + q * FS;
