@@ -236,26 +236,59 @@ struct MinBlocks {
   static constexpr int v = sizeof(T) == 8 ? 1 : (1280 / THREADS < 1 ? 1 : (1280 / THREADS > 8 ? 8 : 1280 / THREADS));
 };
 
+// Blocks of `bytes` dynamic shared memory that fit on one SM (228 KB, 1 KB
+// reserved per block), at most 32.
+__host__ __device__ constexpr int smem_blocks(long bytes) {
+  return 233472 / (bytes + 1024) > 32 ? 32 : (int)(233472 / (bytes + 1024));
+}
+// Tile (elements per block, <= cap) that keeps the most active lanes resident
+// on an SM under the shared-memory and thread limits, counting at most 32
+// warps (beyond that the register file decides); ties go to the larger tile.
+__host__ __device__ constexpr int occupancy_tile(int bytes_el, int per_block, int ln, int cap) {
+  int best = 1;
+  long best_lanes = -1;
+  for (int et = 1; et <= cap; ++et) {
+    const int threads = (et * ln + 31) / 32 * 32;
+    int b = smem_blocks((long)et * bytes_el + per_block);
+    if (b * threads > 2048) b = 2048 / threads;
+    long lanes = (long)b * et * ln;
+    if (lanes > 32 * 32) lanes = 32 * 32;
+    if (lanes >= best_lanes) {
+      best_lanes = lanes;
+      best = et;
+    }
+  }
+  return best;
+}
+
 template <int DIM, int N, typename T, int MODE>
 struct KBLayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
   static constexpr int LN = S::NFP;  // lines per axis per element
+  // Quads stage the velocity cache tiles in shared memory with the state;
+  // hexes read them from global memory where they are used, since the tiles
+  // would take a third of the element's shared memory and cut the resident
+  // warps from 28 to 16 (N = 4).
+  static constexpr bool VT = MODE == 0 && DIM == 2;
   static constexpr int PER_EL_T = NFLD * S::NU          // u, later the divergence
                                   + NFLD * DIM * S::NU  // q~ -> q -> f~
                                   + 2 * NFLD * S::NF    // uo, cor
                                   + S::NG + kMetricRec  // geometry, metric record
-                                  + (MODE == 0 ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
+                                  + (VT ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 57344 / BYTES_EL < 1 ? 1 : 57344 / BYTES_EL;
-  static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr bool OCC = MODE == 0 && DIM == 3;  // tile chosen for resident warps
+  static constexpr int ET = OCC ? occupancy_tile(BYTES_EL, 16 * 13 + 2 * (int)sizeof(T) + 64, LN, ET_T)
+                                : warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
   static constexpr int FS = FRP_FIELD_SPLIT ? NFLD : 1;  // fields split across threads
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
-  static constexpr int MINB = MinBlocks<THREADS, T>::v;
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 13;  // + region alignment
+  static constexpr int SMB = smem_blocks((long)SMEM + ET * 2 * (int)sizeof(T) + 64);
+  static constexpr int MINB = OCC && SMB < MinBlocks<THREADS, T>::v ? SMB : MinBlocks<THREADS, T>::v;
 };
 
 // ============================================================================
@@ -282,8 +315,8 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   T* cor = sc.take<T>(ET * NFLD * NF);        // [ET][NFLD][NF]
   T* gs = sc.take<T>(ET * NG);                // [ET][NG]
   T* mcs = sc.take<T>(ET * kMetricRec);       // [ET][kMetricRec] metric records
-  T* vu = sc.take<T>(MODE == 0 ? ET * DIM * NU : 0);  // MODE 0: velocity cache, solution points
-  T* vf = sc.take<T>(MODE == 0 ? ET * DIM * NF : 0);  // MODE 0: velocity cache, flux points
+  T* vu = sc.take<T>(LY::VT ? ET * DIM * NU : 0);  // velocity cache tiles, solution points
+  T* vf = sc.take<T>(LY::VT ? ET * DIM * NF : 0);  // velocity cache tiles, flux points
   T* chi = sc.take<T>(MODE == 1 ? ET * 2 * NU : 0);   // MODE 1: [ET][2][NU]
   T* nus = sc.take<T>(MODE == 1 ? ET : 0);
   uint16_t* llist = sc.take<uint16_t>(ET * NF);       // [ET*NF] L flux points
@@ -332,10 +365,10 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   if (MODE == 0) tile_async(us, ustg + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
   tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
   tile_async(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne * kMetricRec * (int)sizeof(T));
-  if (MODE == 0 && A.vsu)
-    tile_async(vu, reinterpret_cast<const T*>(A.vsu) + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
-  if (MODE == 0 && A.vsf)
-    tile_async(vf, reinterpret_cast<const T*>(A.vsf) + e0 * DIM * NF, ne * DIM * NF * (int)sizeof(T));
+  const T* vsu = reinterpret_cast<const T*>(A.vsu);
+  const T* vsf = reinterpret_cast<const T*>(A.vsf);
+  if (LY::VT && A.vsu) tile_async(vu, vsu + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
+  if (LY::VT && A.vsf) tile_async(vf, vsf + e0 * DIM * NF, ne * DIM * NF * (int)sizeof(T));
   if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -522,7 +555,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsf) {
-        const T* vc = vf + el * DIM * NF + k;
+        const T* vc = LY::VT ? vf + el * DIM * NF + k : vsf + (e0 + el) * DIM * NF + k;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NF];
       } else {
@@ -593,7 +626,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
       if (A.vsu) {
-        const T* vc = vu + el * DIM * NU + i;
+        const T* vc = LY::VT ? vu + el * DIM * NU + i : vsu + (e0 + el) * DIM * NU + i;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
       } else {
@@ -683,7 +716,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
             const T gel = A.ep ? gfe[el] : gfac;
             const T epsel = A.ep ? epe[el] : P.eps;
             if (A.vsu) {
-              const T* vc = vu + el * DIM * NU + i;
+              const T* vc = LY::VT ? vu + el * DIM * NU + i : vsu + (e0 + el) * DIM * NU + i;
 #pragma unroll
               for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
             } else {

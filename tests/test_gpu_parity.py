@@ -93,6 +93,10 @@ CASES = {
     "hex_periodic_jitter_p2": lambda: _workload(
         lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=4), 2,
         S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 2 / (4 / 3)), 1 / 3),
+    # 64 elements: several full tiles of the p = 3 hex kernels and a ragged one
+    "hex_periodic_jitter_p3": lambda: _workload(
+        lambda: S.hex_grid(4, periodic=(True, True, True), jitter=0.1, seed=5, shuffle_seed=3), 3,
+        S.Velocity("leveque", T=3.0), S.Circle((0.45, 0.5, 0.4), 0.3, 3 * 3 / (4 / 4)), 1 / 4),
 }
 
 
@@ -109,7 +113,8 @@ def test_rhs_parity_fp64(G, case):
         assert _rel(R[1], Ro[1].numpy()) < TOL64, case
 
 
-@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_stream_p5", "hex_periodic_jitter_p2"])
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_stream_p5", "hex_periodic_jitter_p2",
+                                  "hex_periodic_jitter_p3"])
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
 def test_rhs_parity_velocity_evaluated_in_kernel(G, case, precision, tol):
     """The same residual with the velocity evaluated in the kernels instead of
@@ -214,7 +219,8 @@ def test_mass_integral_and_conservation(G, case):
     assert abs(F.mass(0) - m0) < 1e-13 * abs(m0)
 
 
-@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3"])
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3",
+                                  "hex_periodic_jitter_p3"])
 def test_rhs_parity_mixed(G, case):
     w = CASES[case]()
     sol, F = _pair(G, w, precision="mixed")
@@ -227,7 +233,8 @@ def test_rhs_parity_mixed(G, case):
     assert _rel(Rp, sol.rhs_pseudo(sol.psi, sol.phi - 0.5).numpy()) < TOL32
 
 
-@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_stream_p5", "hex_periodic_jitter_p2"])
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_stream_p5", "hex_periodic_jitter_p2",
+                                  "hex_periodic_jitter_p3"])
 def test_mixed_mass_conserved_to_round_off(G, case):
     """Mixed path: each element's float-float solution is corrected so that its
     mass change equals the FP64 sum of its (antisymmetric) face fluxes, so the
