@@ -216,7 +216,6 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
       const int32_t w0 = A.fnbr[(e0 + lel) * NF + k0], w1 = A.fnbr[(e0 + lel) * NF + k1];
       lm[lel * NF + k0] = (unsigned char)(w0 & 1);
       lm[lel * NF + k1] = (unsigned char)(w1 & 1);
-      const int64_t p0 = (int64_t)(w0 >> 1), p1 = (int64_t)(w1 >> 1);
 #pragma unroll
       for (int fld = 0; fld < 2; ++fld) {
         const double* ul = us + (lel * 2 + fld) * NU + base;
@@ -227,8 +226,12 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
           f0 += O.lend[0][j] * v[j];
           f1 += O.lend[1][j] * v[j];
         }
-        const double o0 = (w0 & 1) ? tr[((p0 / NF) * 2 + fld) * NF + p0 % NF] : f0;
-        const double o1 = (w1 & 1) ? tr[((p1 / NF) * 2 + fld) * NF + p1 % NF] : f1;
+        // partner traces: in the own slots with FaceScatter (see ka_tensor),
+        // else in the partner's
+        const int64_t g0 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k0 : (int64_t)(w0 >> 1);
+        const int64_t g1 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k1 : (int64_t)(w1 >> 1);
+        const double o0 = (w0 & 1) ? tr[((g0 / NF) * 2 + fld) * NF + g0 % NF] : f0;
+        const double o1 = (w1 & 1) ? tr[((g1 / NF) * 2 + fld) * NF + g1 % NF] : f1;
         const int fo = (lel * 2 + fld) * NF;
         uf[fo + k0] = f0;
         uf[fo + k1] = f1;

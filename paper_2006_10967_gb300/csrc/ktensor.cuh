@@ -236,6 +236,19 @@ struct MinBlocks {
   static constexpr int v = sizeof(T) == 8 ? 1 : (1280 / THREADS < 1 ? 1 : (1280 / THREADS > 8 ? 8 : 1280 / THREADS));
 };
 
+// Where a kernel finds its partner's face values.  Quads (FaceScatter):
+// the producer writes each value into the slot of the element that reads it
+// (ka_tensor a trace into the L-side partner's slot, kb_tensor a common flux
+// into the R-side partner's slot as well as its own), so both kernels read
+// their partner values from their own slots with loads that do not wait for
+// the connectivity.  Hexes: each value stays in its owner's slot and the
+// reader gathers it through the connectivity (the scattered stores into
+// arrays larger than L2 cost more than the gathers save).
+template <int DIM>
+struct FaceScatter {
+  static constexpr bool v = DIM == 2;
+};
+
 // Blocks of `bytes` dynamic shared memory that fit on one SM (228 KB, 1 KB
 // reserved per block), at most 32.
 __host__ __device__ constexpr int smem_blocks(long bytes) {
@@ -351,14 +364,22 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   const int lel = lin / LN, ll = lin % LN;
   const bool lact = lel < ne && fsel < FS;  // false on the idle lanes of a padded last warp
   // Prefetch this thread's line-end connectivity and partner traces for all
-  // axis passes, so that the dependent global loads overlap the tile load.
+  // axis passes.  With FaceScatter the trace array holds the partner's trace
+  // at each L flux point and both loads are independent; otherwise the
+  // partner traces are gathered below, after the tile copies are issued.
   int32_t wpre[DIM][2];
   T opre[DIM][2][NQ];
   if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) wpre[a][sd] = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+      for (int sd = 0; sd < 2; ++sd) {
+        const int k = (2 * a + sd) * NFP + ll;
+        wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
+        if constexpr (FaceScatter<DIM>::v)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) opre[a][sd][q] = tr[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+      }
   }
   // contiguous tiles: state (both fields), geometry, velocity cache; all in
   // flight together with the connectivity loads above
@@ -369,7 +390,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   const T* vsf = reinterpret_cast<const T*>(A.vsf);
   if (LY::VT && A.vsu) tile_async(vu, vsu + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
   if (LY::VT && A.vsf) tile_async(vf, vsf + e0 * DIM * NF, ne * DIM * NF * (int)sizeof(T));
-  if (lact) {
+  if (!FaceScatter<DIM>::v && lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -517,6 +538,10 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   for (int t = tid; t < nLpts; t += blockDim.x) {
     const int code = llist[t];
     const int el = code / NF, k = code % NF;
+    // partner flux point: the common flux also goes to its slot, where the
+    // partner's ka_tensor lifts it (a wall point is its own partner)
+    const int64_t og = (e0 + el) * NF + k, pg = (int64_t)(A.fnbr[og] >> 1);
+    const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
     T xi[3], Sm[3][3];
@@ -591,6 +616,10 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const T Fp_t = pm * Fp, Fs_t = pm * Fs;
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp_t;
       fc[((e0 + el) * 2 + 1) * NF + k] = Fs_t;
+      if (FaceScatter<DIM>::v && pg != og) {
+        fc[pslot] = Fp_t;
+        fc[pslot + NF] = Fs_t;
+      }
       cor[(el * 2 + 0) * NF + k] = Fp_t;
       cor[(el * 2 + 1) * NF + k] = Fs_t;
 
@@ -609,6 +638,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       for (int j = 0; j < N; ++j) L_ += (s ? O.lend[1][j] : O.lend[0][j]) * us[el * NU + b0 + j * st];
       const T F = pm * (-nus[el] * gn + P.tau_pseudo * (L_ - uo[el * NF + k]));
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
+      if (FaceScatter<DIM>::v && pg != og) fc[pslot + NF] = F;
       cor[el * NF + k] = F;
     }
   }
@@ -866,7 +896,6 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   float2* u2s = sc.take<float2>(PRE ? ET * 2 * NU : 0);  // float-float state, tile order
   float* acs = sc.take<float>(PRE ? ET * 2 * NU : 0);    // RK accumulator
   float2* wds = sc.take<float2>(PRE ? ET * NU : 0);      // w det J (float-float)
-  float* fcs = sc.take<float>(PRE ? ET * 2 * NF : 0);    // own transformed fluxes
   double* tas = sc.take<double>(PRE ? ET * 2 : 0);       // mass-balance accumulator
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
@@ -887,13 +916,23 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   // the mixed path's flux balance, this element's own L-end fluxes
   constexpr bool kCons = sizeof(T) == 4 && MODE == 0;
   const bool cons = kCons && A.tacc != nullptr && stage >= 1;
+  // This element's own transformed common flux at its L points and the
+  // partner's at its R points: with FluxScatter both sit in the own slots
+  // (one independent load per line end), else the R value is gathered from
+  // the partner's slot.
   T fpre[DIM][2][NQ];
   int32_t wpre[DIM][2];
-  if (stage != 0 && lact) {
+  if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) wpre[a][sd] = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
+      for (int sd = 0; sd < 2; ++sd) {
+        const int k = (2 * a + sd) * NFP + ll;
+        wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
+        if (stage != 0)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+      }
   }
   // contiguous tiles, all in flight together with the connectivity loads
   if (MODE == 0) {
@@ -913,21 +952,20 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
     tile_async(u2s, reinterpret_cast<const float2*>(A.u) + e0 * 2 * NU, ne * 2 * NU * 8);
     if (stage >= 2) tile_async(acs, reinterpret_cast<const float*>(A.acc) + e0 * 2 * NU, ne * 2 * NU * 4);
     if (cons) {
-      tile_async(fcs, reinterpret_cast<const float*>(A.fc) + e0 * 2 * NF, ne * 2 * NF * 4);
       if (stage >= 2) tile_async(tas, A.tacc + e0 * 2, ne * 2 * 8);
       if (stage == 4) tile_async(wds, A.wdetf + e0 * NU, ne * NU * 8);
     }
   }
-  if (stage != 0 && lact) {
+  if (!FaceScatter<DIM>::v && stage != 0 && lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int32_t w = wpre[a][sd];
         const int64_t p = (int64_t)(w >> 1);
+        if (!(w & 1))
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-          fpre[a][sd][q] = (w & 1) ? (T)0 : fc[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF];
+          for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF];
       }
   }
   cp_async_wait_all();
@@ -960,13 +998,14 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const int fld = fsel + q * FS;
-          const T c0 = -fpre[a][0][q], c1 = -fpre[a][1][q];
+          // R ends lift minus the partner's F~; L ends were lifted in kb_tensor
+          const bool L0 = wpre[a][0] & 1, L1 = wpre[a][1] & 1;
+          const T c0 = L0 ? (T)0 : -fpre[a][0][q], c1 = L1 ? (T)0 : -fpre[a][1][q];
           if (cons) {
-            // outward transformed flux at both ends: own F~ (L ends, c = 0) or
+            // outward transformed flux at both ends: own F~ (L ends) or
             // -partner F~ (R ends)
             const float2 wf = O.wff[ll];
-            const float* fco = fcs + (lel * 2 + fld) * NF + (2 * a) * NFP + ll;
-            const T o0 = c0 == (T)0 ? fco[0] : c0, o1 = c1 == (T)0 ? fco[NFP] : c1;
+            const T o0 = L0 ? fpre[a][0][q] : c0, o1 = L1 ? fpre[a][1][q] : c1;
             bal[q] = ff_add(bal[q], ff_mul(wf, (float)o0));
             bal[q] = ff_add(bal[q], ff_mul(wf, (float)o1));
           }
@@ -1108,9 +1147,21 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
           t0 += O.lend[0][j] * v;
           t1 += O.lend[1][j] * v;
         }
-        T* trl = tr + ((e0 + lel) * 2 + F0 + fld) * NF;
-        trl[k0] = t0;
-        trl[k1] = t1;
+        if constexpr (FaceScatter<DIM>::v) {
+          // each trace goes where kb_tensor reads it: the L-side partner's
+          // slot at R points, the own slot at walls (own partner); at
+          // interior L points no one reads it
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const int32_t w = wpre[a][sd];
+            const int64_t pg = (int64_t)(w >> 1), og = (e0 + lel) * NF + (sd ? k1 : k0);
+            if (!(w & 1) || pg == og) tr[((pg / NF) * 2 + F0 + fld) * NF + pg % NF] = sd ? t1 : t0;
+          }
+        } else {
+          T* trl = tr + ((e0 + lel) * 2 + F0 + fld) * NF;
+          trl[k0] = t0;
+          trl[k1] = t1;
+        }
       }
     }
   }

@@ -163,10 +163,17 @@ def test_autograd_function_wraps_the_adjoint(G):
     J.backward()
     assert phi0.grad is not None and coef.grad is not None
     assert torch.isfinite(phi0.grad).all() and torch.isfinite(coef.grad).all()
-    # compare with a direct finite difference along phi0
-    h = 1e-6
-    d = torch.randn_like(phi0)
-    with torch.no_grad():
-        jp = 0.5 * (wq * flow(phi0 + h * d, coef).cpu() ** 2).sum()
-        jm = 0.5 * (wq * flow(phi0 - h * d, coef).cpu() ** 2).sum()
-    assert float((phi0.grad * d).sum()) == pytest.approx(float((jp - jm) / (2 * h)), rel=1e-6)
+    # compare with Richardson-extrapolated central differences along a seeded
+    # direction; the bound is relative to |grad J| |d| (the directional
+    # derivative itself can nearly cancel)
+    d = torch.randn(phi0.shape, generator=torch.Generator().manual_seed(7), dtype=phi0.dtype)
+
+    def cd(h):
+        with torch.no_grad():
+            jp = 0.5 * (wq * flow(phi0 + h * d, coef).cpu() ** 2).sum()
+            jm = 0.5 * (wq * flow(phi0 - h * d, coef).cpu() ** 2).sum()
+        return float((jp - jm) / (2 * h))
+
+    fd = (4.0 * cd(5e-7) - cd(1e-6)) / 3.0
+    ad = float((phi0.grad * d).sum())
+    assert abs(ad - fd) <= 1e-7 * float(phi0.grad.norm() * d.norm())
