@@ -366,10 +366,23 @@ def cpu_baseline(S, w, mesh, nsteps):
         sol.rk4_step()
     dt = time.perf_counter() - t0
     ndof = sol.E * sol.Nu
-    return {"value": ndof * 4 * nsteps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
+    # the same oracle on one thread, over a fifth of the sample
+    nthr = torch.get_num_threads()
+    n1 = max(1, nsteps // 5)
+    torch.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        for _ in range(n1):
+            sol.rk4_step()
+        dt1 = time.perf_counter() - t1
+    finally:
+        torch.set_num_threads(nthr)
+    return {"value": ndof * 4 * nsteps / dt, "unit": UNIT, "cores": nthr,
+            "os_cpu_count": os.cpu_count(),
+            "single_thread": {"value": ndof * 4 * n1 / dt1, "unit": UNIT, "steps": n1},
             "kind": "oracle",
             "sample": f"{nsteps} RK4 step(s) (4 residual stages) of the full workload ({w.name}), "
-                      f"FP64 torch-CPU oracle, {dt:.1f} s"}
+                      f"FP64 torch-CPU oracle, {dt:.1f} s; then {n1} step(s) on one thread, {dt1:.1f} s"}
 
 
 def accuracy(G, S, w, mesh, precisions=("fp64", "mixed")):
