@@ -453,8 +453,8 @@ def main():
         wname = w.name
     else:
         n = args.mesh_n or 64
-        w = S.workload("c3", n=n)
-        wname = f"leveque_hex{n}_p3"
+        w = S.workload("c3", n=n, p=args.order or 3)
+        wname = f"leveque_hex{n}_p{w.order}"
     w.normal = args.normal
     if args.normal == "phi":
         wname += "_unpreconditioned"

@@ -272,10 +272,9 @@ def _c2s(n=128, p=3):
     return _finish(w, 2)
 
 
-def _c3(n=64):
-    p = 3
+def _c3(n=64, p=3):
     h = 1.0 / n
-    w = Workload(f"c3_hex{n}_p3_leveque",
+    w = Workload(f"c3_hex{n}_p{p}_leveque",
                  lambda: meshes.hex_grid(n, name=f"hex{n}"), p, Velocity("leveque", T=3.0),
                  Circle((0.35, 0.35, 0.35), 0.15, 3 * p / (4 * h)), t_end=3.0, h=h,
                  precision="mixed")
