@@ -86,7 +86,7 @@ typedef struct fr_field fr_field; /* opaque, host handle to device state */
 typedef struct fr_mesh_desc {
   int32_t dim;           /* 2 or 3 */
   int32_t etype;         /* FR_QUAD, FR_TRI (dim 2) or FR_HEX (dim 3) */
-  int32_t order;         /* p: quad 1..6, tri 1..4, hex 1..5 */
+  int32_t order;         /* p: quad 1..6, tri 1..5, hex 1..5 */
   int32_t reserved;
   int64_t n_nodes;
   const double* nodes;   /* host, n_nodes * dim, node-major */

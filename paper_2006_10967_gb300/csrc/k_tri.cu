@@ -1,4 +1,4 @@
-// Triangle kernel instantiations (p = 1..4, fp64 and mixed).
+// Triangle kernel instantiations (p = 1..5, fp64 and mixed).
 #include "kdispatch.hpp"
 #include "ktri.cuh"
 
@@ -45,7 +45,7 @@ bool kernels_tri(int order, int precision, int64_t E, KernelSet* ks) {
     else fill_tri<P, float>(E, ks);                     \
     return true;
   switch (order) {
-    FRP_T(1) FRP_T(2) FRP_T(3) FRP_T(4)
+    FRP_T(1) FRP_T(2) FRP_T(3) FRP_T(4) FRP_T(5)
     default: return false;
   }
 #undef FRP_T

@@ -128,7 +128,7 @@ int build(const fr_mesh_desc* d, fr_mesh& m) {
   if (!((et == FR_QUAD && dim == 2) || (et == FR_TRI && dim == 2) || (et == FR_HEX && dim == 3)))
     return FR_EINVAL;
   if (p < 1) return FR_EINVAL;
-  if ((et == FR_QUAD && p > 6) || (et == FR_HEX && p > 5) || (et == FR_TRI && p > 4))
+  if ((et == FR_QUAD && p > 6) || (et == FR_HEX && p > 5) || (et == FR_TRI && p > 5))
     return FR_EUNSUPPORTED;
   if (d->n_nodes <= 0 || d->n_elems <= 0 || !d->nodes || !d->conn) return FR_EINVAL;
   m.dim = dim;

@@ -192,7 +192,7 @@ void build_tri(int p, TriRef& t) {
   // Solution points: the Blyth-Pozrikidis map of the Gauss-Legendre nodes
   // v = (g + 1)/2: lattice index (i, j, k), i + j + k = p, goes to the
   // barycentric point l_a = (1 + 2 v_a - v_b - v_c)/3 (symmetric, interior,
-  // positive interpolatory weights for p <= 4)
+  // positive interpolatory weights for p <= 5)
   t.xu.resize(nu * 2);
   int c = 0;
   for (int j = 0; j <= p; ++j)

@@ -84,6 +84,9 @@ CASES = {
     "tri_delaunay_p3": lambda: _workload(
         lambda: S.tri_delaunay(9, seed=2, shuffle_seed=13), 3,
         S.Velocity("rider_kothe", T=8.0), S.Circle((0.5, 0.6), 0.25, 3 * 3 / (4 / 8)), 1 / 8),
+    "tri_delaunay_p5": lambda: _workload(
+        lambda: S.tri_delaunay(7, seed=3, shuffle_seed=5), 5,
+        S.Velocity("rider_kothe", T=8.0), S.Circle((0.5, 0.6), 0.25, 3 * 5 / (4 / 6)), 1 / 6),
     "tri_split_periodic_p2": lambda: _workload(
         lambda: S.tri_split(5, shuffle_seed=1), 2,
         S.Velocity("rotation", a=(0.5, 0.5)), S.Circle((0.5, 0.6), 0.25, 3 * 2 / (4 / 5)), 1 / 5),
@@ -219,8 +222,8 @@ def test_mass_integral_and_conservation(G, case):
     assert abs(F.mass(0) - m0) < 1e-13 * abs(m0)
 
 
-@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3",
-                                  "hex_periodic_jitter_p3"])
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "tri_delaunay_p5",
+                                  "hex_walls_p3", "hex_periodic_jitter_p3"])
 def test_rhs_parity_mixed(G, case):
     w = CASES[case]()
     sol, F = _pair(G, w, precision="mixed")

@@ -8,7 +8,7 @@ import pytest
 from oracle.element import ref_element, _modal_tri, _modal_tensor
 from oracle.polys import gauss_legendre, lagrange_matrix, radau_left_deriv
 
-TYPES = [("quad", p) for p in range(1, 6)] + [("tri", p) for p in range(1, 5)] + \
+TYPES = [("quad", p) for p in range(1, 6)] + [("tri", p) for p in range(1, 6)] + \
         [("hex", p) for p in range(1, 4)]
 
 
@@ -138,7 +138,7 @@ def test_flux_points_on_boundary_and_normals_unit(etype, p):
     assert el.wf.sum() == pytest.approx(meas, rel=1e-13)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_triangle_points_symmetric_interior_positive(p):
     """The triangle's solution points (Blyth-Pozrikidis map of the 1D
     Gauss-Legendre nodes): the set is invariant under the vertex permutations,
