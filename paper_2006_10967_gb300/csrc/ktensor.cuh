@@ -858,8 +858,11 @@ struct KALayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
   static constexpr int LN = S::NFP;
-  // mixed path: float-float state, accumulator, w det J, own fluxes and the
-  // step's mass-balance accumulator staged in shared memory as well
+  // mixed path: float-float state, accumulator, w det J and the step's
+  // mass-balance accumulator staged in shared memory as well, plus 2 NF
+  // words per element that no array uses any more (the own fluxes now come
+  // with the line-end loads): the tile size they give spreads the blocks
+  // better over the SMs than the smaller footprint (measured)
   static constexpr bool PRE = sizeof(T) == 4 && MODE == 0;
   static constexpr int BYTES_EL = (NFLD * S::NU + S::NG + kMetricRec) * (int)sizeof(T) +
                                   (PRE ? 2 * S::NU * 8 + 2 * S::NU * 4 + S::NU * 8 + 2 * S::NF * 4 + 16 : 0);
