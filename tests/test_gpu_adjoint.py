@@ -5,7 +5,9 @@ against central finite differences of the CUDA forward map.
 Loss: J = 1/2 int (phi_T - phi*)^2 with the solution-point quadrature; the
 gradient is taken with respect to phi0 (psi0 = phi0 - 1/2) and the
 stream-function coefficients.  Both adjoints differentiate the same discrete
-map, so they agree to round-off; the tolerance is the benchmark spec's 1e-6.
+map, so they agree to round-off; against finite differences the bound is
+1e-6 relative, the accuracy that Richardson-extrapolated central
+differences of the FP64 forward map reach.
 """
 import numpy as np
 import pytest
