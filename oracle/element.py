@@ -25,8 +25,8 @@ triangle uses the Blyth-Pozrikidis map of the 1D Gauss-Legendre nodes
 v_0 < ... < v_p on [0, 1]: lattice index (i, j, k), i + j + k = p, goes to the
 barycentric point l_a = (1 + 2 v_a - v_b - v_c)/3.  The set is symmetric,
 interior and unisolvent, its interpolatory weights int l_i are positive for
-p <= 5, and the central-flux advection operator on it is close to energy
-neutral (the tests bound the largest real part of its spectrum); the same
+p <= 5, and the advection operator on it (with the penalty tau = 0.1) is close
+to energy neutral (the tests bound the largest real part of its spectrum); the same
 map of equispaced nodes (the principal lattice) gives negative weights and
 advection modes that grow by e^29 over one Rider-Kothe period at p = 3.
 """

@@ -338,7 +338,7 @@ def test_preconditioning_fixed_point_and_sign():
 
 @pytest.mark.parametrize("p", [2, 3, 4])
 def test_triangle_advection_operator_is_nearly_energy_neutral(p):
-    """The central-flux advection operator (gamma = eps = 0) of the
+    """The advection operator (gamma = eps = 0, with the LDG penalty tau = 0.1) of the
     Rider-Kothe field on split and Delaunay triangles has no mode that grows
     by more than e^0.2 over the period T = 8 (max Re lambda < 0.025): the
     triangle solution points keep the collocated flux from exciting growing
