@@ -46,3 +46,31 @@ def test_oracle_adjoint_matches_central_differences(precondition):
         fd = (loss(mesh, p, prm, vel, phi0, phis, n, A=Ap, precondition=precondition)
               - loss(mesh, p, prm, vel, phi0, phis, n, A=Am, precondition=precondition)) / (2 * h)
         assert float(gA[m]) == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+@pytest.mark.parametrize("precondition", [False, True])
+def test_oracle_adjoint_dot_product_with_forward_mode_tangent(precondition):
+    """Dot-product test: the reverse-mode gradient paired with a direction
+    (<dJ/dphi0, dphi> + <dJ/dA, dA>) equals the tangent of J along that
+    direction computed in forward mode (dual numbers through the same march),
+    to round-off: the adjoint is the transpose of the linearised map."""
+    import torch.autograd.forward_ad as fwAD
+    from oracle.adjoint import misfit
+    mesh, p, prm, vel, phi0, phis = _case(precondition)
+    n = 4
+    _, gphi, gA, _ = loss_and_gradients(mesh, p, prm, vel, phi0, phis, n, precondition=precondition)
+    gen = torch.Generator().manual_seed(11)
+    dphi = torch.randn(phi0.shape, generator=gen, dtype=torch.float64)
+    dA = torch.randn(len(vel.A), generator=gen, dtype=torch.float64)
+    sol = Solver(mesh, p, prm, vel)
+    with fwAD.dual_level():
+        ph = fwAD.make_dual(torch.as_tensor(phi0, dtype=torch.float64), dphi)
+        A = fwAD.make_dual(torch.as_tensor(vel.A, dtype=torch.float64), dA)
+        B = torch.as_tensor(vel.B, dtype=torch.float64)
+        sol.initialize(phi=ph, precondition=precondition)
+        for _ in range(n):
+            sol.rk4_step(A, B)
+        tangent = float(fwAD.unpack_dual(misfit(sol, sol.phi, torch.as_tensor(phis))).tangent)
+    paired = float((gphi * dphi).sum() + (gA * dA).sum())
+    scale = float(gphi.norm() * dphi.norm() + gA.norm() * dA.norm())
+    assert abs(paired - tangent) <= 1e-12 * scale
