@@ -32,6 +32,10 @@ MESHES = [
     ("tri", lambda: S.tri_split(4, shuffle_seed=1), 2),
     ("hex", lambda: S.hex_grid(3, periodic=(True, False, True), jitter=0.1, seed=4, shuffle_seed=5), 2),
     ("quad", lambda: S.quad_grid(1), 2),
+    # the highest order of each element type
+    ("tri", lambda: S.tri_delaunay(5, seed=3, shuffle_seed=2), 5),
+    ("quad", lambda: S.quad_grid(3, jitter=0.1, seed=6), 6),
+    ("hex", lambda: S.hex_grid(2, jitter=0.1, seed=7), 5),
 ]
 
 
@@ -59,6 +63,14 @@ def test_invalid_meshes_are_rejected(G):
         G.Mesh(m.nodes, flipped, "quad", 2)
     with pytest.raises(G.FRError) as e:
         G.Mesh(m.nodes, m.conn, "quad", 9)      # order not built
+    assert e.value.code == -6
+    t = S.tri_split(2)
+    with pytest.raises(G.FRError) as e:
+        G.Mesh(t.nodes, t.conn, "tri", 6)
+    assert e.value.code == -6
+    h = S.hex_grid(2)
+    with pytest.raises(G.FRError) as e:
+        G.Mesh(h.nodes, h.conn, "hex", 6)
     assert e.value.code == -6
     bad = m.nodes.copy()
     bad[3, 0] = np.nan
