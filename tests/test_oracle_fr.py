@@ -316,6 +316,31 @@ def test_sensor_closed_forms():
         assert torch.allclose(nu, torch.full_like(nu, 0.15 * (1 + math.sin(-math.pi / 6))), atol=1e-9)
 
 
+def test_sensor_truncation_by_degree():
+    """The truncated modes are those of max degree p (tensor) or total degree
+    p (triangle): their count is (p+1)^d - p^d or p + 1; a polynomial of degree
+    p - 1, sampled at the solution points, has no energy in them (nu = 0) and
+    one of degree p has some."""
+    import numpy as np
+    for et, mesh, d in (("quad", S.quad_grid(1), 2), ("tri", S.tri_split(1), 2), ("hex", S.hex_grid(1), 3)):
+        for p in (2, 3, 4):
+            el = ref_element(et, p)
+            assert int(el.high.sum()) == (p + 1 if et == "tri" else (p + 1) ** d - p ** d)
+            s = _solver(mesh, p, S.Velocity("uniform", a=(1.0, 0.0, 0.0)), s0=-5.0, kappa=5.0, nu_max=0.3)
+            x = s.xu
+            low = (x[..., 0] + 0.3 * x[..., 1]) ** (p - 1) + 0.2
+            top = x[..., 0] ** p + 0.2
+            tot_lo, tot_hi = [], []
+            for u in (low, top):
+                chi = torch.einsum("mi,ei->em", torch.as_tensor(el.Vinv), u)
+                tot_hi.append(float((chi[:, torch.as_tensor(el.high)] ** 2).sum()))
+                tot_lo.append(float((chi ** 2).sum()))
+            assert tot_hi[0] < 1e-24 * tot_lo[0]
+            assert tot_hi[1] > 1e-6 * tot_lo[1]
+            _, nu = s.sensor(low)
+            assert torch.all(nu == 0)
+
+
 def test_preconditioning_fixed_point_and_sign():
     """psi = x - 1/2 (|grad psi| = 1) is a fixed point of the preconditioning equation;
     psi = 2(x - 1/2) relaxes towards slope one (source of Eq. pseudotimesystem)."""
