@@ -67,7 +67,7 @@ extern "C" {
 #define FR_MIXED 1 /* float stage values/fluxes/traces; double solution,
                       RK accumulator, psi0 and mass integral */
 
-#define FR_VEL_UNIFORM 0     /* u = a */
+#define FR_VEL_UNIFORM 0     /* u = a g(t) */
 #define FR_VEL_RIDER_KOTHE 1 /* Section 4.2 field times g(t) */
 #define FR_VEL_LEVEQUE 2     /* Section 4.3 field times g(t) */
 #define FR_VEL_STREAM 3      /* u = dPsi/dy, v = -dPsi/dx,
@@ -109,7 +109,7 @@ typedef struct fr_velocity {
   int32_t kind;          /* FR_VEL_* */
   int32_t n_modes;       /* FR_VEL_STREAM: 1..FR_MAX_MODES */
   double T;              /* g(t) = cos(pi t / T) if T > 0, else 1 */
-  double a[3];           /* FR_VEL_UNIFORM: the velocity; FR_VEL_ROTATION: the centre */
+  double a[3];           /* FR_VEL_UNIFORM: the velocity at g = 1; FR_VEL_ROTATION: the centre */
   const double* kx;      /* host, n_modes each (FR_VEL_STREAM), copied */
   const double* ky;
   const double* A;

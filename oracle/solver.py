@@ -81,9 +81,9 @@ def velocity(vel, x, t, A=None, B=None):
     g = math.cos(pi * t / vel.T) if vel.T > 0 else 1.0
     X = x[..., 0]
     Y = x[..., 1]
-    if vel.kind == "uniform":
+    if vel.kind == "uniform":  # a g(t): steady when T <= 0
         d = x.shape[-1]
-        return torch.tensor(vel.a[:d], dtype=T64).expand(x.shape).clone()
+        return (g * torch.tensor(vel.a[:d], dtype=T64)).expand(x.shape).clone()
     if vel.kind == "rider_kothe":
         u = -torch.sin(pi * X) ** 2 * torch.sin(2 * pi * Y) * g
         v = torch.sin(2 * pi * X) * torch.sin(pi * Y) ** 2 * g
@@ -325,3 +325,7 @@ class Solver:
         """E_L1, E_r of Section 4 against phi_exact at the solution points."""
         el1 = self.integral(torch.abs(self.phi - phi_exact))
         return float(el1), float(el1 / self.integral(phi_exact))
+
+    def mass_error(self, phi0, phi_exact):
+        """E_m of Section 4: (int phi - int phi0) / int phi_exact."""
+        return float((self.integral(self.phi) - self.integral(phi0)) / self.integral(phi_exact))

@@ -182,8 +182,8 @@ __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 template <int DIM, typename R>
 __device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, R* v) {
   switch (V.kind) {
-    case 0:  // uniform
-      for (int c = 0; c < DIM; ++c) v[c] = V.a[c];
+    case 0:  // uniform, a g(t)
+      for (int c = 0; c < DIM; ++c) v[c] = V.a[c] * g;
       break;
     case 1: {  // Rider-Kothe; sin(2 pi a) = 2 sin(pi a) cos(pi a)
       R sx, cx, sy, cy;

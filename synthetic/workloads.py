@@ -18,7 +18,7 @@ from . import meshes
 class Velocity:
     """Analytic velocity field.
 
-    kind: 'uniform'     u = a
+    kind: 'uniform'     u = a g(t)
           'rider_kothe' u = -sin^2(pi x) sin(2 pi y) g(t), v = sin(2 pi x) sin^2(pi y) g(t)
           'leveque'     3D deformation field of Section 4.3 times g(t)
           'stream'      u = dPsi/dy, v = -dPsi/dx with

@@ -369,3 +369,29 @@ def sol_preconditions(n_steps, n_precond):
     """Preconditionings in n_steps steps from set-up (one at set-up, then one
     before every step whose index is a positive multiple of n_precond)."""
     return 1 + sum(1 for k in range(1, n_steps) if k % n_precond == 0)
+
+
+# ---------------------------------------------------------------------------
+# RK4 stage times under a time-dependent velocity (Section 3.1): a uniform
+# field a cos(pi t / T) with T comparable to a few steps, so that a stage
+# evaluated at the wrong time changes the result at first order in dt.
+
+@pytest.mark.parametrize("mk,p", [
+    (lambda: S.quad_grid(5, jitter=0.1, seed=2, shuffle_seed=3, rotate_seed=4), 3),
+    (lambda: S.tri_split(4, shuffle_seed=2), 2),
+    (lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=6), 2),
+])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", 1e-5)])
+def test_time_modulated_uniform_march_parity(G, mk, p, precision, tol):
+    h = 0.25
+    w = _workload(mk, p, S.Velocity("uniform", a=(1.0, 0.5, 0.25), T=0.05),
+                  S.Circle((0.45, 0.55, 0.5), 0.3, 3 * p / (4 * h)), h)
+    w.dt = 0.01
+    w.n_precond = 1000
+    sol, F = _pair(G, w, precision=precision)
+    for nsteps in (1, 5):
+        F.step(nsteps)
+        sol.step(nsteps)
+        assert _rel(F.get(0), sol.phi.numpy()) < tol
+        assert _rel(F.get(1), sol.psi.numpy()) < tol
+    assert F.stats()["t"] == pytest.approx(sol.t, rel=1e-15)
