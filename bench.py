@@ -1,20 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the FR-PCPF hot path: FR DOF-stage updates per second.
 
-Workload: 128 x 128 jittered, shuffled quads on [0,1]^2, p = 4 (409,600
-solution points), Rider-Kothe vortex with T = 8, disk r = 0.15 at (0.5, 0.75),
-the paper's parameters (gamma = 0.09, eps = 0.06 h/p, precondition every
-1000 steps with up to 20 pseudo iterations, s0 = -5).
+Default workload: the 3D deformation test of Section 4.3 on the unit cube,
+64^3 hexahedra, p = 3 (16.8 M solution points), LeVeque field with T = 3,
+sphere r = 0.15 at (0.35, 0.35, 0.35), the paper's parameters (gamma = 0.09,
+eps = 0.06 h/p, precondition every 1000 steps with up to 20 pseudo
+iterations, s0 = -5), mixed precision (FP32 bulk, float-float solution,
+FP64 flux balance and mass integral).
 
 One benchmark step = one pass of the whole hot path: the psi reset and
 pseudo-time preconditioning, 1000 RK4 physical steps (4 FR residual + update
 stages each) and the compensated mass integral.  value = (solution points x
 4 stages x 1000 steps x K steps x ranks) / (max over ranks of the summed
 device time of the K steps).  The L2 cache is flushed (a 512 MiB write)
-before every timed step; within a step the working set (~30 MB) stays in L2.
+before every timed step; the 64^3 working set (~1.8 GB) is larger than L2.
+
+The roofline is the HBM bound with the algorithmic bytes per DOF-stage of
+the two-array-pass model (RK4 registers plus the trace exchange): 82 B
+mixed / 124 B FP64 for hex p = 3.  Secondary lines: the plain FP64 path on
+the same workload, and the 128^2 jittered quad p = 4 Rider-Kothe workload.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (single RK4 steps), on the same metric.
+sample of the same workload (single RK4 steps on a 32^3 sub-grid of the
+same problem), on the same metric.
 """
 import argparse
 import ctypes as C
@@ -42,10 +50,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison (0: skip)")
-    ap.add_argument("--cpu-steps", type=int, default=25, help="oracle RK4 steps for cpu_baseline (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=100,
+                    help="RK4 steps timed for the FP64 comparison on the same workload (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=3, help="oracle RK4 steps for cpu_baseline (0: skip)")
+    ap.add_argument("--cpu-mesh-n", type=int, default=None,
+                    help="elements per side of the oracle's sample (c3: 32, a sub-grid of the same problem)")
     ap.add_argument("--mesh-n", type=int, default=None,
-                    help="elements per side (c2q: 128, the benchmark workload; c3: 64)")
+                    help="elements per side (c3: 64, the benchmark workload; c2q: 128)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 128^2 quad p = 4 secondary line")
     ap.add_argument("--accuracy", action="store_true", help="also run both precisions to t = T and report E_L1")
     ap.add_argument("--accuracy-precision", default="both", choices=["both", "mixed", "fp64"],
                     help="precisions of the --accuracy runs")
@@ -54,9 +66,9 @@ def parse():
                     help="interface normal: psi (preconditioned method) or phi (unpreconditioned CPF)")
     ap.add_argument("--order", type=int, default=None,
                     help="zalesak/rudman: polynomial order (default 4); c2s: (default 3)")
-    ap.add_argument("--workload", default="c2q", choices=["c2q", "c2t", "c2s", "c3", "c4", "zalesak", "rudman"],
-                    help="c2q: 128^2 jittered quads p=4 (the benchmark); c2t: ~30k Delaunay triangles p=3; "
-                         "c3: 64^3 hexes p=3 (LeVeque); c4: 256-instance quad ensemble (200 steps per step); "
+    ap.add_argument("--workload", default="c3", choices=["c2q", "c2t", "c2s", "c3", "c4", "zalesak", "rudman"],
+                    help="c3: 64^3 hexes p=3 (LeVeque; the benchmark); c2q: 128^2 jittered quads p=4; "
+                         "c2t: ~30k Delaunay triangles p=3; c4: 256-instance quad ensemble (200 steps per step); "
                          "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads); "
                          "c2s: Rider-Kothe on split-triangle meshes (--mesh-n, --order <= 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
@@ -145,26 +157,22 @@ class Clocks:
 KB_GRAPH_LAUNCHES = 400
 
 
-def alg_flops_per_dof(dim, p):
-    """Algorithmic flops per solution point per RK stage of the residual kernel
-    (Steps 1-6, both fields, sum-factorised tensor operators; an FMA counts 2).
-    Velocity evaluation and metric terms are excluded (they depend on whether
-    they are stored or recomputed)."""
+def alg_bytes_per_dof(etype, p, precision):
+    """Algorithmic HBM bytes per solution point per RK stage (a lower bound:
+    every array touched once, geometry and velocity recomputed).
+
+    RK4 registers of both fields over the 4 stages: 16 array passes per step
+    (stage 1 reads u^n and writes acc and U_2; stages 2-3 read U_s, u^n, acc
+    and write acc, U_s+1; stage 4 reads U_4, acc and writes u^n+1), 2 fields,
+    / 4 stages: 8 P per DOF-stage in FP64 (64 B), 52 B in the mixed path
+    (FP32 stage values, FP64 u^n and accumulator).  Trace exchange per element
+    flux point: both fields' traces written and read by the neighbour (4 P_b)
+    plus the one-sided viscous normal flux (P_b): 5 P_b Nf / Nu."""
     n = p + 1
-    nu = n ** dim
-    nf = 2 * dim * n ** (dim - 1)
-    r = nf / nu
-    f = 0.0
-    f += 2 * r * n * 2                       # Step 1 traces, 2 fields
-    f += 2 * dim * (n * 2 + 2 * 2)           # Step 3 reference gradient + two line corrections
-    f += 2 * dim * dim * 2                   # q = J^-T q~
-    f += 0.5 * r * 2 * dim * n * 2           # q^f at L flux points
-    f += 0.5 * r * (8 * dim + 14)            # Step 5 common flux (normal, speeds, fluxes, penalty)
-    f += 6 * dim + 10                        # Step 4 pointwise fluxes (|v|, |q_psi|, sharpening)
-    f += 2 * dim * dim * 2                   # f~ = det J J^-1 f
-    f += 2 * r * n * 2 + 2 * r               # discontinuous normal flux and jump
-    f += 2 * dim * (n * 2 + 2 * 2)           # Step 6 divergence + two line lifts
-    return f
+    nu = {"quad": n * n, "hex": n ** 3, "tri": n * (n + 1) // 2}[etype]
+    nf = {"quad": 4 * n, "hex": 6 * n * n, "tri": 3 * n}[etype]
+    rk, pb = (52.0, 4) if precision == "mixed" else (64.0, 8)
+    return rk + 5 * pb * nf / nu
 
 
 def source_sha():
@@ -174,17 +182,18 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if its kernel
-    source hash matches the current source (else None)."""
+def load_traffic(key):
+    """Cold-cache DRAM bytes per solution point of one RK stage (kb + ka of
+    the physical step) from the committed ncu summary, if its kernel source
+    hash matches the current source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    ent = d.get(kernel_key)
+    ent = d.get(key)
     if not ent or ent.get("source_sha") != source_sha():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get("dram_bytes_per_dof")
 
 
 def peaks():
@@ -211,7 +220,10 @@ def oracle_init(sol, S, w):
 
 
 # ---------------------------------------------------------------------------
-def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False, vel_cache=True):
+def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=False, e2e=False, vel_cache=True,
+             rk_steps=STEPS_PER_BENCH_STEP):
+    """K timed steps of rk_steps RK4 steps (plus the preconditioning due among
+    them and the mass integral), after W untimed ones."""
     import torch
     M = G.Mesh.from_synthetic(mesh, w.order)
     P = G.make_params(w, precision, vel_cache=vel_cache)
@@ -219,10 +231,10 @@ def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=Fal
     ndof = M.info.n_dof
     stream = torch.cuda.current_stream()
     for _ in range(W):
-        F.step(STEPS_PER_BENCH_STEP)
+        F.step(rk_steps)
         F.mass(0)
     torch.cuda.synchronize()
-    out = {"ndof": ndof}
+    out = {"ndof": ndof, "rk_steps": rk_steps}
     clocks = Clocks(torch.cuda.current_device())
     times = []
     barrier(world)
@@ -234,7 +246,7 @@ def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=Fal
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        F.step(STEPS_PER_BENCH_STEP)
+        F.step(rk_steps)
         F.mass(0)
         e1.record(stream)
         e1.synchronize()
@@ -244,12 +256,12 @@ def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=Fal
     out["clocks"] = clocks.stop()
     total_ms = max_over_ranks(sum(times), world)
     out["ms_per_step"] = total_ms / K
-    out["value"] = world * K * STEPS_PER_BENCH_STEP * 4 * ndof / (total_ms * 1e-3)
+    out["value"] = world * K * rk_steps * 4 * ndof / (total_ms * 1e-3)
     out["status"] = F.sync()
     if want_kernel:
         flush.zero_()
         F.profile(True)
-        F.step(STEPS_PER_BENCH_STEP)
+        F.step(rk_steps)
         prof = F.profile_read()
         F.profile(False)
         out["kernels"] = prof
@@ -267,18 +279,19 @@ def run_path(G, S, w, mesh, precision, K, W, world, rank, flush, want_kernel=Fal
         ptr = lambda t: C.cast(C.c_void_p(t.data_ptr()), dp)
         m = C.c_double()
         times = []
-        for _ in range(K):
+        Ke = min(K, 3)   # end-to-end steps (each moves the state through host memory)
+        for _ in range(Ke):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             G.check(L.fr_field_set(F.handle, 0, ptr(phi), sp), "fr_field_set")
             G.check(L.fr_field_set(F.handle, 1, ptr(psi), sp), "fr_field_set")
-            G.check(L.fr_step(F.handle, STEPS_PER_BENCH_STEP, sp), "fr_step")
+            G.check(L.fr_step(F.handle, rk_steps, sp), "fr_step")
             G.check(L.fr_mass_integral(F.handle, 0, C.byref(m), sp), "fr_mass_integral")
             G.check(L.fr_field_get(F.handle, 0, ptr(res), sp), "fr_field_get")
             times.append(time.perf_counter() - t0)
         tot = max_over_ranks(sum(times), world)
-        out["e2e"] = {"value": world * K * STEPS_PER_BENCH_STEP * 4 * ndof / tot, "unit": UNIT,
+        out["e2e"] = {"value": world * Ke * rk_steps * 4 * ndof / tot, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 2 * ndof * 8, "d2h_bytes_per_step": ndof * 8 + 8}
     return out, F
 
@@ -356,7 +369,10 @@ def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_ste
             "per_order": per_order, "status": status, "rk_steps": rk_steps, "instances": n_inst}
 
 
-def cpu_baseline(S, w, mesh, nsteps):
+def cpu_baseline(S, w, mesh, nsteps, sample_note):
+    """The FP64 torch-CPU oracle on the host cores: nsteps RK4 steps with all
+    threads, then one step on one thread, on `mesh` (the workload or a
+    sub-grid of the same problem, described by sample_note)."""
     import torch
     from oracle import Params, Solver
     sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
@@ -366,23 +382,20 @@ def cpu_baseline(S, w, mesh, nsteps):
         sol.rk4_step()
     dt = time.perf_counter() - t0
     ndof = sol.E * sol.Nu
-    # the same oracle on one thread, over a fifth of the sample
     nthr = torch.get_num_threads()
-    n1 = max(1, nsteps // 5)
     torch.set_num_threads(1)
     try:
         t1 = time.perf_counter()
-        for _ in range(n1):
-            sol.rk4_step()
+        sol.rk4_step()
         dt1 = time.perf_counter() - t1
     finally:
         torch.set_num_threads(nthr)
     return {"value": ndof * 4 * nsteps / dt, "unit": UNIT, "cores": nthr,
             "os_cpu_count": os.cpu_count(),
-            "single_thread": {"value": ndof * 4 * n1 / dt1, "unit": UNIT, "steps": n1},
+            "single_thread": {"value": ndof * 4 / dt1, "unit": UNIT, "steps": 1},
             "kind": "oracle",
-            "sample": f"{nsteps} RK4 step(s) (4 residual stages) of the full workload ({w.name}), "
-                      f"FP64 torch-CPU oracle, {dt:.1f} s; then {n1} step(s) on one thread, {dt1:.1f} s"}
+            "sample": f"{nsteps} RK4 step(s) (4 residual stages) of {sample_note}, "
+                      f"FP64 torch-CPU oracle, {dt:.1f} s; then 1 step on one thread, {dt1:.1f} s"}
 
 
 def accuracy(G, S, w, mesh, precisions=("fp64", "mixed")):
@@ -436,45 +449,31 @@ def main():
         if rank == 0:
             print(json.dumps(line))
         return
-    if args.workload == "c2q":
-        n = args.mesh_n or 128
-        w = S.workload("c2q", n=n)
-        wname = f"rider_kothe_quad{n}_jitter_p4"
-    elif args.workload == "c2t":
-        w = S.workload("c2t")
-        wname = "rider_kothe_tri_delaunay_p3"
-    elif args.workload == "c2s":
-        n = args.mesh_n or 128
-        w = S.workload("c2s", n=n, p=args.order or 3)
-        wname = f"rider_kothe_trisplit{n}_p{w.order}"
-    elif args.workload in ("zalesak", "rudman"):
-        n = args.mesh_n or (100 if args.workload == "zalesak" else 200)
-        w = S.workload(args.workload, n=n, p=args.order or 4)
-        wname = w.name
-    else:
-        n = args.mesh_n or 64
-        w = S.workload("c3", n=n, p=args.order or 3)
-        wname = f"leveque_hex{n}_p{w.order}"
+    w, wname = select_workload(S, args.workload, args.mesh_n, args.order)
     w.normal = args.normal
     if args.normal == "phi":
         wname += "_unpreconditioned"
     mesh = w.mesh()
-    nu_el = {"quad": (w.order + 1) ** 2, "tri": (w.order + 1) * (w.order + 2) // 2, "hex": (w.order + 1) ** 3}[mesh.etype]
-    workload_cfg = {"workload": wname, "normal": {"psi": "grad psi (preconditioned)",
-                                                  "phi": "grad phi (unpreconditioned CPF)"}[args.normal],
-                    "elements": mesh.n_elems, "order": w.order,
-                    "solution_points": mesh.n_elems * nu_el, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
-                    "stages_per_rk_step": 4, "precondition_every": w.n_precond, "pseudo_kmax": w.pseudo_kmax,
-                    "l2": "flushed before each timed step (512 MiB write); working set L2-resident within a step",
-                    "parallelism": f"replicas x{world}"}
+    workload_cfg = workload_config(w, wname, mesh, args.normal, world)
+    # the oracle's bounded sample: the workload itself, or for the 64^3 hex
+    # workload a 32^3 sub-grid of the same problem (same order, field and
+    # parameters; the rate is per DOF-stage)
+    cpu_n = args.cpu_mesh_n or (32 if args.workload == "c3" and (args.mesh_n or 64) > 32 else None)
+    if cpu_n is not None:
+        w_cpu, cpu_name = select_workload(S, args.workload, cpu_n, args.order)
+        w_cpu.normal = args.normal
+        cpu_note = f"the same problem on a {cpu_n}^3 sub-grid ({cpu_name}, {cpu_n ** 3} elements)"
+    else:
+        w_cpu, cpu_note = w, f"the full workload ({wname})"
 
     if args.impl == "reference":
         if rank != 0:
             return
         import torch
         from oracle import Params, Solver
-        sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
-        oracle_init(sol, S, w)
+        mesh_cpu = w_cpu.mesh() if w_cpu is not w else mesh
+        sol = Solver(mesh_cpu, w_cpu.order, Params.from_workload(w_cpu), w_cpu.velocity)
+        oracle_init(sol, S, w_cpu)
         for _ in range(args.warmup):
             sol.rk4_step()
         t0 = time.perf_counter()
@@ -488,7 +487,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": dict(workload_cfg, reference_step="one RK4 step of the oracle"),
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                                 "sample": f"{args.steps} RK4 steps of the full workload after {args.warmup} warm-up"},
+                                 "sample": f"{args.steps} RK4 steps of {cpu_note} after {args.warmup} warm-up"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -502,41 +501,20 @@ def main():
     vc = not args.no_vel_cache
     main_out, F = run_path(G, S, w, mesh, args.precision, args.steps, max(args.warmup, 3), world, rank, flush,
                            want_kernel=True, e2e=True, vel_cache=vc)
+    del F
     fp64_out = None
     if args.precision == "mixed" and args.fp64_steps > 0:
-        fp64_out, _ = run_path(G, S, w, mesh, "fp64", args.fp64_steps, 1, world, rank, flush, want_kernel=True,
-                               vel_cache=vc)
+        fp64_out, F64 = run_path(G, S, w, mesh, "fp64", 1, 1, world, rank, flush, want_kernel=True,
+                                 vel_cache=vc, rk_steps=args.fp64_steps)
+        del F64
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel (kb: the physical residual + common flux)
-    kern = main_out["kernels"]
-    dom = "kb_phys"
-    ms_launch = main_out["kb_graph_ms"]
-    pk = peaks()
-    sm_max = pk.get("sm_max_mhz", 2070.0)
-    if args.precision == "mixed":
-        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 lanes x FMA x clock
-        peak_note = "FP32: 152 SM x 128 lanes x 2 flop x max SM clock"
-    else:
-        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12     # FP64: 2 DFMA/clk/SM
-        peak_note = "FP64: 152 SM x 2 DFMA x 2 flop x max SM clock"
-    ndof = main_out["ndof"]
-    flops_launch = alg_flops_per_dof(mesh.dim, w.order) * ndof
-    achieved = flops_launch / (ms_launch * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak,
-            "traffic": load_traffic(f"kb_phys_{args.workload}_{args.precision}"),
-            "peak_source": peak_note + " (derived, nominal units and clocks)",
-            "avg_launch_us": ms_launch * 1e3,
-            "timing": f"CUDA events around a CUDA graph of {KB_GRAPH_LAUNCHES} back-to-back launches on the "
-                      "benchmark state, after the timed region",
-            "event_pair_us": {k: v[0] / v[1] * 1e3 for k, v in kern.items() if v[1]},
-            "share_of_step": kern[dom][0] / sum(v[0] for v in kern.values()),
-            "alg_flops_per_launch": flops_launch}
-
+    roof = roofline(main_out, mesh.etype, w.order, args.precision, args.workload)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_steps > 0:
-        cpu = cpu_baseline(S, w, mesh, args.cpu_steps)
+        cpu = cpu_baseline(S, w_cpu, w_cpu.mesh() if w_cpu is not w else mesh, args.cpu_steps, cpu_note)
 
+    kern = main_out["kernels"]
     line = {"metric": METRIC, "value": main_out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": main_out["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -546,16 +524,96 @@ def main():
             "gpu_launches": int(sum(v[1] for v in kern.values())) * args.steps + 3 * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "status": main_out["status"]}
     if fp64_out is not None:
-        line["fp64"] = {"value": fp64_out["value"], "ms_per_step": fp64_out["ms_per_step"],
-                        "kb_phys_avg_us": fp64_out["kernels"]["kb_phys"][0] / fp64_out["kernels"]["kb_phys"][1] * 1e3}
+        line["fp64"] = {"value": fp64_out["value"], "rk_steps_timed": fp64_out["rk_steps"],
+                        "roofline": roofline(fp64_out, mesh.etype, w.order, "fp64", args.workload),
+                        "note": "the plain FP64 path on the same workload, one timed window of RK4 steps"}
         line["speedup_mixed_over_fp64"] = main_out["value"] / fp64_out["value"]
     if args.accuracy:
         line["accuracy"] = accuracy(G, S, w, mesh, {"both": ("fp64", "mixed"), "mixed": ("mixed",),
                                                     "fp64": ("fp64",)}[args.accuracy_precision])
+    if not args.no_secondary and args.workload == "c3" and args.mesh_n in (None, 64) and args.order in (None, 3):
+        w2, n2 = select_workload(S, "c2q", 128, None)
+        sec, F2 = run_path(G, S, w2, w2.mesh(), args.precision, args.steps, max(args.warmup, 3), world, rank,
+                           flush, want_kernel=True, vel_cache=vc)
+        del F2
+        line["secondary"] = {"workload": n2, "value": sec["value"], "unit": UNIT, "ms_per_step": sec["ms_per_step"],
+                             "solution_points": sec["ndof"], "precision": args.precision,
+                             "roofline": roofline(sec, "quad", 4, args.precision, "c2q"),
+                             "note": "working set (~30 MB) L2-resident within a step; latency bound"}
     if not args.no_adjoint and world == 1:
         line["adjoint"] = adjoint_ratio(G, S)
     if rank == 0:
         print(json.dumps(line))
+
+
+def select_workload(S, name, mesh_n, order):
+    if name == "c2q":
+        n = mesh_n or 128
+        return S.workload("c2q", n=n), f"rider_kothe_quad{n}_jitter_p4"
+    if name == "c2t":
+        return S.workload("c2t"), "rider_kothe_tri_delaunay_p3"
+    if name == "c2s":
+        n = mesh_n or 128
+        w = S.workload("c2s", n=n, p=order or 3)
+        return w, f"rider_kothe_trisplit{n}_p{w.order}"
+    if name in ("zalesak", "rudman"):
+        n = mesh_n or (100 if name == "zalesak" else 200)
+        w = S.workload(name, n=n, p=order or 4)
+        return w, w.name
+    n = mesh_n or 64
+    w = S.workload("c3", n=n, p=order or 3)
+    return w, f"leveque_hex{n}_p{w.order}"
+
+
+def workload_config(w, wname, mesh, normal, world):
+    nu_el = {"quad": (w.order + 1) ** 2, "tri": (w.order + 1) * (w.order + 2) // 2,
+             "hex": (w.order + 1) ** 3}[mesh.etype]
+    ndof = mesh.n_elems * nu_el
+    big = ndof * 2 * 4 * 6 > 129e6
+    return {"workload": wname, "normal": {"psi": "grad psi (preconditioned)",
+                                          "phi": "grad phi (unpreconditioned CPF)"}[normal],
+            "elements": mesh.n_elems, "order": w.order,
+            "solution_points": ndof, "rk_steps_per_step": STEPS_PER_BENCH_STEP,
+            "stages_per_rk_step": 4, "precondition_every": w.n_precond, "pseudo_kmax": w.pseudo_kmax,
+            "l2": ("flushed before each timed step (512 MiB write); working set larger than L2" if big else
+                   "flushed before each timed step (512 MiB write); working set L2-resident within a step"),
+            "parallelism": f"replicas x{world}"}
+
+
+def roofline(out, etype, p, precision, workload):
+    """HBM roofline of one RK stage (the kb + ka launch pair of the physical
+    step): algorithmic bytes per DOF-stage x solution points / stage time,
+    with the stage time taken from the CUDA-event timed region (which also
+    holds the preconditioning and the mass integral, so the figure is a lower
+    bound), against the measured HBM copy bandwidth."""
+    import torch
+    ndof = out["ndof"]
+    b_alg = alg_bytes_per_dof(etype, p, precision)
+    stage_s = ndof / out["value"]                    # seconds per stage, all ranks' work per rank
+    achieved = b_alg * ndof / stage_s / 1e9
+    pk = peaks()
+    peak = pk.get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    if not peak:
+        peak, src = 6800.0, "fallback 6.8 TB/s"
+    kern = out.get("kernels", {})
+    stage_kern = {k: {"avg_us": v[0] / v[1] * 1e3, "launches": v[1]} for k, v in kern.items() if v[1]}
+    tot = sum(v[0] for v in kern.values()) or 1.0
+    for k, v in kern.items():
+        if v[1]:
+            stage_kern[k]["share_of_step"] = v[0] / tot
+    traffic_dof = load_traffic(f"stage_{workload}_{etype}_p{p}_{precision}")
+    return {"bound": "hbm", "kernel": "RK stage: kb_tensor + ka_tensor" if etype != "tri" else
+            "RK stage: kb_tri + ka_tri",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_dof * ndof if traffic_dof else None,
+            "alg_bytes_per_dof_stage": b_alg, "stage_us": stage_s * 1e6,
+            "peak_source": src, "sm_count": torch.cuda.get_device_properties(0).multi_processor_count,
+            "timing": "stage time = timed region (CUDA events on the launching stream) / (RK steps x 4)",
+            "kernels_profiled": stage_kern,
+            "kb_graph_us": out["kb_graph_ms"] * 1e3 if out.get("kb_graph_ms") else None,
+            "traffic_note": "cold-cache dram__bytes_read.sum + dram__bytes_write.sum of kb + ka per stage from "
+                            "a small ncu capture, scaled by solution points (null: none at this source)"}
 
 
 if __name__ == "__main__":
