@@ -182,7 +182,9 @@ typedef struct fr_stats {
  * physical position).  The L side of an interior face is the lower element
  * number.  Unmatched faces are walls (copy ghost states, Section 3.3).
  * Errors: FR_EINVAL (bad dim/type/order/index, face shared by > 2 elements,
- * non-coinciding flux points, det J <= 0), FR_ENOMEM, FR_EUNSUPPORTED. */
+ * non-coinciding flux points, det J <= 0), FR_ENOMEM, FR_EUNSUPPORTED (order
+ * not built, or n_elems * Nf >= 2^30: the packed partner index of a flux
+ * point, 2 (e Nf + k) + L, is an int32; checked before the arrays are read). */
 int fr_mesh_create(const fr_mesh_desc* desc, fr_mesh** out);
 int fr_mesh_info_get(const fr_mesh* mesh, fr_mesh_info* info);
 /* Physical solution-point coordinates, host out[n_dof * dim] (point-major). */

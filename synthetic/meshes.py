@@ -85,8 +85,35 @@ def quad_grid(nx, ny=None, lengths=(1.0, 1.0), periodic=(True, True), jitter=0.0
     return Mesh("quad", nodes, conn.astype(np.int64), tuple(periodic), tuple(lengths), name)
 
 
+def _hex_rotations():
+    """The 24 proper rotations of the reference cube as permutations of the
+    8 vertex slots: perm[k] is the old local vertex at R (ref corner k), so
+    that the new map is x_old(R xi) and det J keeps its sign."""
+    import itertools
+    ref = [(-1, -1, -1), (1, -1, -1), (1, 1, -1), (-1, 1, -1),
+           (-1, -1, 1), (1, -1, 1), (1, 1, 1), (-1, 1, 1)]
+    index = {c: k for k, c in enumerate(ref)}
+    out = []
+    for axes in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=int)
+            for a in range(3):
+                R[a, axes[a]] = signs[a]
+            if round(np.linalg.det(R)) != 1:
+                continue
+            out.append([index[tuple(int(v) for v in R @ np.array(c))] for c in ref])
+    return np.array(out, dtype=np.int64)
+
+
 def hex_grid(nx, ny=None, nz=None, lengths=(1.0, 1.0, 1.0), periodic=(False, False, False),
-             jitter=0.0, seed=1, shuffle_seed=None, name=""):
+             jitter=0.0, seed=1, shuffle_seed=None, rotate_seed=None, name=""):
+    """nx x ny x nz hexahedra on [0,Lx]x[0,Ly]x[0,Lz].
+
+    rotate_seed: give each element's vertex list one of the 24 proper
+                 rotations of the reference cube (seeded), so that
+                 neighbouring elements see a shared face in different
+                 orientations (all 8 point orderings of a face occur).
+    """
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     ns = (nx, ny, nz)
@@ -101,6 +128,10 @@ def hex_grid(nx, ny=None, nz=None, lengths=(1.0, 1.0, 1.0), periodic=(False, Fal
                      nid(i, j, k + 1), nid(i + 1, j, k + 1), nid(i + 1, j + 1, k + 1),
                      nid(i, j + 1, k + 1)], axis=1)
     conn = _reorder(conn, shuffle_seed, None, 8)
+    if rotate_seed is not None:
+        rots = _hex_rotations()
+        r = np.random.default_rng(rotate_seed).integers(0, len(rots), size=conn.shape[0])
+        conn = np.take_along_axis(conn, rots[r], axis=1)
     return Mesh("hex", nodes, conn.astype(np.int64), tuple(periodic), tuple(lengths), name)
 
 

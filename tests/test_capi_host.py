@@ -36,6 +36,8 @@ MESHES = [
     ("tri", lambda: S.tri_delaunay(5, seed=3, shuffle_seed=2), 5),
     ("quad", lambda: S.quad_grid(3, jitter=0.1, seed=6), 6),
     ("hex", lambda: S.hex_grid(2, jitter=0.1, seed=7), 5),
+    # every hex carries one of the 24 rotations of its vertex list
+    ("hex", lambda: S.hex_grid(3, periodic=(True, True, False), jitter=0.1, seed=4, rotate_seed=9), 3),
 ]
 
 
@@ -96,3 +98,26 @@ def test_workspace_size_and_param_validation(G):
     p.dt = -1.0
     assert G.lib().fr_field_workspace_bytes(M.handle, C.byref(p), C.byref(n)) == -1
     assert G.lib().fr_strerror(-4) == b"non-finite value in the state"
+
+
+def test_partner_index_width_is_guarded(G):
+    """The packed partner index of a flux point (2 (e Nf + k) + L bit) is an
+    int32: a mesh with E Nf >= 2^30 is refused before its arrays are read."""
+    from paper_2006_10967_gb300 import _capi as capi
+    d = capi.fr_mesh_desc()
+    d.dim, d.etype, d.order = 3, 2, 5            # hex, p = 5: Nf = 216
+    nodes = np.zeros(24)
+    conn = np.zeros(8, dtype=np.int64)
+    d.n_nodes = 8
+    d.nodes = nodes.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_elems = (1 << 30) // 216 + 1               # the arrays are far shorter than this
+    d.conn = conn.ctypes.data_as(C.POINTER(C.c_int64))
+    h = C.c_void_p()
+    assert G.lib().fr_mesh_create(C.byref(d), C.byref(h)) == -6
+    assert not h.value
+    d.n_elems = 1                                   # a one-element mesh with the same descriptor builds
+    nodes[:] = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                         [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], dtype=float).ravel()
+    conn[:] = np.arange(8)
+    assert G.lib().fr_mesh_create(C.byref(d), C.byref(h)) == 0
+    G.lib().fr_mesh_destroy(h)

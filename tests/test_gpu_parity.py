@@ -96,6 +96,14 @@ CASES = {
     "hex_periodic_jitter_p2": lambda: _workload(
         lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=4), 2,
         S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 2 / (4 / 3)), 1 / 3),
+    # every hex with one of the 24 rotations of its vertex list: shared faces
+    # meet in all 8 relative orientations of their point grids
+    "hex_rotated_walls_p3": lambda: _workload(
+        lambda: S.hex_grid(3, shuffle_seed=2, rotate_seed=5), 3,
+        S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 3 / (4 / 3)), 1 / 3),
+    "hex_rotated_periodic_jitter_p2": lambda: _workload(
+        lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=4, rotate_seed=6), 2,
+        S.Velocity("leveque", T=3.0), S.Circle((0.4, 0.45, 0.5), 0.3, 3 * 2 / (4 / 3)), 1 / 3),
     # 64 elements: several full tiles of the p = 3 hex kernels and a ragged one
     "hex_periodic_jitter_p3": lambda: _workload(
         lambda: S.hex_grid(4, periodic=(True, True, True), jitter=0.1, seed=5, shuffle_seed=3), 3,
@@ -142,7 +150,7 @@ def test_pseudo_rhs_parity_fp64(G, case):
     assert _rel(R, Ro) < TOL64, case
 
 
-@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "tri_delaunay_p3", "hex_walls_p3"])
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "tri_delaunay_p3", "hex_walls_p3", "hex_rotated_walls_p3"])
 def test_rk_steps_and_preconditioning_parity_fp64(G, case):
     w = CASES[case]()
     w.n_precond = 2
@@ -223,7 +231,8 @@ def test_mass_integral_and_conservation(G, case):
 
 
 @pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "tri_delaunay_p3", "tri_delaunay_p5",
-                                  "hex_walls_p3", "hex_periodic_jitter_p3"])
+                                  "hex_walls_p3", "hex_periodic_jitter_p3", "hex_rotated_walls_p3",
+                                  "hex_rotated_periodic_jitter_p2"])
 def test_rhs_parity_mixed(G, case):
     w = CASES[case]()
     sol, F = _pair(G, w, precision="mixed")
@@ -237,7 +246,7 @@ def test_rhs_parity_mixed(G, case):
 
 
 @pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_stream_p5", "hex_periodic_jitter_p2",
-                                  "hex_periodic_jitter_p3"])
+                                  "hex_periodic_jitter_p3", "hex_rotated_periodic_jitter_p2"])
 def test_mixed_mass_conserved_to_round_off(G, case):
     """Mixed path: each element's float-float solution is corrected so that its
     mass change equals the FP64 sum of its (antisymmetric) face fluxes, so the

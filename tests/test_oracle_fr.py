@@ -30,6 +30,7 @@ WALL_MESHES = [
     ("tri", lambda: S.tri_split(3, periodic=(False, False), shuffle_seed=1), [2, 3]),
     ("tri", lambda: S.tri_delaunay(5, jitter=0.1, seed=7), [2]),
     ("hex", lambda: S.hex_grid(2, shuffle_seed=3), [2]),
+    ("hex", lambda: S.hex_grid(2, shuffle_seed=3, rotate_seed=7), [2, 3]),
 ]
 
 
@@ -106,6 +107,7 @@ def test_residual_exact_for_quadratic_advection_diffusion(et, mk, p):
     (lambda: S.quad_grid(4, jitter=0.15, seed=3, shuffle_seed=4, rotate_seed=5), 3),
     (lambda: S.tri_split(4, shuffle_seed=2), 3),
     (lambda: S.hex_grid(2, periodic=(True, True, True), jitter=0.1, seed=2), 2),
+    (lambda: S.hex_grid(2, periodic=(True, True, True), jitter=0.1, seed=2, rotate_seed=3), 2),
 ])
 def test_free_stream_preserved(mk, p):
     """Constant states under a uniform velocity have zero residual: with gamma = 0
@@ -132,6 +134,8 @@ def test_free_stream_preserved(mk, p):
      S.Velocity("rider_kothe", T=8.0)),
     (lambda: S.tri_split(5, shuffle_seed=2), 3, S.Velocity("rider_kothe", T=8.0)),
     (lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=2), 2,
+     S.Velocity("leveque", T=3.0)),
+    (lambda: S.hex_grid(3, periodic=(True, True, True), jitter=0.1, seed=2, rotate_seed=8), 2,
      S.Velocity("leveque", T=3.0)),
 ])
 def test_discrete_conservation(mk, p, vel):
