@@ -393,8 +393,9 @@ def sol_preconditions(n_steps, n_precond):
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", 1e-5)])
 def test_time_modulated_uniform_march_parity(G, mk, p, precision, tol):
     h = 0.25
+    dim = mk().dim
     w = _workload(mk, p, S.Velocity("uniform", a=(1.0, 0.5, 0.25), T=0.05),
-                  S.Circle((0.45, 0.55, 0.5), 0.3, 3 * p / (4 * h)), h)
+                  S.Circle((0.45, 0.55, 0.5)[:dim], 0.3, 3 * p / (4 * h)), h)
     w.dt = 0.01
     w.n_precond = 1000
     sol, F = _pair(G, w, precision=precision)
