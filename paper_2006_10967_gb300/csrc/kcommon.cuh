@@ -230,6 +230,58 @@ __device__ __forceinline__ void velocity(const VelDescT<R>& V, const R* x, R g, 
   }
 }
 
+// Separable velocity fields on elements whose map is affine with a diagonal
+// Jacobian (x_c depends on xi_c alone): every factor of the uniform,
+// Rider-Kothe, LeVeque and rotation fields is a function of one coordinate,
+// so an element needs them only at the N solution coordinates of each axis
+// and at the two ends.  Table layout per element: tab[(c (N + 2) + j) 2 + m],
+// j < N the solution coordinate j, N the end xi = -1, N + 1 the end xi = +1;
+// m = 0: sin^2(pi x_c) (rotation: x_c itself), m = 1: sin(2 pi x_c).
+__host__ __device__ constexpr bool vel_separable(int kind) { return kind == 0 || kind == 1 || kind == 2 || kind == 4; }
+
+template <typename R>
+__device__ __forceinline__ void vel_tab_entry(int kind, R x, R* e) {
+  if (kind == 4) {
+    e[0] = x;
+    e[1] = 0;
+    return;
+  }
+  R s, c;
+  scpi(x, &s, &c);
+  e[0] = s * s;
+  e[1] = (R)2 * s * c;
+}
+
+// Velocity at the point with per-axis table indices j[0..DIM-1].
+template <int DIM, int NT, typename R>
+__device__ __forceinline__ void velocity_tab(const VelDescT<R>& V, const R* tab, const int* j, R g, R* v) {
+  auto A = [&](int c) { return tab[(c * NT + j[c]) * 2]; };
+  auto B = [&](int c) { return tab[(c * NT + j[c]) * 2 + 1]; };
+  switch (V.kind) {
+    case 0:
+      for (int c = 0; c < DIM; ++c) v[c] = V.a[c] * g;
+      break;
+    case 1:  // u = -sin^2(pi x) sin(2 pi y) g, v = sin(2 pi x) sin^2(pi y) g
+      v[0] = -A(0) * B(1) * g;
+      v[1] = B(0) * A(1) * g;
+      if (DIM == 3) v[DIM - 1] = 0;
+      break;
+    case 2:
+      if (DIM == 3) {
+        v[0] = (R)2 * A(0) * B(1) * B(DIM - 1) * g;
+        v[1] = -B(0) * A(1) * B(DIM - 1) * g;
+        v[DIM - 1] = -B(0) * B(1) * A(DIM - 1) * g;
+      } else {
+        v[0] = v[1] = 0;
+      }
+      break;
+    default:  // rotation about (a[0], a[1]); the table holds the coordinates
+      v[0] = V.a[1] - A(1);
+      v[1] = A(0) - V.a[0];
+      if (DIM == 3) v[DIM - 1] = 0;
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ bool finite_(R x) { return isfinite(x); }
 

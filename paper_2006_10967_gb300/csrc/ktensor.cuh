@@ -179,7 +179,8 @@ struct LineMetric<2, T> {
 // reference centre, [9] its determinant, [10] the reciprocal, [11] whether
 // the map is affine (then [0..10] hold everywhere in the element), [12..13]
 // 1/W with W = sum_i w_i det J_i the element's quadrature area (FP64 value
-// split into two bulk-type parts).
+// split into two bulk-type parts), [14] whether the affine map has a diagonal
+// Jacobian (then separable velocity fields come from per-axis tables).
 template <int DIM, typename T>
 __global__ void k_metric_const(const KArgs A, int NG, int NU) {
   T* mc = reinterpret_cast<T*>(A.mcg);
@@ -198,7 +199,13 @@ __global__ void k_metric_const(const KArgs A, int NG, int NU) {
     const double rW = 1.0 / W;
     o[12] = (T)rW;
     o[13] = (T)(rW - (double)o[12]);
-    o[14] = o[15] = (T)0;
+    // [14]: affine with a diagonal Jacobian (x_c a function of xi_c alone)
+    bool diag = is_affine<DIM>(g);
+    for (int c = 0; c < DIM; ++c)
+      for (int b = 0; b < DIM; ++b)
+        if (b != c) diag = diag && g[c * (DIM == 2 ? 4 : 8) + 1 + b] == (T)0;
+    o[14] = diag ? (T)1 : (T)0;
+    o[15] = (T)0;
   }
 }
 
@@ -289,6 +296,7 @@ struct KBLayout {
                                   + 2 * NFLD * S::NF    // uo, cor
                                   + S::NG + kMetricRec  // geometry, metric record
                                   + (VT ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
+                                  + (MODE == 0 ? DIM * (N + 2) * 2 : 0)  // separable velocity tables
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
@@ -332,6 +340,8 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   T* vf = sc.take<T>(LY::VT ? ET * DIM * NF : 0);  // velocity cache tiles, flux points
   T* chi = sc.take<T>(MODE == 1 ? ET * 2 * NU : 0);   // MODE 1: [ET][2][NU]
   T* nus = sc.take<T>(MODE == 1 ? ET : 0);
+  constexpr int NT = N + 2;                           // velocity table entries per axis
+  T* vtab = sc.take<T>(MODE == 0 ? ET * DIM * NT * 2 : 0);  // [ET][DIM][NT][2]
   uint16_t* llist = sc.take<uint16_t>(ET * NF);       // [ET*NF] L flux points
   unsigned char* lm = sc.take<unsigned char>(ET * NF);  // [ET][NF]
 
@@ -410,6 +420,18 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   cp_async_wait_all();
   __syncthreads();
   const T gfac = gfac_s;
+  // separable velocity: per-axis tables of the elements with a diagonal map
+  // (read after the first axis pass's barrier)
+  const bool sepk = MODE == 0 && vel_separable(BC.vel.kind);
+  if (sepk)
+    for (int t = tid; t < ne * DIM * NT; t += blockDim.x) {
+      const int el = t / (DIM * NT), r = t % (DIM * NT), c = r / NT, j = r % NT;
+      if (mcs[el * kMetricRec + 14] == (T)0) continue;
+      const T* g = gs + el * NG + c * S::NC;
+      const T xi = j < N ? O.x[j] : (j == N ? (T)-1 : (T)1);
+      vel_tab_entry<T>(BC.vel.kind, g[0] + g[1 + c] * xi, vtab + (el * DIM * NT + r) * 2);
+    }
+  auto tab_of = [&](int el) -> bool { return sepk && mcs[el * kMetricRec + 14] != (T)0; };
 
   // ---- Steps 1-3, one pass per axis: traces at the line ends, partner
   //      traces (Step 2), reference derivative plus the two end corrections;
@@ -431,12 +453,6 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int fld = fsel + q * FS;
-        if (!(w0 & 1)) cor[(lel * NFLD + fld) * NF + k0] = 0;
-        if (!(w1 & 1)) cor[(lel * NFLD + fld) * NF + k1] = 0;
-      }
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int fld = fsel + q * FS;
         const T* ul = us + (lel * NFLD + fld) * NU + base;
         T v[N];
 #pragma unroll
@@ -452,6 +468,10 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
         const int fo = (lel * NFLD + fld) * NF;
         uo[fo + k0] = o0;
         uo[fo + k1] = o1;
+        // the own trace at L points (Step 5 reads it, then overwrites it with
+        // the common flux); no correction at R points in kb
+        cor[fo + k0] = (w0 & 1) ? f0 : (T)0;
+        cor[fo + k1] = (w1 & 1) ? f1 : (T)0;
         const T jm = o0 - f0, jp = o1 - f1;
         T* qa = qt + ((lel * NFLD + fld) * DIM + a) * NU + base;
 #pragma unroll
@@ -544,18 +564,32 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
-    T xi[3], Sm[3][3];
+    T xi[3];
     fpt_xi<DIM, N>(k, O.x, xi);
-    metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec);
     const T sg = s ? (T)1 : (T)-1;
+    // transformed face normal: row a of S = det J J^{-1} (from the record on
+    // affine elements)
+    const T* mcl = mcs + el * kMetricRec;
+    T srow[3];
+    if (mcl[11] != (T)0) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) srow[c] = mcl[a * 3 + c];
+    } else {
+      T Sm[3][3];
+      metric<DIM>(gs + el * NG, xi, Sm);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T sac = Sm[0][c];
+#pragma unroll
+        for (int b = 1; b < DIM; ++b)
+          if (b == a) sac = Sm[b][c];
+        srow[c] = sac;
+      }
+    }
     T pn[3], pm = 0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      T sac = Sm[0][c];
-#pragma unroll
-      for (int b = 1; b < DIM; ++b)
-        if (b == a) sac = Sm[b][c];
-      pn[c] = sg * sac;
+      pn[c] = sg * srow[c];
       pm += pn[c] * pn[c];
     }
     pm = sqrt_(pm);
@@ -579,7 +613,12 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
-      if (A.vsf) {
+      if (tab_of(el)) {
+        int jj[3];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) jj[b] = b == a ? N + s : ucoord<N>(b0, b);
+        velocity_tab<DIM, NT, T>(BC.vel, vtab + el * DIM * NT * 2, jj, gel, v);
+      } else if (A.vsf) {
         const T* vc = LY::VT ? vf + el * DIM * NF + k : vsf + (e0 + el) * DIM * NF + k;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NF];
@@ -598,13 +637,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       }
       const T M = fmax(sqrt_(v2), P.gamma);
       const T gm = fmax(sqrt_(g2), P.delta);
-      T pL = 0, sL = 0;  // own traces at this L point (Step 1, recomputed)
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const T lw = s ? O.lend[1][j] : O.lend[0][j];
-        pL += lw * us[(el * 2 + 0) * NU + b0 + j * st];
-        sL += lw * us[(el * 2 + 1) * NU + b0 + j * st];
-      }
+      const T pL = cor[(el * 2 + 0) * NF + k], sL = cor[(el * 2 + 1) * NF + k];  // own traces (Step 1)
       const T pR = uo[(el * 2 + 0) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
       const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
@@ -633,9 +666,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
         for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
         gn += nh[c] * acc;
       }
-      T L_ = 0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) L_ += (s ? O.lend[1][j] : O.lend[0][j]) * us[el * NU + b0 + j * st];
+      const T L_ = cor[el * NF + k];  // own trace (Step 1)
       const T F = pm * (-nus[el] * gn + P.tau_pseudo * (L_ - uo[el * NF + k]));
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       if (FaceScatter<DIM>::v && pg != og) fc[pslot + NF] = F;
@@ -655,7 +686,12 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
       const T epsel = A.ep ? epe[el] : P.eps;
-      if (A.vsu) {
+      if (tab_of(el)) {
+        int jj[3];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) jj[b] = ucoord<N>(i, b);
+        velocity_tab<DIM, NT, T>(BC.vel, vtab + el * DIM * NT * 2, jj, gel, v);
+      } else if (A.vsu) {
         const T* vc = LY::VT ? vu + el * DIM * NU + i : vsu + (e0 + el) * DIM * NU + i;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];
@@ -745,7 +781,12 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
             T v[3];
             const T gel = A.ep ? gfe[el] : gfac;
             const T epsel = A.ep ? epe[el] : P.eps;
-            if (A.vsu) {
+            if (tab_of(el)) {
+              int jj[3];
+#pragma unroll
+              for (int b = 0; b < DIM; ++b) jj[b] = ucoord<N>(i, b);
+              velocity_tab<DIM, NT, T>(BC.vel, vtab + el * DIM * NT * 2, jj, gel, v);
+            } else if (A.vsu) {
               const T* vc = LY::VT ? vu + el * DIM * NU + i : vsu + (e0 + el) * DIM * NU + i;
 #pragma unroll
               for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NU];

@@ -1,0 +1,93 @@
+"""Accuracy contract of the mixed-precision path (Section 4 error measures):
+both precisions marched to t = T on reduced versions of the benchmark flows,
+through the C ABI.
+
+* E_L1(mixed) <= 1.05 E_L1(FP64), E_L1 = int |phi_T - phi_e| with phi_e the
+  initial disk (the Rider-Kothe field reverses at T/2, so the exact solution
+  at t = T is the initial shape).
+* Mass: E_m = (int phi_T - int phi_0) / int phi_e.  On periodic meshes both
+  precisions conserve mass to round-off; on walled meshes the copy ghost state
+  lets the diffusive/sharpening flux through the walls, so E_m is that flux,
+  and the mixed path must add no more than 1e-10 to what FP64 shows; every
+  |E_m| is at most 1e-10 on these cases.
+* Interface normal: n = grad psi / |grad psi| from the corrected gradient of
+  Steps 2-3 (evaluated by the oracle on the GPU's psi), mean |n_mixed - n_FP64|
+  over the solution points with 0.05 < phi_FP64 < 0.95, reported and bounded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from libutil import ensure_built
+from oracle import Params, Solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_2006_10967_gb300 as G
+    return G
+
+
+def _march(G, w, precision):
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    F = G.Field(M, G.make_params(w, precision), ic=w.circle, precondition=True)
+    m0 = F.mass(0)
+    F.step(w.n_steps)
+    assert F.sync() == 0
+    return M, F, m0
+
+
+def _normals(sol, psi):
+    U = torch.as_tensor(psi, dtype=torch.float64)[:, None, :]
+    q, _ = sol.gradient(U, sol.trace(U))
+    q = q[:, 0]
+    return q / torch.clamp(torch.sqrt((q * q).sum(-1, keepdim=True)), min=1e-12)
+
+
+def _contract(G, w):
+    mesh = w.mesh()
+    res = {}
+    for prec in ("fp64", "mixed"):
+        M, F, m0 = _march(G, w, prec)
+        phi = F.get(0)
+        psi = F.get(1)
+        wq = M.quadrature()
+        phi_e = S.initial_phi(w, M.solution_points())
+        res[prec] = dict(E_L1=float((wq * np.abs(phi - phi_e)).sum()),
+                         E_m=float((F.mass(0) - m0) / (wq * phi_e).sum()), phi=phi, psi=psi)
+    sol = Solver(mesh, w.order, Params.from_workload(w), w.velocity)
+    n64 = _normals(sol, res["fp64"]["psi"])
+    n32 = _normals(sol, res["mixed"]["psi"])
+    band = (res["fp64"]["phi"] > 0.05) & (res["fp64"]["phi"] < 0.95)
+    dn = torch.sqrt(((n32 - n64) ** 2).sum(-1)).numpy()
+    res["normal_error"] = float(dn[band].mean())
+    res["ratio"] = res["mixed"]["E_L1"] / res["fp64"]["E_L1"]
+    return res
+
+
+CASES = {
+    "quad32_jitter_walls_p4": lambda: S.workload("c2q", n=32),
+    "quad32_periodic_p4": lambda: S.workload("c2q", n=32).with_(
+        mesh_fn=lambda: S.quad_grid(32, jitter=0.1, seed=1, shuffle_seed=11, rotate_seed=12)),
+    "tri_split32_walls_p3": lambda: S.workload("c2s", n=32, p=3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_mixed_precision_accuracy_contract(G, case):
+    w = CASES[case]()
+    r = _contract(G, w)
+    print(case, {k: (v if not isinstance(v, dict) else {a: b for a, b in v.items() if a.startswith("E")})
+                 for k, v in r.items()})
+    assert r["ratio"] <= 1.05, r["ratio"]
+    assert abs(r["mixed"]["E_m"]) <= 1e-10, r["mixed"]["E_m"]
+    assert abs(r["fp64"]["E_m"]) <= 1e-10, r["fp64"]["E_m"]
+    assert abs(r["mixed"]["E_m"] - r["fp64"]["E_m"]) <= 1e-10
+    assert r["normal_error"] < 1e-3, r["normal_error"]
