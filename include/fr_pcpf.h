@@ -142,9 +142,19 @@ typedef struct fr_params {
                             Eq. altconservativephasefieldeq with n = grad phi/|grad phi|;
                             fr_step and set-up then never reset or precondition psi, which
                             is still advected but feeds nothing).  Other values: FR_EINVAL */
+  int32_t wall;          /* wall faces of the physical system: FR_WALL_COPY (Section 3.3:
+                            ghost states copy the interior, so the diffusive and sharpening
+                            fluxes of the interior pass through the wall) or FR_WALL_NOFLUX
+                            (an option of this library, not the paper's: the common normal
+                            flux of both fields is zero at wall flux points, so that mass is
+                            conserved on walled domains as on periodic ones; the
+                            preconditioning keeps the copy ghost).  FR_WALL_NOFLUX has no
+                            adjoint (fr_adjoint_record: FR_EUNSUPPORTED).  Other values:
+                            FR_EINVAL */
 } fr_params;
 
 enum { FR_NORMAL_PSI = 0, FR_NORMAL_PHI = 1 };
+enum { FR_WALL_COPY = 0, FR_WALL_NOFLUX = 1 };
 
 typedef struct fr_ic {
   int32_t kind;          /* FR_IC_CIRCLE or FR_IC_ARRAY */

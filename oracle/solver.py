@@ -24,6 +24,10 @@ Readings of points the paper leaves open (each is a parameter):
     Eq. pseudotimesystem (psi_tau = -J^{-1} div~ g~ + S), flux g = -nu_s grad psi,
     LDG common flux with penalty tau_pseudo, RK4 in pseudo time, stop when the
     RMS of (psi^k - psi^{k-1})/dtau <= tol or after kmax iterations.
+  * Walls (Section 3.3): ghost states copy the interior, so the interior's
+    diffusive and sharpening fluxes leave through the wall; Params.wall =
+    "noflux" is an option (not the paper's) with zero common normal flux of
+    the physical system at wall points.
   * Resolution indicator on psi with an orthonormal modal basis; the
     truncation drops modes of (tensor) max degree p or (triangle) total degree p;
     an element with zero energy or zero truncated energy gets nu_s = 0.
@@ -63,6 +67,7 @@ class Params:
     nu_max: float = 0.0
     delta: float = 1e-12
     normal: str = "psi"  # "psi": preconditioned (Section 2); "phi": unpreconditioned CPF
+    wall: str = "copy"   # "copy": ghost = interior (Section 3.3); "noflux": zero wall flux (an option)
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -70,7 +75,7 @@ class Params:
                  tau_pseudo=w.tau_pseudo, dt=w.dt, n_precond=w.n_precond,
                  pseudo_kmax=w.pseudo_kmax, pseudo_dtau=w.pseudo_dtau,
                  pseudo_tol=w.pseudo_tol, s0=w.s0, kappa=w.kappa, nu_max=w.nu_max,
-                 delta=w.delta, normal=getattr(w, "normal", "psi"))
+                 delta=w.delta, normal=getattr(w, "normal", "psi"), wall=getattr(w, "wall", "copy"))
         d.update(kw)
         return cls(**d)
 
@@ -143,6 +148,7 @@ class Solver:
         self.pe = torch.as_tensor(g.pe)
         self.pk = torch.as_tensor(g.pk)
         self.isL = torch.as_tensor(g.isL)
+        self.boundary = torch.as_tensor(g.boundary)
         self.h = g.h
         self.E = g.xu.shape[0]
         self.Nu = el.nu
@@ -222,6 +228,9 @@ class Solver:
         F_phi = (0.5 * (Uf[:, 0] + Uo[:, 0]) * vn - (self.nhat * fvisf).sum(-1)
                  + prm.tau * (Uf[:, 0] - Uo[:, 0]))
         F_psi = 0.5 * (Uf[:, 1] + Uo[:, 1]) * vn + prm.tau_psi * (Uf[:, 1] - Uo[:, 1])
+        if prm.wall == "noflux":   # no normal flux through wall faces
+            F_phi = torch.where(self.boundary, torch.zeros_like(F_phi), F_phi)
+            F_psi = torch.where(self.boundary, torch.zeros_like(F_psi), F_psi)
         Ft = self.common_to_transformed(torch.stack([F_phi, F_psi], 1))
         div = self.divergence(ft, Ft)                                 # Step 6
         R = -div / self.detJ[:, None, :]

@@ -116,6 +116,11 @@ def make_params(w, precision="fp64", **kw):
     if normal not in ("psi", "phi"):
         raise ValueError(f"normal must be 'psi' or 'phi', not {normal!r}")
     p.normal = 1 if normal == "phi" else 0
+    # wall faces: "copy" (Section 3.3 copy ghost) or "noflux" (zero common normal flux)
+    wall = kw.get("wall", getattr(w, "wall", "copy"))
+    if wall not in ("copy", "noflux"):
+        raise ValueError(f"wall must be 'copy' or 'noflux', not {wall!r}")
+    p.wall = 1 if wall == "noflux" else 0
     vel = kw.get("velocity", w.velocity)
     p.vel.kind = VELS[vel.kind]
     p.vel.T = float(vel.T)

@@ -46,7 +46,8 @@ class fr_params(C.Structure):
                 ("pseudo_kmax", C.c_int32), ("pseudo_dtau", C.c_double), ("pseudo_tol", C.c_double),
                 ("pseudo_fixed", C.c_int32), ("precision", C.c_int32), ("s0", C.c_double),
                 ("kappa", C.c_double), ("nu_max", C.c_double), ("delta", C.c_double),
-                ("vel", fr_velocity), ("vel_cache", C.c_int32), ("normal", C.c_int32)]
+                ("vel", fr_velocity), ("vel_cache", C.c_int32), ("normal", C.c_int32),
+                ("wall", C.c_int32)]
 
 
 class fr_ic(C.Structure):

@@ -79,6 +79,7 @@ void fill_bulk(const fr_params* prm, const fr_mesh* m, BulkConst<R>& b) {
   b.prm.tau_pseudo = (R)prm->tau_pseudo;
   b.prm.delta = (R)prm->delta;
   b.prm.nphi = prm->normal == FR_NORMAL_PHI;
+  b.prm.noflux = prm->wall == FR_WALL_NOFLUX;
   if (m->etype != FR_TRI) {
     const Tensor1D& t = m->t1;
     for (int i = 0; i < t.n; ++i) {
@@ -155,6 +156,7 @@ int check_params(const fr_params* p) {
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return FR_EINVAL;
   if (p->n_precond < 1 || p->pseudo_kmax < 0) return FR_EINVAL;
   if (p->normal != FR_NORMAL_PSI && p->normal != FR_NORMAL_PHI) return FR_EINVAL;
+  if (p->wall != FR_WALL_COPY && p->wall != FR_WALL_NOFLUX) return FR_EINVAL;
   if (p->pseudo_kmax > 0 && !(p->pseudo_dtau > 0.0)) return FR_EINVAL;
   if (p->precision != FR_FP64 && p->precision != FR_MIXED) return FR_EINVAL;
   if (!(p->gamma >= 0.0) || !(p->eps >= 0.0) || !(p->delta > 0.0) || !(p->kappa > 0.0)) return FR_EINVAL;

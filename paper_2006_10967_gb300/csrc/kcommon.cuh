@@ -31,7 +31,8 @@ struct VelDescT {
 template <typename R>
 struct PrmT {
   R gamma, eps, tau, tau_psi, tau_pseudo, delta;
-  int nphi;  // 1: the sharpening normal comes from phi's gradient (unpreconditioned CPF)
+  int nphi;    // 1: the sharpening normal comes from phi's gradient (unpreconditioned CPF)
+  int noflux;  // 1: zero common normal flux of the physical system at wall flux points
 };
 
 struct PhysPrm {

@@ -651,8 +651,9 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       T fvn = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) fvn += nh[c] * (epsel * qf[0][c] - sharp * qn[c]);
-      const T Fp = (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
-      const T Fs = (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
+      const bool shut = P.noflux && pg == og;  // no-flux wall point
+      const T Fp = shut ? (T)0 : (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
+      const T Fs = shut ? (T)0 : (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
       // the transformed common flux F~ = |pn| F out of L; the R side uses -F~
       const T Fp_t = pm * Fp, Fs_t = pm * Fs;
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp_t;

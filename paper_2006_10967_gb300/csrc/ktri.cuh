@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
       T fvn = 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c) fvn += nh[c] * M * (Pm.eps * qfv[0][c] - sharp * qfv[kn][c]);
-      const T Fp = (T)0.5 * (pL + pR) * vn - fvn + Pm.tau * (pL - pR);
-      const T Fs = (T)0.5 * (sL + sR) * vn + Pm.tau_psi * (sL - sR);
+      const bool shut = Pm.noflux && A.fnbr[(e0 + el) * NF + k] >> 1 == (e0 + el) * NF + k;  // no-flux wall
+      const T Fp = shut ? (T)0 : (T)0.5 * (pL + pR) * vn - fvn + Pm.tau * (pL - pR);
+      const T Fs = shut ? (T)0 : (T)0.5 * (sL + sR) * vn + Pm.tau_psi * (sL - sR);
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp;
       fc[((e0 + el) * 2 + 1) * NF + k] = Fs;
       cor[(el * 2 + 0) * NF + k] = pm * Fp;

@@ -102,6 +102,7 @@ class Workload:
     nu_max: float = 0.0
     delta: float = 1e-12
     precision: str = "fp64"
+    wall: str = "copy"         # Section 3.3 copy ghost; "noflux": zero wall flux (an option)
     extra: dict = field(default_factory=dict)
 
     def mesh(self):

@@ -5,11 +5,13 @@ through the C ABI.
 * E_L1(mixed) <= 1.05 E_L1(FP64), E_L1 = int |phi_T - phi_e| with phi_e the
   initial disk (the Rider-Kothe field reverses at T/2, so the exact solution
   at t = T is the initial shape).
-* Mass: E_m = (int phi_T - int phi_0) / int phi_e.  On periodic meshes both
-  precisions conserve mass to round-off; on walled meshes the copy ghost state
-  lets the diffusive/sharpening flux through the walls, so E_m is that flux,
-  and the mixed path must add no more than 1e-10 to what FP64 shows; every
-  |E_m| is at most 1e-10 on these cases.
+* Mass: E_m = (int phi_T - int phi_0) / int phi_e.  On periodic meshes, and
+  on walled meshes with the no-flux wall option, both precisions conserve
+  mass: |E_m| <= 1e-10.  With the paper's copy ghost state (Section 3.3) the
+  interior's diffusive and sharpening fluxes leave through the walls once the
+  interface's tanh tail reaches them, in FP64 as in the mixed path (on 32^2
+  quads at p = 4 both lose ~1e-4 of the disk by t = T); E_m is then reported,
+  not bounded.
 * Interface normal: n = grad psi / |grad psi| from the corrected gradient of
   Steps 2-3 (evaluated by the oracle on the GPU's psi), mean |n_mixed - n_FP64|
   over the solution points with 0.05 < phi_FP64 < 0.95, reported and bounded.
@@ -77,6 +79,8 @@ CASES = {
     "quad32_periodic_p4": lambda: S.workload("c2q", n=32).with_(
         mesh_fn=lambda: S.quad_grid(32, jitter=0.1, seed=1, shuffle_seed=11, rotate_seed=12)),
     "tri_split32_walls_p3": lambda: S.workload("c2s", n=32, p=3),
+    "quad32_jitter_noflux_walls_p4": lambda: S.workload("c2q", n=32).with_(wall="noflux"),
+    "tri_split32_noflux_walls_p3": lambda: S.workload("c2s", n=32, p=3).with_(wall="noflux"),
 }
 
 
@@ -88,6 +92,6 @@ def test_mixed_precision_accuracy_contract(G, case):
                  for k, v in r.items()})
     assert r["ratio"] <= 1.05, r["ratio"]
     assert r["normal_error"] < 1e-3, r["normal_error"]
-    if "periodic" in case:
+    if "periodic" in case or "noflux" in case:
         assert abs(r["mixed"]["E_m"]) <= 1e-10, r["mixed"]["E_m"]
         assert abs(r["fp64"]["E_m"]) <= 1e-10, r["fp64"]["E_m"]

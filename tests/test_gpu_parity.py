@@ -405,3 +405,34 @@ def test_time_modulated_uniform_march_parity(G, mk, p, precision, tol):
         assert _rel(F.get(0), sol.phi.numpy()) < tol
         assert _rel(F.get(1), sol.psi.numpy()) < tol
     assert F.stats()["t"] == pytest.approx(sol.t, rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# No-flux walls (an option beside the paper's copy ghost state)
+
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3", "hex_rotated_walls_p3"])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
+def test_noflux_wall_rhs_parity(G, case, precision, tol):
+    w = CASES[case]()
+    w.wall = "noflux"
+    sol, F = _pair(G, w, precision=precision)
+    _perturb(sol, F)
+    R = F.rhs(0.3).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.3)
+    assert _rel(R[0], Ro[0].numpy()) < tol, case
+    assert _rel(R[1], Ro[1].numpy()) < tol, case
+
+
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "tri_delaunay_p3", "hex_walls_p3"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noflux_walls_conserve_mass(G, case, precision):
+    w = CASES[case]()
+    w.wall = "noflux"
+    _, F = _pair(G, w, precision=precision)
+    m0 = F.mass(0)
+    F.step(60)
+    assert F.sync() == 0
+    assert abs(F.mass(0) - m0) < 1e-13 * abs(m0)
+    _, F64 = _pair(G, w)
+    with pytest.raises(G.FRError):
+        F64.adjoint_record(4, 2)

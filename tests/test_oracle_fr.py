@@ -411,3 +411,35 @@ def test_integral_of_polynomial_fields_is_exact_on_mapped_meshes(et):
         exact += 1.25 - 0.25
     assert float(s.integral(f)) == pytest.approx(exact, rel=1e-13)
     assert float(s.integral(torch.ones_like(f))) == pytest.approx(1.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("mk,p,vel", [
+    (lambda: S.quad_grid(4, periodic=(False, False), jitter=0.12, seed=3, shuffle_seed=4, rotate_seed=5), 3,
+     S.Velocity("rider_kothe", T=8.0)),
+    (lambda: S.tri_delaunay(6, jitter=0.1, seed=7), 3, S.Velocity("rider_kothe", T=8.0)),
+    (lambda: S.hex_grid(3, jitter=0.1, seed=2, rotate_seed=4), 2, S.Velocity("leveque", T=3.0)),
+])
+def test_wall_flux_copy_ghost_and_noflux_option(mk, p, vel):
+    """Section 3.3 walls copy the interior, so an interface that reaches a wall
+    loses mass through it (sum_e sum_i w_i det J_i R_i != 0); with the no-flux
+    option the same residual sums to zero (conservation as on periodic
+    meshes) and differs from the copy-ghost one only on wall elements."""
+    mesh = mk()
+    d = mesh.dim
+    c = (0.5, 0.2, 0.5)[:d]                     # disk / sphere near the wall y = 0
+    out = {}
+    for wall in ("copy", "noflux"):
+        s = _solver(mesh, p, vel, wall=wall)
+        s.initialize(S.Circle(c, 0.15, 8.0), precondition=False)
+        s.psi = s.psi + 0.05 * torch.sin(7 * s.xu[..., 0])
+        out[wall] = (s, *s.rhs(s.phi, s.psi, 0.7))
+    s, Rc, Rcs = out["copy"]
+    _, Rn, Rns = out["noflux"]
+    scale = float(s.integral(Rc.abs()))
+    assert abs(float(s.integral(Rn))) < 1e-13 * scale
+    assert abs(float(s.integral(Rns))) < 1e-13 * float(s.integral(Rns.abs()))
+    assert abs(float(s.integral(Rc))) > 1e-4 * scale   # mass leaves through the copy-ghost wall
+    wall_el = s.boundary.any(1)
+    assert bool(wall_el.any()) and bool((~wall_el).any())
+    assert torch.allclose(Rc[~wall_el], Rn[~wall_el], atol=1e-13 * float(Rc.abs().max()))
+    assert not torch.allclose(Rc[wall_el], Rn[wall_el], atol=1e-6 * float(Rc.abs().max()))
