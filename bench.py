@@ -72,6 +72,8 @@ def parse():
                          "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads); "
                          "c2s: Rider-Kothe on split-triangle meshes (--mesh-n, --order <= 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--rk-steps", type=int, default=STEPS_PER_BENCH_STEP,
+                    help="RK4 steps per benchmark step (profiling captures use fewer launches)")
     return ap.parse_args()
 
 
@@ -500,6 +502,7 @@ def main():
         wname += "_unpreconditioned"
     mesh = w.mesh()
     workload_cfg = workload_config(w, wname, mesh, args.normal, world)
+    workload_cfg["rk_steps_per_step"] = args.rk_steps
     # the oracle's bounded sample: the workload itself, or for the 64^3 hex
     # workload a 32^3 sub-grid of the same problem (same order, field and
     # parameters; the rate is per DOF-stage)
@@ -545,7 +548,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     vc = not args.no_vel_cache
     main_out, F = run_path(G, S, w, mesh, args.precision, args.steps, max(args.warmup, 3), world, rank, flush,
-                           want_kernel=True, e2e=True, vel_cache=vc)
+                           want_kernel=True, e2e=True, vel_cache=vc, rk_steps=args.rk_steps)
     del F
     fp64_out = None
     if args.precision == "mixed" and args.fp64_steps > 0:
