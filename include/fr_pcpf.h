@@ -260,10 +260,14 @@ int fr_mass_integral(fr_field* field, int which, double* out_host, void* stream)
  * callers that hold their data on the device without an fr_field workspace.
  *
  * Computes sum_i w[i] * u[i] over n doubles (dev_u, dev_w: device arrays,
- * caller-owned) with the compensated, fixed-order reduction of
- * fr_mass_integral and writes it to *out_host (synchronous on `stream`).
+ * caller-owned) with the same Neumaier-compensated FP64 method as
+ * fr_mass_integral, in its own fixed order (contiguous blocks of 2048 values,
+ * then the block partials in index order), so the result is deterministic
+ * for a given n and agrees with fr_mass_integral to about 1e-13 relative
+ * (the two summation orders differ).  The result is written to *out_host:
+ * the call waits for the stream (cudaStreamSynchronize) before returning.
  * Pass u = one field from fr_field_get_device and w = fr_mesh_quadrature
- * copied to the device to get fr_mass_integral's value.
+ * copied to the device to compare with fr_mass_integral.
  *
  * Scratch: a static device array of FR_NOALLOC_MAX_BLOCKS (sum, compensation)
  * pairs plus two words (~256 KB), held by every GPU that loads the library

@@ -1,6 +1,8 @@
-// Allocation-free weighted integral: sum_i w_i u_i with the same compensated,
-// fixed-order reduction as fr_mass_integral, for callers that cannot call
-// cudaMalloc (see include/fr_pcpf.h, fr_mass_integral_noalloc).
+// Allocation-free weighted integral: sum_i w_i u_i with the same Neumaier
+// compensation as fr_mass_integral but its own fixed summation order
+// (contiguous 2048-value blocks, then the block partials in order), for
+// callers that cannot call cudaMalloc (see include/fr_pcpf.h,
+// fr_mass_integral_noalloc).
 //
 // Its scratch (per-block partial sums, the last-block counter and the result)
 // is one file-scope __device__ array.  Host code cannot use the array's name
