@@ -151,6 +151,13 @@ typedef struct fr_params {
                             preconditioning keeps the copy ghost).  FR_WALL_NOFLUX has no
                             adjoint (fr_adjoint_record: FR_EUNSUPPORTED).  Other values:
                             FR_EINVAL */
+  int32_t variant;       /* implementation of the residual and update kernels, all giving the
+                            same result to round-off: 0 the default; fr_kernel_variants gives
+                            the count for a mesh and precision (triangles, FR_MIXED: 0 scalar
+                            dot products, 1 the operator applies on tensor cores, mma.sync
+                            m16n8k8 in three-term TF32 with FP32 accumulation).  An autotuner
+                            picks among them by measurement.  Out of range: FR_EUNSUPPORTED
+                            from fr_field_init, negative: FR_EINVAL */
 } fr_params;
 
 enum { FR_NORMAL_PSI = 0, FR_NORMAL_PHI = 1 };
@@ -291,6 +298,10 @@ int fr_field_set(fr_field* field, int which, const double* host, void* stream);
 /* Device-pointer variants (asynchronous on `stream`), n_dof doubles. */
 int fr_field_get_device(fr_field* field, int which, double* dev, void* stream);
 int fr_field_set_device(fr_field* field, int which, const double* dev, void* stream);
+
+/* Number of kernel variants (fr_params.variant) built for the mesh's element
+ * type and order in `precision` (FR_FP64 or FR_MIXED): *count >= 1. */
+int fr_kernel_variants(const fr_mesh* mesh, int precision, int32_t* count);
 
 /* Evaluate the semi-discrete right-hand side du/dt = -J^{-1} div~ f~ (Step 6)
  * of the physical system at the current state and time t into dev_out

@@ -121,6 +121,11 @@ def make_params(w, precision="fp64", **kw):
     if wall not in ("copy", "noflux"):
         raise ValueError(f"wall must be 'copy' or 'noflux', not {wall!r}")
     p.wall = 1 if wall == "noflux" else 0
+    # kernel variant: an explicit index, or "auto": the autotuner's table entry
+    # for the field's mesh (resolved by Field), else 0
+    variant = kw.get("variant", "auto")
+    p._variant = variant
+    p.variant = 0 if variant == "auto" else int(variant)
     vel = kw.get("velocity", w.velocity)
     p.vel.kind = VELS[vel.kind]
     p.vel.T = float(vel.T)
@@ -136,6 +141,20 @@ def make_params(w, precision="fp64", **kw):
     return p
 
 
+def kernel_variants(mesh, precision):
+    """Number of kernel variants built for the mesh's element type and order."""
+    n = C.c_int32()
+    check(lib().fr_kernel_variants(mesh.handle, FR_MIXED if precision in ("mixed", FR_MIXED) else FR_FP64,
+                                   C.byref(n)), "fr_kernel_variants")
+    return n.value
+
+
+def _resolve_variant(mesh, params):
+    if getattr(params, "_variant", None) == "auto":
+        from . import tune
+        params.variant = tune.lookup(mesh.info.etype, mesh.info.order, params.precision)
+
+
 class Field:
     """Device state of one FR-PCPF problem (fr_field_init); PyTorch owns the workspace."""
 
@@ -143,6 +162,7 @@ class Field:
         import torch
         self.mesh = mesh
         self.params = params
+        _resolve_variant(mesh, params)
         self.torch = torch
         nbytes = C.c_size_t()
         check(lib().fr_field_workspace_bytes(mesh.handle, C.byref(params), C.byref(nbytes)),
@@ -179,6 +199,7 @@ class Field:
         obj = cls.__new__(cls)
         obj.mesh = mesh
         obj.params = params
+        _resolve_variant(mesh, params)
         obj.torch = torch
         nbytes = C.c_size_t()
         check(lib().fr_field_workspace_bytes(mesh.handle, C.byref(params), C.byref(nbytes)),

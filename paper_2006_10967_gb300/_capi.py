@@ -47,7 +47,7 @@ class fr_params(C.Structure):
                 ("pseudo_fixed", C.c_int32), ("precision", C.c_int32), ("s0", C.c_double),
                 ("kappa", C.c_double), ("nu_max", C.c_double), ("delta", C.c_double),
                 ("vel", fr_velocity), ("vel_cache", C.c_int32), ("normal", C.c_int32),
-                ("wall", C.c_int32)]
+                ("wall", C.c_int32), ("variant", C.c_int32)]
 
 
 class fr_ic(C.Structure):
@@ -93,6 +93,7 @@ _SIGS = {
     "fr_adjoint_workspace_bytes": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
     "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "fr_kernel_variants": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int32)]),
     "fr_profile": (C.c_int, [_vp, C.c_int]),
     "fr_profile_read": (C.c_int, [_vp, _vp, _dp, C.POINTER(C.c_int64)]),
     "fr_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _dp]),

@@ -20,6 +20,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf, ep, mcg;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
+  size_t wphys;                   // triangles: physical edge quadrature weight per flux point (float-float)
   size_t total;
 };
 
@@ -140,15 +141,20 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
     L.tri_d = take(nops * sizeof(double));
     L.tri_f = take(nops * sizeof(float));
     L.tri_high = take(NU);
+    L.wphys = take(E * NF * 2 * sizeof(float));
   }
   L.total = off;
   return L;
 }
 
-bool get_kernels(const fr_mesh& m, int precision, KernelSet* ks) {
-  if (m.etype == FR_QUAD) return kernels_quad(m.order, precision, m.E, ks);
-  if (m.etype == FR_HEX) return kernels_hex(m.order, precision, m.E, ks);
-  return kernels_tri(m.order, precision, m.E, ks);
+bool get_kernels(const fr_mesh& m, int precision, int variant, KernelSet* ks) {
+  if (m.etype == FR_QUAD) return variant == 0 && kernels_quad(m.order, precision, m.E, ks);
+  if (m.etype == FR_HEX) return variant == 0 && kernels_hex(m.order, precision, m.E, ks);
+  return kernels_tri(m.order, precision, m.E, variant, ks);
+}
+
+int variant_count(const fr_mesh& m, int precision) {
+  return m.etype == FR_TRI && precision == FR_MIXED ? 2 : 1;
 }
 
 int check_params(const fr_params* p) {
@@ -157,6 +163,7 @@ int check_params(const fr_params* p) {
   if (p->n_precond < 1 || p->pseudo_kmax < 0) return FR_EINVAL;
   if (p->normal != FR_NORMAL_PSI && p->normal != FR_NORMAL_PHI) return FR_EINVAL;
   if (p->wall != FR_WALL_COPY && p->wall != FR_WALL_NOFLUX) return FR_EINVAL;
+  if (p->variant < 0) return FR_EINVAL;
   if (p->pseudo_kmax > 0 && !(p->pseudo_dtau > 0.0)) return FR_EINVAL;
   if (p->precision != FR_FP64 && p->precision != FR_MIXED) return FR_EINVAL;
   if (!(p->gamma >= 0.0) || !(p->eps >= 0.0) || !(p->delta > 0.0) || !(p->kappa > 0.0)) return FR_EINVAL;
@@ -476,7 +483,7 @@ extern "C" int fr_field_workspace_bytes(const fr_mesh* m, const fr_params* prm, 
   int rc = check_params(prm);
   if (rc) return rc;
   KernelSet ks;
-  if (!get_kernels(*m, prm->precision, &ks)) return FR_EUNSUPPORTED;
+  if (!get_kernels(*m, prm->precision, prm->variant, &ks)) return FR_EUNSUPPORTED;
   int mg;
   launch_elementwise_grid(m->E * m->nu, &mg);
   const int mb = ks.max_blocks > mg ? ks.max_blocks : mg;
@@ -492,7 +499,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   if (rc) return rc;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return FR_EINVAL;
   KernelSet ks;
-  if (!get_kernels(*m, prm->precision, &ks)) return FR_EUNSUPPORTED;
+  if (!get_kernels(*m, prm->precision, prm->variant, &ks)) return FR_EUNSUPPORTED;
   if (!ks.prepared) return FR_ECUDA;
   int mg;
   launch_elementwise_grid(m->E * m->nu, &mg);
@@ -556,7 +563,8 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.vsu = L.vsu ? b + L.vsu : nullptr;
   A.vsf = L.vsf ? b + L.vsf : nullptr;
   // element flux balances of the mixed path's conservation correction (tensor elements)
-  A.tacc = (prm->precision == FR_MIXED && m->etype != FR_TRI) ? reinterpret_cast<double*>(b + L.tacc) : nullptr;
+  A.tacc = prm->precision == FR_MIXED ? reinterpret_cast<double*>(b + L.tacc) : nullptr;
+  A.wphys = m->etype == FR_TRI ? reinterpret_cast<const float2*>(b + L.wphys) : nullptr;
   A.wdetf = reinterpret_cast<const float2*>(b + L.wdetf);
   A.ep = nullptr;
   A.mcg = L.mcg ? b + L.mcg : nullptr;
@@ -611,6 +619,38 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
     const uint8_t* hi = reinterpret_cast<const uint8_t*>(b + L.tri_high);
     A.trid = tri_pointers<double>(m->tri, reinterpret_cast<const double*>(b + L.tri_d), hi);
     A.trif = tri_pointers<float>(m->tri, reinterpret_cast<const float*>(b + L.tri_f), hi);
+    // physical quadrature weight of every flux point, w_j |edge| / 2, computed
+    // once per edge from the L side's geometry and given bitwise to both
+    // sides, so that the element flux balances telescope exactly
+    const int n = m->n, NF = m->nf;
+    std::vector<double> w1(n), x1(n);
+    {
+      frp::Tensor1D t;
+      frp::build_tensor1d(m->order, t);
+      for (int j = 0; j < n; ++j) w1[j] = t.w[j];
+    }
+    const double V[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
+    std::vector<double> wp(m->E * NF, 0.0);
+    for (int64_t e = 0; e < m->E; ++e)
+      for (int k = 0; k < NF; ++k) {
+        const int32_t w = m->fnbr[e * NF + k];
+        if (!(w & 1)) continue;  // R points take the L side's value
+        const int ed = k / n, ed1 = (ed + 1) % 3;
+        const double* g = &m->geo[e * 2 * 3];
+        double dx[2];
+        for (int c = 0; c < 2; ++c)
+          dx[c] = g[c * 3 + 1] * (V[ed1][0] - V[ed][0]) + g[c * 3 + 2] * (V[ed1][1] - V[ed][1]);
+        const double val = w1[k % n] * 0.5 * std::sqrt(dx[0] * dx[0] + dx[1] * dx[1]);
+        wp[e * NF + k] = val;
+        wp[(int64_t)(w >> 1)] = val;
+      }
+    std::vector<float> wpf(wp.size() * 2);
+    for (size_t g = 0; g < wp.size(); ++g) {
+      const float hi = (float)wp[g];
+      wpf[2 * g] = hi;
+      wpf[2 * g + 1] = (float)(wp[g] - (double)hi);
+    }
+    up(L.wphys, wpf.data(), wpf.size() * sizeof(float));
   }
   // u = [phi, phi - 1/2] element-major (float-float pairs in the mixed path)
   std::vector<double> u0(m->E * 2 * m->nu);
@@ -878,6 +918,12 @@ extern "C" int fr_rhs_pseudo(fr_field* f, double* dev_out, void* stream) {
   a.out = dev_out;
   f->ks.ka[1](a, s);
   CK(cudaGetLastError());
+  return FR_OK;
+}
+
+extern "C" int fr_kernel_variants(const fr_mesh* m, int precision, int32_t* count) {
+  if (!m || !count || (precision != FR_FP64 && precision != FR_MIXED)) return FR_EINVAL;
+  *count = variant_count(*m, precision);
   return FR_OK;
 }
 

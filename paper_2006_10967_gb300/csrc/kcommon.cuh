@@ -124,7 +124,8 @@ struct KArgs {
   double* tacc;          // E x 2: RK accumulation of the element flux balances (mixed path) or nullptr
   ElemPar* ep;           // E per-element parameters (batched instances) or nullptr (uniform)
   const float2* wdetf;   // E x nu: w_i det J_i as float-float pairs (mixed path)
-  void* mcg;             // tensor elements: E x 12 metric records (bulk type)
+  void* mcg;             // tensor elements: E x 16 metric records (bulk type)
+  const float2* wphys;   // triangles: E x nf physical flux-point weights (float-float), equal on both sides
   int stage;             // 1..4 RK stage, -1: write the rate into out
   int use_dev_time;      // KB: t = dstate[DS_TIME] + c_s dt
   double t;              // KB: stage time when !use_dev_time

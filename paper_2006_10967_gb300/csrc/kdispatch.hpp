@@ -20,7 +20,7 @@ struct KernelSet {
 // Return false if the (order, precision) pair is not built.
 bool kernels_quad(int order, int precision, int64_t E, KernelSet* ks);
 bool kernels_hex(int order, int precision, int64_t E, KernelSet* ks);
-bool kernels_tri(int order, int precision, int64_t E, KernelSet* ks);
+bool kernels_tri(int order, int precision, int64_t E, int variant, KernelSet* ks);
 
 template <typename K>
 inline void launch_kernel(K kern, size_t smem, int et, const KArgs& A, cudaStream_t s, int threads = kThreads) {

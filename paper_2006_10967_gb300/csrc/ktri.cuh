@@ -75,11 +75,13 @@ __device__ __forceinline__ void tri_metric(const T* g, TriMet<T>& m) {
   m.S[1][1] = Sm[1][1];
 }
 
-template <int P, typename T, int MODE>
+// TC: the float path's operator applies on tensor cores (mma_tf32.cuh);
+// otherwise scalar dot products (the only form of the FP64 path).
+template <int P, typename T, int MODE, bool TC = false>
 struct KBTriLayout {
   using S = TriS<P>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr bool MMA = std::is_same<T, float>::value;
+  static constexpr bool MMA = TC && std::is_same<T, float>::value;
   // + the float path's [ET][NFLD][2][NF] buffer of L applied to q, then to f~
   static constexpr int PER_EL_T = NFLD * S::NU + 3 * NFLD * S::NF + NFLD * 2 * S::NU + S::NG + 5 + 1 +
                                   (MMA ? NFLD * 2 * S::NF : 0);
@@ -89,10 +91,10 @@ struct KBTriLayout {
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
 };
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool TC = false>
 __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   using S = TriS<P>;
-  using LY = KBTriLayout<P, T, MODE>;
+  using LY = KBTriLayout<P, T, MODE, TC>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET, N = S::N;
   constexpr int F0 = MODE == 0 ? 0 : 1;
   constexpr bool kMMA = LY::MMA;
@@ -424,22 +426,26 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
   (void)N;
 }
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool TC = false>
 struct KATriLayout {
   using S = TriS<P>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
-  static constexpr bool MMA = std::is_same<T, float>::value;
-  // + the float path's [ET][NFLD][NU] lift buffer
-  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1 + (MMA ? NFLD * S::NU : 0)) * (int)sizeof(T);
+  static constexpr bool FLT = std::is_same<T, float>::value;
+  static constexpr bool MMA = TC && FLT;
+  static constexpr bool CONS = FLT && MODE == 0;  // mixed-path flux balance
+  // + the float path's [ET][NFLD][NU] lift / increment buffer and, for the
+  // flux balance, the float-float states [ET][2][NU]
+  static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1 + (FLT ? NFLD * S::NU : 0)) * (int)sizeof(T) +
+                                  (CONS ? 2 * S::NU * 8 : 0);
   static constexpr int ETr = 16384 / BYTES_EL;
   static constexpr int ET = ETr < 1 ? 1 : (ETr > 128 ? 128 : ETr);
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
 };
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool TC = false>
 __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   using S = TriS<P>;
-  using LY = KATriLayout<P, T, MODE>;
+  using LY = KATriLayout<P, T, MODE, TC>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFLD = LY::NFLD, ET = LY::ET;
   constexpr int F0 = MODE == 0 ? 0 : 1;
   if (MODE == 1 && *(volatile int32_t*)&A.status[ST_PSEUDO_DONE]) return;
@@ -452,8 +458,17 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   T* cr = ys + ET * NFLD * NU;
   T* gs = cr + ET * NFLD * NF;
   T* djs = gs + ET * NG;
-  T* lf = djs + ET;                     // float path: LIFT c, [ET][NFLD][NU]
+  T* lf = djs + ET;                     // float path: LIFT c, then the RK increments, [ET][NFLD][NU]
+  float2* u2s = reinterpret_cast<float2*>(lf + (LY::FLT ? ET * NFLD * NU : 0));  // [ET][2][NU] (flux balance)
   constexpr bool kMMA = LY::MMA;
+  // Mixed path: each element's float-float solution is shifted at stage 4 so
+  // that its quadrature-weighted mass change equals the RK4-weighted sum of
+  // its edge fluxes, -sum_k w_k F_out,k with w_k the physical edge weight
+  // shared bitwise by both sides; the global mass then changes only through
+  // walls (as in ka_tensor).
+  constexpr bool kCons = LY::CONS;
+  __shared__ double tgt[kCons ? 2 * ET : 1];
+  __shared__ float dlt[kCons ? 4 * ET : 1];
 
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
@@ -505,6 +520,27 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
           [&](int c, int r, float v) { lf[c * NU + r] = v; });
       __syncthreads();
     }
+    const bool cons = kCons && A.tacc && A.wphys && stage >= 1;
+    if (cons) {
+      // element flux balance T = -sum_k w_k F_out,k (float-float), RK4-accumulated in FP64
+      for (int t = tid; t < ne * 2; t += blockDim.x) {
+        const int el = t / 2, fld = t % 2;
+        float2 bsum = make_float2(0.f, 0.f);
+        for (int k = 0; k < NF; ++k) {
+          const int64_t og = (e0 + el) * NF + k;
+          const int32_t w = A.fnbr[og];
+          const int64_t pg = (int64_t)(w >> 1);
+          const float Fo = (w & 1) ? (float)fc[((e0 + el) * 2 + fld) * NF + k]
+                                   : -(float)fc[((pg / NF) * 2 + fld) * NF + pg % NF];
+          bsum = ff_add(bsum, ff_mul(A.wphys[og], Fo));
+        }
+        const double Te = -((double)bsum.x + (double)bsum.y);
+        const int64_t gt = (e0 + el) * 2 + fld;
+        if (stage == 1) A.tacc[gt] = Te;
+        else if (stage < 4) A.tacc[gt] = A.tacc[gt] + 2.0 * Te;
+        else tgt[t] = rkc.ddt6 * (A.tacc[gt] + Te);
+      }
+    }
     for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
       const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
       T div = ys[idx];
@@ -521,12 +557,56 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
         A.out[(int64_t)fld * A.E * NU + (e0 + el) * NU + i] = (double)R;
         continue;
       }
+      if constexpr (kCons) {
+        if (cons && stage == 4) {
+          // float-float update now, the element's uniform shift below
+          const float2 u = reinterpret_cast<const float2*>(A.u)[g];
+          const float inc = rkc.dt6 * (reinterpret_cast<const float*>(A.acc)[g] + (float)R);
+          const float s2 = u.x + inc;
+          const float e2 = two_sum_lo(u.x, inc, s2) + u.y;
+          const float hi = s2 + e2;
+          u2s[idx] = make_float2(hi, e2 - (hi - s2));
+          lf[idx] = inc;
+          continue;
+        }
+      }
       const T yt = rk_apply(A, stage, g, R, rkc, (MODE == 1 && stage == 4) ? &sq : nullptr);
       if (!isfinite(yt)) atomicExch(&A.status[ST_STATUS], -4);
       ustg[g] = yt;
       ys[idx] = yt;
     }
     __syncthreads();
+    if (kCons && cons && stage == 4) {
+      for (int t = tid; t < ne * 2; t += blockDim.x) {
+        const int el = t / 2;
+        float2 S2 = make_float2(0.f, 0.f);
+        double W = 0.0;
+        for (int i = 0; i < NU; ++i) {
+          const float2 wd = A.wdetf[(e0 + el) * NU + i];
+          S2 = ff_add(S2, ff_mul(wd, (float)lf[t * NU + i]));
+          W += (double)wd.x + (double)wd.y;
+        }
+        const double d = (tgt[t] - ((double)S2.x + (double)S2.y)) / W;
+        const float dh = (float)d;
+        dlt[2 * t] = dh;
+        dlt[2 * t + 1] = (float)(d - (double)dh);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < ne * NFLD * NU; idx += blockDim.x) {
+        const int el = idx / (NFLD * NU), r = idx % (NFLD * NU), fld = r / NU, i = r % NU;
+        const int64_t g = ((e0 + el) * 2 + F0 + fld) * NU + i;
+        const float2 u = u2s[idx];
+        const float dh = dlt[2 * (el * 2 + fld)], dl = dlt[2 * (el * 2 + fld) + 1];
+        const float s2 = u.x + dh;
+        const float e2 = two_sum_lo(u.x, dh, s2) + (u.y + dl);
+        const float hi = s2 + e2;
+        reinterpret_cast<float2*>(A.u)[g] = make_float2(hi, e2 - (hi - s2));
+        if (!isfinite(hi)) atomicExch(&A.status[ST_STATUS], -4);
+        ustg[g] = (T)hi;
+        ys[idx] = (T)hi;
+      }
+      __syncthreads();
+    }
   }
   if (stage >= 0) {
     if constexpr (kMMA) {

@@ -44,13 +44,13 @@ def _workload(mesh_fn, p, vel, circle, h, **kw):
     return w
 
 
-def _pair(G, w, precision="fp64", precondition=False, fixed=True, vel_cache=True, **okw):
+def _pair(G, w, precision="fp64", precondition=False, fixed=True, vel_cache=True, variant="auto", **okw):
     mesh = w.mesh()
     prm = Params.from_workload(w, pseudo_fixed=fixed, **okw)
     sol = Solver(mesh, w.order, prm, w.velocity)
     sol.initialize(w.circle, precondition=precondition)
     M = G.Mesh.from_synthetic(mesh, w.order)
-    P = G.make_params(w, precision, pseudo_fixed=fixed, vel_cache=vel_cache, **okw)
+    P = G.make_params(w, precision, pseudo_fixed=fixed, vel_cache=vel_cache, variant=variant, **okw)
     F = G.Field(M, P, ic=w.circle, precondition=precondition)
     return sol, F
 
@@ -246,7 +246,7 @@ def test_rhs_parity_mixed(G, case):
 
 
 @pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_stream_p5", "hex_periodic_jitter_p2",
-                                  "hex_periodic_jitter_p3", "hex_rotated_periodic_jitter_p2"])
+                                  "hex_periodic_jitter_p3", "hex_rotated_periodic_jitter_p2", "tri_split_periodic_p2"])
 def test_mixed_mass_conserved_to_round_off(G, case):
     """Mixed path: each element's float-float solution is corrected so that its
     mass change equals the FP64 sum of its (antisymmetric) face fluxes, so the
@@ -436,3 +436,46 @@ def test_noflux_walls_conserve_mass(G, case, precision):
     _, F64 = _pair(G, w)
     with pytest.raises(G.FRError):
         F64.adjoint_record(4, 2)
+
+
+# ---------------------------------------------------------------------------
+# Kernel variants: triangle operator applies on tensor cores (float path)
+
+@pytest.mark.parametrize("case", ["tri_delaunay_p3", "tri_delaunay_p5", "tri_split_periodic_p2"])
+def test_triangle_tensor_core_variant_parity(G, case):
+    w = CASES[case]()
+    sol, F = _pair(G, w, precision="mixed", variant=1)
+    assert F.params.variant == 1
+    _perturb(sol, F)
+    R = F.rhs(0.3).cpu().numpy()
+    Ro = sol.rhs(sol.phi, sol.psi, 0.3)
+    assert _rel(R[0], Ro[0].numpy()) < TOL32, case
+    assert _rel(R[1], Ro[1].numpy()) < TOL32, case
+    Rp = F.rhs_pseudo().cpu().numpy()
+    assert _rel(Rp, sol.rhs_pseudo(sol.psi, sol.phi - 0.5).numpy()) < TOL32
+    # the scalar variant gives the same march to float round-off
+    _, F0 = _pair(G, w, precision="mixed", variant=0)
+    F.step(10)
+    F0.step(10)
+    assert F.sync() == 0 and F0.sync() == 0
+    assert _rel(F.get(0), F0.get(0)) < 1e-5
+
+
+def test_variant_counts_and_rejection(G):
+    w = CASES["tri_delaunay_p3"]()
+    M = G.Mesh.from_synthetic(w.mesh(), w.order)
+    assert G.kernel_variants(M, "mixed") == 2 and G.kernel_variants(M, "fp64") == 1
+    with pytest.raises(G.FRError):
+        G.Field(M, G.make_params(w, "fp64", variant=1), ic=w.circle)
+    wq = CASES["quad_periodic_jitter_p3"]()
+    Mq = G.Mesh.from_synthetic(wq.mesh(), wq.order)
+    assert G.kernel_variants(Mq, "mixed") == 1
+
+
+def test_autotuner_measures_every_variant(G):
+    from paper_2006_10967_gb300 import tune
+    w = CASES["tri_delaunay_p3"]()
+    table = tune.tune([w], "mixed", write=False, steps=20, warmup=5)
+    ent = table[tune.key(1, w.order, "mixed")]
+    assert set(ent["us_per_stage"]) == {"0", "1"}
+    assert str(ent["variant"]) == min(ent["us_per_stage"], key=lambda k: ent["us_per_stage"][k])
