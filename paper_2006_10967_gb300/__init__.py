@@ -360,23 +360,42 @@ def fr_adjoint_step(*a):
     return lib().fr_adjoint_step(*a)
 
 
+class _PlaceholderIC:
+    """Circle initial condition used only to set up a field whose state is
+    then overwritten from device memory."""
+    centre = (0.0, 0.0, 0.0)
+    radius = 0.0
+    beta = 1.0
+
+
+_PLACEHOLDER_IC = _PlaceholderIC()
+
+
 def flow_function(mesh, params_fn, n_steps, ckpt_every):
     """A torch.autograd.Function for phi_T = Flow(phi0, coef): the FR march of
     n_steps from phi0 (psi0 = phi0 - 1/2, no preconditioning) with a stream
     velocity whose coefficients are coef = (A_1..A_M, B_1..B_M).
     params_fn(coef) -> fr_params.  Backward is the hand-written adjoint
-    (fr_adjoint_record / fr_adjoint_step)."""
+    (fr_adjoint_record / fr_adjoint_step).  phi0 (a CUDA float64 tensor of
+    the mesh's shape) and phi_T stay on the device: the field is set up with a
+    placeholder state and then loaded from phi0 by device copies."""
     import torch
 
     class _Flow(torch.autograd.Function):
         @staticmethod
         def forward(ctx, phi0, coef):
             P = params_fn(coef.detach().cpu().numpy())
-            F = Field(mesh, P, phi0=phi0.detach().cpu().numpy(), precondition=False)
+            u0 = phi0.detach().to(device="cuda", dtype=torch.float64).reshape(mesh.shape).contiguous()
+            F = Field(mesh, P, ic=_PLACEHOLDER_IC, precondition=False)
+            F.set_device(0, u0)
+            F.set_device(1, u0 - 0.5)
+            F.set_device(2, u0 - 0.5)
             F.adjoint_record(n_steps, ckpt_every)
             ctx.field = F
             ctx.n_coef = coef.numel()
-            return torch.from_numpy(F.get(0)).to(phi0.device)
+            out = torch.empty_like(u0)
+            F.get_device(0, out)
+            return out.to(phi0.device)
 
         @staticmethod
         def backward(ctx, g):

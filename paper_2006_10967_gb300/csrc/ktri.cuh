@@ -437,9 +437,10 @@ struct KATriLayout {
   // flux balance, the float-float states [ET][2][NU]
   static constexpr int BYTES_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1 + (FLT ? NFLD * S::NU : 0)) * (int)sizeof(T) +
                                   (CONS ? 2 * S::NU * 8 : 0);
+  static constexpr int HEAD_EL = (NFLD * S::NU + NFLD * S::NF + S::NG + 1 + (FLT ? NFLD * S::NU : 0));  // T values before u2s
   static constexpr int ETr = 16384 / BYTES_EL;
   static constexpr int ET = ETr < 1 ? 1 : (ETr > 128 ? 128 : ETr);
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64;
+  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + sizeof(TriOpsS<P, T>) + 64 + 16;  // + u2s alignment
 };
 
 template <int P, typename T, int MODE, bool TC = false>
@@ -459,7 +460,9 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   T* gs = cr + ET * NFLD * NF;
   T* djs = gs + ET * NG;
   T* lf = djs + ET;                     // float path: LIFT c, then the RK increments, [ET][NFLD][NU]
-  float2* u2s = reinterpret_cast<float2*>(lf + (LY::FLT ? ET * NFLD * NU : 0));  // [ET][2][NU] (flux balance)
+  // [ET][2][NU] float-float states of the flux balance, on a 16-byte boundary
+  float2* u2s = reinterpret_cast<float2*>(
+      (reinterpret_cast<uintptr_t>(base + ET * LY::HEAD_EL) + 15) & ~static_cast<uintptr_t>(15));
   constexpr bool kMMA = LY::MMA;
   // Mixed path: each element's float-float solution is shifted at stage 4 so
   // that its quadrature-weighted mass change equals the RK4-weighted sum of
