@@ -342,33 +342,100 @@ def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_ste
     """The batched ensemble: 256 periodic quad instances (n ~ U{16..96},
     p ~ U{2..5}, random circles, random-phase stream-function velocities), one
     batch field per order, each on its own CUDA stream; one benchmark step =
-    rk_steps RK4 steps of every instance."""
+    rk_steps RK4 steps of every instance.  Timed with CUDA events on the
+    current stream, which the order streams join at the start and the end."""
     import torch
     ws = S.ensemble_instances(n_inst, seed=3)
     fields = G.batch_from_workloads(ws, precision=precision)
     streams = [torch.cuda.Stream() for _ in fields]
     ndof = sum(F.mesh.info.n_dof for _, F, _ in fields)
+    cur = torch.cuda.current_stream()
+
     def one():
+        start = torch.cuda.Event()
+        start.record(cur)
         for (p, F, _), st in zip(fields, streams):
+            st.wait_event(start)
             F.step(rk_steps, stream=st)
         for st in streams:
-            st.synchronize()
+            done = torch.cuda.Event()
+            done.record(st)
+            cur.wait_event(done)
     for _ in range(W):
         one()
     torch.cuda.synchronize()
     times = []
+    barrier(world)
     for _ in range(K):
         flush.zero_()
         torch.cuda.synchronize()
-        barrier(world)
-        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
         one()
-        times.append(time.perf_counter() - t0)
+        e1.record(cur)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
     tot = max_over_ranks(sum(times), world)
+    value = world * K * rk_steps * 4 * ndof / tot
     per_order = {str(p): {"instances": len(r), "dof": F.mesh.info.n_dof} for p, F, r in fields}
     status = max((F.sync() for _, F, _ in fields), key=abs)
-    return {"value": world * K * rk_steps * 4 * ndof / tot, "ms_per_step": tot / K * 1e3, "ndof": ndof,
-            "per_order": per_order, "status": status, "rk_steps": rk_steps, "instances": n_inst}
+    # HBM roofline: algorithmic bytes of every order group per stage
+    b_stage = sum(alg_bytes_per_dof("quad", p, precision) * F.mesh.info.n_dof for p, F, _ in fields)
+    stage_s = tot / (K * rk_steps * 4)
+    pk = peaks()
+    peak = pk.get("hbm_gbs") or 6800.0
+    roof = {"bound": "hbm", "kernel": "RK stage of every order group (kb_tensor + ka_tensor per order, 4 streams)",
+            "achieved": b_stage / stage_s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": b_stage / stage_s / 1e9 / peak, "traffic": None,
+            "alg_bytes_per_stage": b_stage, "stage_us": stage_s * 1e6,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk.get("hbm_gbs") else "fallback 6.8 TB/s",
+            "timing": "CUDA events on the current stream around the joined order streams"}
+    # end to end through the C ABI with host buffers (phi and psi up, phi down, every field)
+    L = G.lib()
+    dp = C.POINTER(C.c_double)
+    ptr = lambda t: C.cast(C.c_void_p(t.data_ptr()), dp)
+    host = [(torch.from_numpy(F.get(0)).pin_memory(), torch.from_numpy(F.get(1)).pin_memory(),
+             torch.empty(F.mesh.shape, dtype=torch.float64).pin_memory()) for _, F, _ in fields]
+    te = []
+    Ke = min(K, 3)
+    for _ in range(Ke):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
+            sp = C.c_void_p(st.cuda_stream)
+            G.check(L.fr_field_set(F.handle, 0, ptr(hphi), sp), "fr_field_set")
+            G.check(L.fr_field_set(F.handle, 1, ptr(hpsi), sp), "fr_field_set")
+            G.check(L.fr_step(F.handle, rk_steps, sp), "fr_step")
+        for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
+            G.check(L.fr_field_get(F.handle, 0, ptr(hres), C.c_void_p(st.cuda_stream)), "fr_field_get")
+        te.append(time.perf_counter() - t0)
+    e2e = {"value": world * Ke * rk_steps * 4 * ndof / max_over_ranks(sum(te), world), "unit": UNIT,
+           "steps": Ke, "h2d_bytes_per_step": 2 * ndof * 8, "d2h_bytes_per_step": ndof * 8}
+    return {"value": value, "ms_per_step": tot / K * 1e3, "ndof": ndof, "roofline": roof, "e2e": e2e,
+            "per_order": per_order, "status": status, "rk_steps": rk_steps, "instances": n_inst,
+            "workloads": ws}
+
+
+def ensemble_cpu_baseline(S, ws, n_sample=16, nsteps=1):
+    """The FP64 oracle on the first n_sample instances of the ensemble, nsteps
+    RK4 steps each, all host threads; DOF-stage/s over the sample."""
+    import torch
+    from oracle import Params, Solver
+    tot_dof, tot_t = 0, 0.0
+    for w in ws[:n_sample]:
+        sol = Solver(w.mesh(), w.order, Params.from_workload(w), w.velocity)
+        sol.initialize(w.circle, precondition=False)
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            sol.rk4_step()
+        tot_t += time.perf_counter() - t0
+        tot_dof += sol.E * sol.Nu
+    return {"value": tot_dof * 4 * nsteps / tot_t, "unit": UNIT, "cores": torch.get_num_threads(),
+            "os_cpu_count": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nsteps} RK4 step(s) of each of the first {n_sample} ensemble instances "
+                      f"({tot_dof} solution points), FP64 torch-CPU oracle, {tot_t:.1f} s"}
 
 
 def cpu_baseline(S, w, mesh, nsteps, sample_note):
@@ -483,6 +550,7 @@ def main():
         import paper_2006_10967_gb300 as G
         flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
         out = run_ensemble(G, S, args.steps, max(args.warmup, 3), world, flush, args.precision)
+        cpu = ensemble_cpu_baseline(S, out["workloads"]) if rank == 0 and world == 1 and args.cpu_steps > 0 else None
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": out["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
@@ -492,6 +560,8 @@ def main():
                            "per_order": out["per_order"], "precision": args.precision,
                            "launch": "one batch field per order, each on its own CUDA stream",
                            "l2": "flushed before each timed step; working set larger than L2"},
+                "roofline": out["roofline"], "e2e": out["e2e"], "cpu_baseline": cpu,
+                "gpu_launches": 2 * 4 * out["rk_steps"] * len(out["per_order"]) * args.steps,
                 "status": out["status"]}
         if rank == 0:
             print(json.dumps(line))

@@ -453,11 +453,15 @@ def test_triangle_tensor_core_variant_parity(G, case):
     assert _rel(R[1], Ro[1].numpy()) < TOL32, case
     Rp = F.rhs_pseudo().cpu().numpy()
     assert _rel(Rp, sol.rhs_pseudo(sol.psi, sol.phi - 0.5).numpy()) < TOL32
-    # the scalar variant gives the same march to float round-off
+    # both variants march with the oracle to float round-off
     _, F0 = _pair(G, w, precision="mixed", variant=0)
+    F0.set(1, sol.psi.numpy())
     F.step(10)
     F0.step(10)
+    sol.step(10)
     assert F.sync() == 0 and F0.sync() == 0
+    assert _rel(F.get(0), sol.phi.numpy()) < 1e-5
+    assert _rel(F0.get(0), sol.phi.numpy()) < 1e-5
     assert _rel(F.get(0), F0.get(0)) < 1e-5
 
 
