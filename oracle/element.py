@@ -28,7 +28,11 @@ interior and unisolvent, its interpolatory weights int l_i are positive for
 p <= 5, and the advection operator on it (with the penalty tau = 0.1) is close
 to energy neutral (the tests bound the largest real part of its spectrum); the same
 map of equispaced nodes (the principal lattice) gives negative weights and
-advection modes that grow by e^29 over one Rider-Kothe period at p = 3.
+advection modes that grow by e^29 over one Rider-Kothe period at p = 3.  At
+p = 5 the Gauss-Legendre set leaves a mode growing at Re lambda = 0.05 (the
+Rider-Kothe march fails), so p = 5 maps the Chebyshev nodes of the second
+kind instead, x_k = cos(k pi / (p + 2)), k = 1..p+1 (the Gauss-Jacobi(1/2, 1/2)
+roots), whose advection spectrum keeps Re lambda below 0.01.
 """
 import math
 from dataclasses import dataclass
@@ -205,10 +209,14 @@ def ref_element(etype, p):
         high = np.array([max(d) == p for d in degrees])
         modal = lambda x: _modal_tensor(p, dim, x)[:2]
     else:
-        # Blyth-Pozrikidis map of the 1D Gauss-Legendre nodes v on [0, 1]:
+        # Blyth-Pozrikidis map of the 1D nodes v on [0, 1] (Gauss-Legendre;
+        # Chebyshev of the second kind at p = 5):
         # lattice index (i, j, k), i + j + k = p, goes to the barycentric point
         # l_a = (1 + 2 v_a - v_b - v_c) / 3 (equispaced v would give the lattice)
-        v = (g + 1.0) / 2.0
+        if p == 5:   # Chebyshev nodes of the second kind, ascending
+            v = (np.cos(np.arange(n, 0, -1) * math.pi / (n + 1)) + 1.0) / 2.0
+        else:
+            v = (g + 1.0) / 2.0
         pts = []
         for j in range(p + 1):
             for i in range(p + 1 - j):

@@ -189,16 +189,22 @@ void build_tri(int p, TriRef& t) {
   t.nf = nf;
   double g[kMaxN], w[kMaxN];
   gauss_legendre(n, g, w);
-  // Solution points: the Blyth-Pozrikidis map of the Gauss-Legendre nodes
-  // v = (g + 1)/2: lattice index (i, j, k), i + j + k = p, goes to the
-  // barycentric point l_a = (1 + 2 v_a - v_b - v_c)/3 (symmetric, interior,
-  // positive interpolatory weights for p <= 5)
+  // Solution points: the Blyth-Pozrikidis map of 1D nodes v on [0, 1]:
+  // lattice index (i, j, k), i + j + k = p, goes to the barycentric point
+  // l_a = (1 + 2 v_a - v_b - v_c)/3 (symmetric, interior, positive
+  // interpolatory weights).  The nodes are the Gauss-Legendre points for
+  // p <= 4 and the Chebyshev points of the second kind for p = 5,
+  // cos(m pi / (p + 2)), m = p + 1, ..., 1, whose advection operator has no
+  // growing mode where the Gauss-Legendre one does.
+  double v1[kMaxN];
+  for (int m = 0; m < n; ++m)
+    v1[m] = p == 5 ? 0.5 * (std::cos((double)(n - m) * M_PI / (double)(n + 1)) + 1.0) : 0.5 * (g[m] + 1.0);
   t.xu.resize(nu * 2);
   int c = 0;
   for (int j = 0; j <= p; ++j)
     for (int i = 0; i <= p - j; ++i, ++c) {
       const int k = p - i - j;
-      const double vi = 0.5 * (g[i] + 1.0), vj = 0.5 * (g[j] + 1.0), vk = 0.5 * (g[k] + 1.0);
+      const double vi = v1[i], vj = v1[j], vk = v1[k];
       const double l1 = (1.0 + 2.0 * vi - vj - vk) / 3.0;
       const double l2 = (1.0 + 2.0 * vj - vi - vk) / 3.0;
       const double l0 = 1.0 - l1 - l2;

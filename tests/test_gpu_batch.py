@@ -69,3 +69,26 @@ def test_ensemble_workload_builds_and_steps(G):
         F.step(5)
         assert F.sync() == 0
         assert abs(F.mass(0) - m0) < 1e-12 * abs(m0)   # periodic instances conserve mass
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_multi_order_ensemble_matches_independent_oracle_runs(G, precision, tol):
+    """An ensemble with instances of orders 2, 3 and 4 (one batch field per
+    order, as the 256-instance benchmark builds it) against one oracle run per
+    instance, preconditioning inside the window."""
+    ws = _instances(2, [3, 4], seed=5) + _instances(3, [3], seed=6) + _instances(4, [2, 3], seed=7)
+    fields = G.batch_from_workloads(ws, precision=precision, pseudo_fixed=True)
+    assert sorted(p for p, _, _ in fields) == [2, 3, 4]
+    by_order = {}
+    for w in ws:
+        by_order.setdefault(w.order, []).append(w)
+    for p, F, ranges in fields:
+        F.step(4)
+        assert F.sync() == 0
+        phi = F.get(0)
+        for w, (b, e) in zip(by_order[p], ranges):
+            sol = Solver(w.mesh(), p, Params.from_workload(w, pseudo_fixed=True), w.velocity)
+            sol.initialize(w.circle, precondition=True)
+            sol.step(4)
+            ref = sol.phi.numpy()
+            assert np.abs(phi[b:e] - ref).max() / np.abs(ref).max() < tol, (p, b, e)

@@ -141,8 +141,10 @@ def test_flux_points_on_boundary_and_normals_unit(etype, p):
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_triangle_points_symmetric_interior_positive(p):
     """The triangle's solution points (Blyth-Pozrikidis map of the 1D
-    Gauss-Legendre nodes): the set is invariant under the vertex permutations,
-    interior, and its interpolatory weights int l_i are positive."""
+    Gauss-Legendre nodes; of the Chebyshev nodes of the second kind,
+    cos(k pi / (p + 2)), at p = 5): the set is invariant under the vertex
+    permutations, interior, and its interpolatory weights int l_i are
+    positive."""
     el = ref_element("tri", p)
     x = el.xu
     lam = np.stack([-(x[:, 0] + x[:, 1]) / 2, (1 + x[:, 0]) / 2, (1 + x[:, 1]) / 2], 1)
@@ -152,7 +154,12 @@ def test_triangle_points_symmetric_interior_positive(p):
         assert key(lam[:, perm]) == key(lam)
     assert el.wq.min() > 0.0 and el.wq.sum() == pytest.approx(2.0, rel=1e-14)
     # the smallest barycentric coordinate is the one of lattice index (0, 0, p):
-    # (1 + 2 v_0 - v_0 - v_p) / 3 with v the Gauss-Legendre nodes on [0, 1]
-    g, _ = gauss_legendre(p + 1)
+    # (1 + 2 v_0 - v_0 - v_p) / 3 with v the 1D nodes on [0, 1]
+    if p == 5:
+        g = np.cos(np.arange(p + 1, 0, -1) * math.pi / (p + 2))   # the roots of U_{p+1}
+        t = np.arccos(g)
+        assert np.allclose(np.sin((p + 2) * t) / np.sin(t), 0.0, atol=1e-12)
+    else:
+        g, _ = gauss_legendre(p + 1)
     v = (g + 1) / 2
     assert lam.min() == pytest.approx((1 + v[0] - v[p]) / 3, abs=1e-14)

@@ -365,7 +365,7 @@ def test_preconditioning_fixed_point_and_sign():
     assert float(slope.mean()) < 2.0 and float(slope.mean()) > 1.0
 
 
-@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
 def test_triangle_advection_operator_is_nearly_energy_neutral(p):
     """The advection operator (gamma = eps = 0, with the LDG penalty tau = 0.1) of the
     Rider-Kothe field on split and Delaunay triangles has no mode that grows
