@@ -72,6 +72,8 @@ def parse():
                          "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads); "
                          "c2s: Rider-Kothe on split-triangle meshes (--mesh-n, --order <= 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--ensemble-launch", default="group", choices=["group", "streams"],
+                    help="c4: one launch per RK stage over all orders, or one field per order on its own stream")
     ap.add_argument("--rk-steps", type=int, default=STEPS_PER_BENCH_STEP,
                     help="RK4 steps per benchmark step (profiling captures use fewer launches)")
     return ap.parse_args()
@@ -338,7 +340,7 @@ def adjoint_ratio(G, S):
     return res
 
 
-def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_steps=200):
+def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_steps=200, launch="group"):
     """The batched ensemble: 256 periodic quad instances (n ~ U{16..96},
     p ~ U{2..5}, random circles, random-phase stream-function velocities), one
     batch field per order, each on its own CUDA stream; one benchmark step =
@@ -351,7 +353,12 @@ def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_ste
     ndof = sum(F.mesh.info.n_dof for _, F, _ in fields)
     cur = torch.cuda.current_stream()
 
+    group = G.Group([F for _, F, _ in fields]) if launch == "group" else None
+
     def one():
+        if group is not None:          # one launch per kernel per RK stage over all orders
+            group.step(rk_steps, stream=cur)
+            return
         start = torch.cuda.Event()
         start.record(cur)
         for (p, F, _), st in zip(fields, streams):
@@ -385,7 +392,9 @@ def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_ste
     stage_s = tot / (K * rk_steps * 4)
     pk = peaks()
     peak = pk.get("hbm_gbs") or 6800.0
-    roof = {"bound": "hbm", "kernel": "RK stage of every order group (kb_tensor + ka_tensor per order, 4 streams)",
+    roof = {"bound": "hbm", "kernel": ("RK stage of all orders: kb_group + ka_group (one launch each)"
+                                       if group is not None else
+                                       "RK stage of every order group (kb_tensor + ka_tensor per order, 4 streams)"),
             "achieved": b_stage / stage_s / 1e9, "peak": peak, "unit": "GB/s",
             "frac": b_stage / stage_s / 1e9 / peak, "traffic": None,
             "alg_bytes_per_stage": b_stage, "stage_us": stage_s * 1e6,
@@ -403,17 +412,26 @@ def run_ensemble(G, S, K, W, world, flush, precision="mixed", n_inst=256, rk_ste
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
-            sp = C.c_void_p(st.cuda_stream)
-            G.check(L.fr_field_set(F.handle, 0, ptr(hphi), sp), "fr_field_set")
-            G.check(L.fr_field_set(F.handle, 1, ptr(hpsi), sp), "fr_field_set")
-            G.check(L.fr_step(F.handle, rk_steps, sp), "fr_step")
-        for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
-            G.check(L.fr_field_get(F.handle, 0, ptr(hres), C.c_void_p(st.cuda_stream)), "fr_field_get")
+        if group is not None:
+            sp = C.c_void_p(cur.cuda_stream)
+            for ((p, F, _), (hphi, hpsi, hres)) in zip(fields, host):
+                G.check(L.fr_field_set(F.handle, 0, ptr(hphi), sp), "fr_field_set")
+                G.check(L.fr_field_set(F.handle, 1, ptr(hpsi), sp), "fr_field_set")
+            G.check(L.fr_group_step(group.handle, rk_steps, sp), "fr_group_step")
+            for ((p, F, _), (hphi, hpsi, hres)) in zip(fields, host):
+                G.check(L.fr_field_get(F.handle, 0, ptr(hres), sp), "fr_field_get")
+        else:
+            for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
+                sp = C.c_void_p(st.cuda_stream)
+                G.check(L.fr_field_set(F.handle, 0, ptr(hphi), sp), "fr_field_set")
+                G.check(L.fr_field_set(F.handle, 1, ptr(hpsi), sp), "fr_field_set")
+                G.check(L.fr_step(F.handle, rk_steps, sp), "fr_step")
+            for ((p, F, _), st, (hphi, hpsi, hres)) in zip(fields, streams, host):
+                G.check(L.fr_field_get(F.handle, 0, ptr(hres), C.c_void_p(st.cuda_stream)), "fr_field_get")
         te.append(time.perf_counter() - t0)
     e2e = {"value": world * Ke * rk_steps * 4 * ndof / max_over_ranks(sum(te), world), "unit": UNIT,
            "steps": Ke, "h2d_bytes_per_step": 2 * ndof * 8, "d2h_bytes_per_step": ndof * 8}
-    return {"value": value, "ms_per_step": tot / K * 1e3, "ndof": ndof, "roofline": roof, "e2e": e2e,
+    return {"value": value, "ms_per_step": tot / K * 1e3, "ndof": ndof, "roofline": roof, "e2e": e2e, "launch": launch,
             "per_order": per_order, "status": status, "rk_steps": rk_steps, "instances": n_inst,
             "workloads": ws}
 
@@ -549,7 +567,8 @@ def main():
         __graft_entry__.build()
         import paper_2006_10967_gb300 as G
         flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-        out = run_ensemble(G, S, args.steps, max(args.warmup, 3), world, flush, args.precision)
+        out = run_ensemble(G, S, args.steps, max(args.warmup, 3), world, flush, args.precision,
+                           launch=args.ensemble_launch)
         cpu = ensemble_cpu_baseline(S, out["workloads"]) if rank == 0 and world == 1 and args.cpu_steps > 0 else None
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": out["ms_per_step"], "higher_is_better": True,
@@ -558,7 +577,9 @@ def main():
                 "config": {"workload": "ensemble256_quad_p2to5_stream", "instances": out["instances"],
                            "solution_points": out["ndof"], "rk_steps_per_step": out["rk_steps"],
                            "per_order": out["per_order"], "precision": args.precision,
-                           "launch": "one batch field per order, each on its own CUDA stream",
+                           "launch": ("one launch per kernel per RK stage over the order groups (fr_group_step)"
+                                      if out["launch"] == "group" else
+                                      "one batch field per order, each on its own CUDA stream"),
                            "l2": "flushed before each timed step; working set larger than L2"},
                 "roofline": out["roofline"], "e2e": out["e2e"], "cpu_baseline": cpu,
                 "gpu_launches": 2 * 4 * out["rk_steps"] * len(out["per_order"]) * args.steps,

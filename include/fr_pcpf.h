@@ -299,6 +299,26 @@ int fr_field_set(fr_field* field, int which, const double* host, void* stream);
 int fr_field_get_device(fr_field* field, int which, double* dev, void* stream);
 int fr_field_set_device(fr_field* field, int which, const double* dev, void* stream);
 
+/* ---- groups ----------------------------------------------------------
+ * A group steps several fields together with one launch of the residual
+ * kernel and one of the update kernel per RK stage: block b of a launch
+ * belongs to the field whose range of blocks holds b (a work list over the
+ * fields' element tiles), and each field keeps its own state, time and
+ * per-element parameters.  Built for the batched ensemble (Section 4's
+ * workloads in an uneven ensemble): quadrilateral FR_MIXED fields of
+ * distinct orders 2..5, with equal n_precond and step counts.  The physical
+ * steps of all fields run as one launch sequence (captured in CUDA graphs);
+ * a preconditioning due before a step runs per field (fr_precondition).
+ * The fields must outlive the group and must not be stepped on their own
+ * while it is used.  Errors: FR_EINVAL (null, n outside 1..4),
+ * FR_EUNSUPPORTED (a field outside that set, two fields of one order,
+ * differing n_precond or step counts), FR_ENOMEM, FR_ECUDA. */
+typedef struct fr_group fr_group;
+int fr_group_create(fr_field* const* fields, int n, fr_group** out);
+/* n_steps RK4 steps of every field of the group, asynchronous on `stream`. */
+int fr_group_step(fr_group* group, int n_steps, void* stream);
+void fr_group_destroy(fr_group* group);
+
 /* Number of kernel variants (fr_params.variant) built for the mesh's element
  * type and order in `precision` (FR_FP64 or FR_MIXED): *count >= 1. */
 int fr_kernel_variants(const fr_mesh* mesh, int precision, int32_t* count);

@@ -406,6 +406,33 @@ def flow_function(mesh, params_fn, n_steps, ckpt_every):
     return _Flow.apply
 
 
+class Group:
+    """Fields stepped together, one launch per kernel per RK stage
+    (fr_group_create / fr_group_step): the quad mixed-precision batch fields
+    of distinct orders 2..5 of an ensemble."""
+
+    def __init__(self, fields):
+        import torch
+        self.torch = torch
+        self.fields = list(fields)
+        arr = (C.c_void_p * len(self.fields))(*[f.handle for f in self.fields])
+        h = C.c_void_p()
+        check(lib().fr_group_create(arr, len(self.fields), C.byref(h)), "fr_group_create")
+        self.handle = h
+
+    def step(self, n=1, stream=None):
+        s = stream if stream is not None else self.torch.cuda.current_stream()
+        check(lib().fr_group_step(self.handle, int(n), C.c_void_p(s.cuda_stream)), "fr_group_step")
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None:
+            try:
+                lib().fr_group_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
 def batch_from_workloads(workloads, precision="mixed", precondition=True, **kw):
     """Group workload records (synthetic.Workload, all quad or hex) by order and
     build one batch field per order.  Returns [(order, Field, [element ranges])]."""

@@ -94,6 +94,9 @@ _SIGS = {
     "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
     "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fr_kernel_variants": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int32)]),
+    "fr_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "fr_group_step": (C.c_int, [_vp, C.c_int, _vp]),
+    "fr_group_destroy": (None, [_vp]),
     "fr_profile": (C.c_int, [_vp, C.c_int]),
     "fr_profile_read": (C.c_int, [_vp, _vp, _dp, C.POINTER(C.c_int64)]),
     "fr_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _dp]),

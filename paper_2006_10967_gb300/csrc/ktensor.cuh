@@ -312,6 +312,7 @@ struct KBLayout {
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
   static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 13;  // + region alignment
+  static_assert(ET * S::NF < 0x8000, "L-list entries keep bit 15 for the wall flag");
   static constexpr int SMB = smem_blocks((long)SMEM + ET * 2 * (int)sizeof(T) + 64);
   static constexpr int MINB = OCC && SMB < MinBlocks<THREADS, T>::v ? SMB : MinBlocks<THREADS, T>::v;
 };
@@ -321,8 +322,7 @@ struct KBLayout {
 // thread one solution-point line; the 1D operators are read from the kernel
 // parameters (constant bank) with compile-time indices.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<DIM, N, T, MODE>::MINB)
-    kb_tensor(const KArgs A) {
+__device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
   using S = TS<DIM, N>;
   using LY = KBLayout<DIM, N, T, MODE>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   T* vtab = sc.take<T>(MODE == 0 ? ET * DIM * NT * 2 : 0);  // [ET][DIM][NT][2]
   uint16_t* llist = sc.take<uint16_t>(ET * NF);       // [ET*NF] L flux points
 
-  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int64_t e0 = (int64_t)blk * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
   const T* ustg = reinterpret_cast<const T*>(A.ustg);
   const T* tr = reinterpret_cast<const T*>(A.tr);
@@ -455,8 +455,10 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
       if (fsel == 0) {
         // L points go to the compacted list of Step 5; R points get no flux here
-        if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k0);
-        if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)(lel * NF + k1);
+        // entry: tile flux point, bit 15 set at walls (own partner)
+        const int64_t g0 = (e0 + lel) * NF + k0, g1 = (e0 + lel) * NF + k1;
+        if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k0) | ((w0 >> 1) == g0 ? 0x8000 : 0));
+        if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k1) | ((w1 >> 1) == g1 ? 0x8000 : 0));
       }
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
@@ -564,11 +566,13 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   // ---- Step 5 on L flux points (q^f by Eq. extrapolateGrad) ----------------
   const int nLpts = nL;
   for (int t = tid; t < nLpts; t += blockDim.x) {
-    const int code = llist[t];
+    const int code = llist[t] & 0x7fff;
+    const bool wallp = (llist[t] >> 15) != 0;  // wall point (own partner)
     const int el = code / NF, k = code % NF;
-    // partner flux point: the common flux also goes to its slot, where the
-    // partner's ka_tensor lifts it (a wall point is its own partner)
-    const int64_t og = (e0 + el) * NF + k, pg = (int64_t)(A.fnbr[og] >> 1);
+    // partner flux point: the common flux also goes to its slot on quads,
+    // where the partner's ka_tensor lifts it (a wall point is its own partner)
+    const int64_t og = (e0 + el) * NF + k;
+    const int64_t pg = FaceScatter<DIM>::v ? (int64_t)(A.fnbr[og] >> 1) : og;
     const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
@@ -651,14 +655,14 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       T fvn = 0;
 #pragma unroll
       for (int c = 0; c < DIM; ++c) fvn += nh[c] * (epsel * qf[0][c] - sharp * qn[c]);
-      const bool shut = P.noflux && pg == og;  // no-flux wall point
+      const bool shut = P.noflux && wallp;  // no-flux wall point
       const T Fp = shut ? (T)0 : (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
       const T Fs = shut ? (T)0 : (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
       // the transformed common flux F~ = |pn| F out of L; the R side uses -F~
       const T Fp_t = pm * Fp, Fs_t = pm * Fs;
       fc[((e0 + el) * 2 + 0) * NF + k] = Fp_t;
       fc[((e0 + el) * 2 + 1) * NF + k] = Fs_t;
-      if (FaceScatter<DIM>::v && pg != og) {
+      if (FaceScatter<DIM>::v && !wallp) {
         fc[pslot] = Fp_t;
         fc[pslot + NF] = Fs_t;
       }
@@ -678,7 +682,7 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
       const T L_ = cor[el * NF + k];  // own trace (Step 1)
       const T F = pm * (-nus[el] * gn + P.tau_pseudo * (L_ - uo[el * NF + k]));
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
-      if (FaceScatter<DIM>::v && pg != og) fc[pslot + NF] = F;
+      if (FaceScatter<DIM>::v && !wallp) fc[pslot + NF] = F;
       cor[el * NF + k] = F;
     }
   }
@@ -902,6 +906,14 @@ __global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<D
   }
 }
 
+// kb_tensor: one block per tile of ET elements (the body above with the
+// block's index; a group launch calls the same body, see k_group.cu)
+template <int DIM, int N, typename T, int MODE>
+__global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<DIM, N, T, MODE>::MINB)
+    kb_tensor(const KArgs A) {
+  kb_tensor_body<DIM, N, T, MODE>(A, blockIdx.x);
+}
+
 // ============================================================================
 template <int DIM, int N, typename T, int MODE>
 struct KALayout {
@@ -923,15 +935,17 @@ struct KALayout {
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
   static constexpr int MINB = MinBlocks<THREADS, T>::v;
-  static constexpr size_t SMEM = (size_t)ET * BYTES_EL + 16 * 9;  // + region alignment
+  // per-element RK constants and the mixed path's flux-balance work arrays
+  // (beside the tile; not counted in the tile-size budget above)
+  static constexpr int EXTRA_EL = (int)sizeof(RKConstF) + (PRE ? 2 * LN * 8 + 2 * 8 + 4 * 4 : 0);
+  static constexpr size_t SMEM = (size_t)ET * (BYTES_EL + EXTRA_EL) + 16 * 13;  // + region alignment
 };
 
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
 // as in kb_tensor, the last of which also applies the update to its line.  stage -1 writes du/dt to A.out (fp64) and leaves the
 // state alone; stage 0 only recomputes the traces of ustg.
 template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<DIM, N, T, MODE>::MINB)
-    ka_tensor(const KArgs A) {
+__device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   using S = TS<DIM, N>;
   using LY = KALayout<DIM, N, T, MODE>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
@@ -950,8 +964,12 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   float* acs = sc.take<float>(PRE ? ET * 2 * NU : 0);    // RK accumulator
   float2* wds = sc.take<float2>(PRE ? ET * NU : 0);      // w det J (float-float)
   double* tas = sc.take<double>(PRE ? ET * 2 : 0);       // mass-balance accumulator
+  RKConstF* rks = sc.take<RKConstF>(ET);                 // RK constants per element (batches)
+  float2* fb = sc.take<float2>(PRE ? 2 * ET * LN : 0);   // flux balances, per line
+  double* tgt = sc.take<double>(PRE ? 2 * ET : 0);       // target mass change per element and field
+  float* dlt = sc.take<float>(PRE ? 4 * ET : 0);         // uniform shift (float-float)
 
-  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int64_t e0 = (int64_t)blk * ET;
   const int ne = (int)min((int64_t)ET, A.E - e0);
   T* ustg = reinterpret_cast<T*>(A.ustg);
   T* tr = reinterpret_cast<T*>(A.tr);
@@ -1026,7 +1044,6 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
 
   double sq = 0.0;
   // RK constants: one set, or one per element for batched instances
-  __shared__ RKConstF rks[ET];
   const RKConstF& rk0 = A.rk;
   if (A.ep) {
     for (int el = tid; el < ne; el += blockDim.x) rks[el] = MODE == 0 ? A.ep[e0 + el].rk : A.ep[e0 + el].rkp;
@@ -1034,9 +1051,6 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
   }
   auto rkc_el = [&](int el) -> const RKConstF& { return A.ep ? rks[el] : rk0; };
   // mixed path: element flux balances (float-float partial sums per line)
-  __shared__ float2 fb[kCons ? 2 * ET * LN : 1];
-  __shared__ double tgt[kCons ? 2 * ET : 1];
-  __shared__ float dlt[kCons ? 4 * ET : 1];
   if (stage != 0) {
     // ---- lift of the R-side common fluxes: minus L's transformed flux, one
     //      pass per axis
@@ -1218,11 +1232,17 @@ __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<D
       }
     }
   }
-  if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)
+  if (MODE == 0 && stage == 4 && A.use_dev_time && blk == 0 && tid == 0)
     A.dstate[DS_TIME] = A.dstate[DS_TIME] + A.dt;
   if (MODE == 0 && stage == 4 && A.use_dev_time && A.ep)
     for (int el = tid; el < ne; el += blockDim.x) A.ep[e0 + el].t += A.ep[e0 + el].dt;
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
+}
+
+template <int DIM, int N, typename T, int MODE>
+__global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<DIM, N, T, MODE>::MINB)
+    ka_tensor(const KArgs A) {
+  ka_tensor_body<DIM, N, T, MODE>(A, blockIdx.x);
 }
 
 // Spatial velocity factor v(x) (g = 1) at the solution and flux points of

@@ -92,3 +92,37 @@ def test_multi_order_ensemble_matches_independent_oracle_runs(G, precision, tol)
             sol.step(4)
             ref = sol.phi.numpy()
             assert np.abs(phi[b:e] - ref).max() / np.abs(ref).max() < tol, (p, b, e)
+
+
+@pytest.mark.parametrize("precondition_every", [1000, 3])
+def test_group_launch_matches_per_field_steps(G, precondition_every):
+    """One launch per kernel per RK stage over the order groups of an
+    ensemble (fr_group_step) gives the same bits as stepping each order's
+    batch field on its own, with and without a preconditioning in the window."""
+    ws = _instances(2, [3, 4], seed=5) + _instances(3, [3], seed=6) + _instances(4, [2, 3], seed=7) + \
+        _instances(5, [2], seed=8)
+    for w in ws:
+        w.n_precond = precondition_every
+    fa = G.batch_from_workloads(ws, precision="mixed", pseudo_fixed=True)
+    fb = G.batch_from_workloads(ws, precision="mixed", pseudo_fixed=True)
+    grp = G.Group([F for _, F, _ in fa])
+    for n in (5, 17):
+        grp.step(n)
+        for _, F, _ in fb:
+            F.step(n)
+    for (p, Fa, _), (_, Fb, _) in zip(fa, fb):
+        assert Fa.sync() == 0 and Fb.sync() == 0
+        for which in (0, 1):
+            assert np.array_equal(Fa.get(which), Fb.get(which)), (p, which)
+        assert Fa.stats()["t"] == Fb.stats()["t"]
+
+
+def test_group_rejects_unsupported_fields(G):
+    ws = _instances(2, [3], seed=5) + _instances(2, [4], seed=6)
+    (p, F64, _), = G.batch_from_workloads(ws[:1], precision="fp64")
+    with pytest.raises(G.FRError):
+        G.Group([F64])
+    a = G.batch_from_workloads(ws[:1], precision="mixed")[0][1]
+    b = G.batch_from_workloads(ws[1:], precision="mixed")[0][1]
+    with pytest.raises(G.FRError):
+        G.Group([a, b])          # two fields of one order
