@@ -72,8 +72,9 @@ def parse():
                          "zalesak / rudman: slotted disks in solid-body rotation (100^2 / 200^2 quads); "
                          "c2s: Rider-Kothe on split-triangle meshes (--mesh-n, --order <= 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
-    ap.add_argument("--ensemble-launch", default="group", choices=["group", "streams"],
-                    help="c4: one launch per RK stage over all orders, or one field per order on its own stream")
+    ap.add_argument("--ensemble-launch", default="streams", choices=["group", "streams"],
+                    help="c4: one field per order on its own stream (faster, measured), or one launch per RK "
+                         "stage over all orders (fr_group_step)")
     ap.add_argument("--rk-steps", type=int, default=STEPS_PER_BENCH_STEP,
                     help="RK4 steps per benchmark step (profiling captures use fewer launches)")
     return ap.parse_args()

