@@ -22,6 +22,8 @@
 // system for psi alone (Eq. pseudotimesystem) with element viscosity nu_s
 // from the resolution indicator (Eqs. resolutionIndicator, nu_s).
 #pragma once
+#include <type_traits>
+
 #include "kcommon.cuh"
 
 namespace frp {
@@ -574,8 +576,13 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     const int64_t og = (e0 + el) * NF + k;
     const int64_t pg = FaceScatter<DIM>::v ? (int64_t)(A.fnbr[og] >> 1) : og;
     const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
-    int a, s, b0;
-    fline<DIM, N>(k, a, s, b0);
+    // the face's axis as a compile-time constant (the list is grouped by
+    // axis, one group per gradient pass), so that the line strides and the
+    // metric row are immediate offsets
+    auto lpoint = [&](auto AX) {
+    constexpr int a = decltype(AX)::value;
+    const int s = (k / NFP) & 1;
+    const int b0 = line_base<DIM, N>(a, k % NFP);
     T xi[3];
     fpt_xi<DIM, N>(k, O.x, xi);
     const T sg = s ? (T)1 : (T)-1;
@@ -609,7 +616,7 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     T nh[3];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) nh[c] = pn[c] * rpm;
-    const int st = ipow(N, a);
+    constexpr int st = ipow(N, a);
     if (MODE == 0) {
       T qf[2][3];
 #pragma unroll
@@ -684,6 +691,13 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       if (FaceScatter<DIM>::v && !wallp) fc[pslot + NF] = F;
       cor[el * NF + k] = F;
+    }
+    };
+    switch (k / (2 * NFP)) {
+      case 0: lpoint(std::integral_constant<int, 0>{}); break;
+      case 1: lpoint(std::integral_constant<int, 1>{}); break;
+      default:
+        if constexpr (DIM == 3) lpoint(std::integral_constant<int, DIM - 1>{});
     }
   }
   __syncthreads();
@@ -1000,7 +1014,9 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
       for (int sd = 0; sd < 2; ++sd) {
         const int k = (2 * a + sd) * NFP + ll;
         wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
-        if (stage != 0)
+        // with FaceScatter both values sit in the own slot; otherwise only
+        // the L ends' own fluxes do (the R ends gather below)
+        if (stage != 0 && FaceScatter<DIM>::v)
 #pragma unroll
           for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
       }
@@ -1028,15 +1044,17 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
     }
   }
   if (!FaceScatter<DIM>::v && stage != 0 && lact) {
+    // one load per line end: the own slot at L ends, the partner's at R ends
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int32_t w = wpre[a][sd];
-        const int64_t p = (int64_t)(w >> 1);
-        if (!(w & 1))
+        // flux-point indices fit 31 bits (E Nf < 2^30, checked at mesh creation)
+        const int32_t p = (w & 1) ? (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll) : (w >> 1);
+        const int64_t pe = p / NF, pk = p % NF;
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF];
+        for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[(pe * 2 + F0 + fsel + q * FS) * NF + pk];
       }
   }
   cp_async_wait_all();
