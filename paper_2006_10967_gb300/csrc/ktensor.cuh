@@ -418,10 +418,10 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int32_t w = wpre[a][sd];
-        const int64_t p = (int64_t)(w >> 1);
+        const int32_t p = w >> 1;  // < 2^30 (checked at mesh creation)
+        const int64_t pe = p / NF, pk = p % NF;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-          opre[a][sd][q] = (w & 1) ? tr[((p / NF) * 2 + F0 + fsel + q * FS) * NF + p % NF] : (T)0;
+        for (int q = 0; q < NQ; ++q) opre[a][sd][q] = (w & 1) ? tr[(pe * 2 + F0 + fsel + q * FS) * NF + pk] : (T)0;
       }
   }
   if (MODE == 1)
@@ -576,13 +576,8 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     const int64_t og = (e0 + el) * NF + k;
     const int64_t pg = FaceScatter<DIM>::v ? (int64_t)(A.fnbr[og] >> 1) : og;
     const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
-    // the face's axis as a compile-time constant (the list is grouped by
-    // axis, one group per gradient pass), so that the line strides and the
-    // metric row are immediate offsets
-    auto lpoint = [&](auto AX) {
-    constexpr int a = decltype(AX)::value;
-    const int s = (k / NFP) & 1;
-    const int b0 = line_base<DIM, N>(a, k % NFP);
+    int a, s, b0;
+    fline<DIM, N>(k, a, s, b0);
     T xi[3];
     fpt_xi<DIM, N>(k, O.x, xi);
     const T sg = s ? (T)1 : (T)-1;
@@ -616,7 +611,7 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     T nh[3];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) nh[c] = pn[c] * rpm;
-    constexpr int st = ipow(N, a);
+    const int st = ipow(N, a);
     if (MODE == 0) {
       T qf[2][3];
 #pragma unroll
@@ -691,13 +686,6 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
       fc[((e0 + el) * 2 + 1) * NF + k] = F;
       if (FaceScatter<DIM>::v && !wallp) fc[pslot + NF] = F;
       cor[el * NF + k] = F;
-    }
-    };
-    switch (k / (2 * NFP)) {
-      case 0: lpoint(std::integral_constant<int, 0>{}); break;
-      case 1: lpoint(std::integral_constant<int, 1>{}); break;
-      default:
-        if constexpr (DIM == 3) lpoint(std::integral_constant<int, DIM - 1>{});
     }
   }
   __syncthreads();

@@ -483,3 +483,52 @@ def test_autotuner_measures_every_variant(G):
     ent = table[tune.key(1, w.order, "mixed")]
     assert set(ent["us_per_stage"]) == {"0", "1"}
     assert str(ent["variant"]) == min(ent["us_per_stage"], key=lambda k: ent["us_per_stage"][k])
+
+
+# ---------------------------------------------------------------------------
+# Full-size headline workload (64^3 hexes, p = 3, LeVeque field) in the
+# benchmark's launch configuration, checked on sampled elements: the residual
+# of an element depends on its neighbours and their neighbours, so the oracle
+# evaluated on a 6^3 block cut from the same mesh (same nodes, same state)
+# gives the exact residual of the block's central 2^3 elements.
+
+def _hex_block(mesh, n, lo):
+    """The 6^3 sub-block of an n^3 hex_grid mesh starting at element index lo
+    (i, j, k), as a mesh of its own, and the global ids of its elements."""
+    i, j, k = np.meshgrid(*[np.arange(l, l + 6) for l in lo], indexing="ij")
+    ids = (i + n * (j + n * k)).ravel(order="F")
+    conn = mesh.conn[ids]
+    used, inv = np.unique(conn, return_inverse=True)
+    sub = S.meshes.Mesh("hex", mesh.nodes[used], inv.reshape(conn.shape).astype(np.int64),
+                        (False, False, False), (1.0, 1.0, 1.0), "block")
+    ci, cj, ck = np.meshgrid(*[np.arange(l + 2, l + 4) for l in lo], indexing="ij")
+    centre = (ci + n * (cj + n * ck)).ravel(order="F")
+    local = np.array([int(np.nonzero(ids == g)[0][0]) for g in centre])
+    return sub, centre, local
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
+def test_full_size_c3_sampled_parity(G, precision, tol):
+    w = S.workload("c3")
+    n = 64
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    F = G.Field(M, G.make_params(w, precision), ic=w.circle, precondition=False)
+    t = 0.7
+    R = F.rhs(t).cpu().numpy()
+    scale = np.abs(R).max(axis=(1, 2))
+    for lo in ((0, 0, 0), (20, 17, 18), (58, 29, 40), (23, 58, 0)):   # corners, edges and the interior
+        sub, centre, local = _hex_block(mesh, n, lo)
+        sol = Solver(sub, w.order, Params.from_workload(w), w.velocity)
+        sol.initialize(w.circle, precondition=False)
+        Ro = sol.rhs(sol.phi, sol.psi, t)
+        for f in (0, 1):
+            d = np.abs(R[f][centre] - Ro[f].numpy()[local]).max() / scale[f]
+            assert d < tol, (lo, f, d)
+    # mass conservation of the full field over a few steps with no-flux walls
+    wn = w.with_(wall="noflux")
+    Fn = G.Field(M, G.make_params(wn, precision), ic=wn.circle, precondition=True)
+    m0 = Fn.mass(0)
+    Fn.step(8)
+    assert Fn.sync() == 0
+    assert abs(Fn.mass(0) - m0) < 1e-12 * abs(m0)
