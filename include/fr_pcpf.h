@@ -153,11 +153,12 @@ typedef struct fr_params {
                             FR_EINVAL */
   int32_t variant;       /* implementation of the residual and update kernels, all giving the
                             same result to round-off: 0 the default; fr_kernel_variants gives
-                            the count for a mesh and precision (triangles, FR_MIXED: 0 scalar
+                            the count for a mesh and precision (FR_MIXED: triangles 0 scalar
                             dot products, 1 the operator applies on tensor cores, mma.sync
-                            m16n8k8 in three-term TF32 with FP32 accumulation).  An autotuner
-                            picks among them by measurement.  Out of range: FR_EUNSUPPORTED
-                            from fr_field_init, negative: FR_EINVAL */
+                            m16n8k8 in three-term TF32 with FP32 accumulation; quads and hexes
+                            0 the default element tiles of the physical-step kernels, 1 half
+                            tiles).  An autotuner picks among them by measurement.  Out of
+                            range: FR_EUNSUPPORTED from fr_field_init, negative: FR_EINVAL */
 } fr_params;
 
 enum { FR_NORMAL_PSI = 0, FR_NORMAL_PHI = 1 };

@@ -148,13 +148,17 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
 }
 
 bool get_kernels(const fr_mesh& m, int precision, int variant, KernelSet* ks) {
-  if (m.etype == FR_QUAD) return variant == 0 && kernels_quad(m.order, precision, m.E, ks);
-  if (m.etype == FR_HEX) return variant == 0 && kernels_hex(m.order, precision, m.E, ks);
+  if (m.etype == FR_QUAD) return kernels_quad(m.order, precision, m.E, variant, ks);
+  if (m.etype == FR_HEX) return kernels_hex(m.order, precision, m.E, variant, ks);
   return kernels_tri(m.order, precision, m.E, variant, ks);
 }
 
+// FR_MIXED: two variants per element type (triangles: scalar / tensor-core
+// operator applies; quads and hexes: the default / half tiles of the
+// physical-step kernels); FR_FP64: one
 int variant_count(const fr_mesh& m, int precision) {
-  return m.etype == FR_TRI && precision == FR_MIXED ? 2 : 1;
+  (void)m;
+  return precision == FR_MIXED ? 2 : 1;
 }
 
 int check_params(const fr_params* p) {

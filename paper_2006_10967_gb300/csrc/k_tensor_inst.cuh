@@ -5,16 +5,16 @@
 
 namespace frp {
 
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 void launch_kb_tensor(const KArgs& A, cudaStream_t s) {
-  using LY = KBLayout<DIM, N, T, MODE>;
-  launch_kernel(kb_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
+  using LY = KBLayout<DIM, N, T, MODE, TD>;
+  launch_kernel(kb_tensor<DIM, N, T, MODE, TD>, LY::SMEM, LY::ET, A, s, LY::THREADS);
 }
 
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
-  using LY = KALayout<DIM, N, T, MODE>;
-  launch_kernel(ka_tensor<DIM, N, T, MODE>, LY::SMEM, LY::ET, A, s, LY::THREADS);
+  using LY = KALayout<DIM, N, T, MODE, TD>;
+  launch_kernel(ka_tensor<DIM, N, T, MODE, TD>, LY::SMEM, LY::ET, A, s, LY::THREADS);
 }
 
 template <int DIM, int N, typename T>
@@ -30,25 +30,27 @@ void launch_vcache(const KArgs& A, cudaStream_t s) {
 
 // Shared-memory opt-in of one (kb, ka) pair; done when the kernel table is
 // filled, so that no launch (and no graph capture) has to do it.
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 bool prepare_tensor() {
-  return cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)KBLayout<DIM, N, T, MODE>::SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)KALayout<DIM, N, T, MODE>::SMEM) == cudaSuccess;
+  return cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KBLayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KALayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess;
 }
 
-template <int DIM, int N, typename T>
+// TD: the physical-step kernels' tile divisor (the kernel variant; the
+// preconditioning kernels keep the default tile)
+template <int DIM, int N, typename T, int TD = 1>
 void fill_tensor(int64_t E, KernelSet* ks) {
-  ks->prepared = prepare_tensor<DIM, N, T, 0>() && prepare_tensor<DIM, N, T, 1>();
+  ks->prepared = prepare_tensor<DIM, N, T, 0, TD>() && prepare_tensor<DIM, N, T, 1>();
   ks->vcache = launch_vcache<DIM, N, T>;
   ks->mconst = launch_mconst<DIM, N, T>;
-  ks->kb[0] = launch_kb_tensor<DIM, N, T, 0>;
+  ks->kb[0] = launch_kb_tensor<DIM, N, T, 0, TD>;
   ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;
-  ks->ka[0] = launch_ka_tensor<DIM, N, T, 0>;
+  ks->ka[0] = launch_ka_tensor<DIM, N, T, 0, TD>;
   ks->ka[1] = launch_ka_tensor<DIM, N, T, 1>;
-  const int et_min = KBLayout<DIM, N, T, 0>::ET < KALayout<DIM, N, T, 0>::ET ? KBLayout<DIM, N, T, 0>::ET
-                                                                              : KALayout<DIM, N, T, 0>::ET;
+  const int et_min = KBLayout<DIM, N, T, 0, TD>::ET < KALayout<DIM, N, T, 0, TD>::ET ? KBLayout<DIM, N, T, 0, TD>::ET
+                                                                                      : KALayout<DIM, N, T, 0, TD>::ET;
   const int et_min1 = KBLayout<DIM, N, T, 1>::ET < KALayout<DIM, N, T, 1>::ET ? KBLayout<DIM, N, T, 1>::ET
                                                                                : KALayout<DIM, N, T, 1>::ET;
   const int et = et_min < et_min1 ? et_min : et_min1;

@@ -18,8 +18,8 @@ struct KernelSet {
 };
 
 // Return false if the (order, precision) pair is not built.
-bool kernels_quad(int order, int precision, int64_t E, KernelSet* ks);
-bool kernels_hex(int order, int precision, int64_t E, KernelSet* ks);
+bool kernels_quad(int order, int precision, int64_t E, int variant, KernelSet* ks);
+bool kernels_hex(int order, int precision, int64_t E, int variant, KernelSet* ks);
 bool kernels_tri(int order, int precision, int64_t E, int variant, KernelSet* ks);
 
 template <typename K>

@@ -287,7 +287,10 @@ __host__ __device__ constexpr int occupancy_tile(int bytes_el, int per_block, in
   return best;
 }
 
-template <int DIM, int N, typename T, int MODE>
+// TD: tile divisor of a kernel variant (1: the default tile below; 2: half
+// of it, rounded to whole warps where possible), chosen per element type,
+// order and precision by the autotuner.
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 struct KBLayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
@@ -308,8 +311,9 @@ struct KBLayout {
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 57344 / BYTES_EL < 1 ? 1 : 57344 / BYTES_EL;
   static constexpr bool OCC = MODE == 0 && DIM == 3;  // tile chosen for resident warps
-  static constexpr int ET = OCC ? occupancy_tile(BYTES_EL, 16 * 13 + 2 * (int)sizeof(T) + 64, LN, ET_T)
-                                : warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr int ET0 = OCC ? occupancy_tile(BYTES_EL, 16 * 13 + 2 * (int)sizeof(T) + 64, LN, ET_T)
+                                 : warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr int ET = TD == 1 ? ET0 : (ET0 / TD < 1 ? 1 : warp_tile(ET0 / TD, LN));
   static constexpr int FS = FRP_FIELD_SPLIT ? NFLD : 1;  // fields split across threads
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
@@ -323,10 +327,10 @@ struct KBLayout {
 // kb_tensor: Steps 1-6 on a tile of ET elements.  Line passes give each
 // thread one solution-point line; the 1D operators are read from the kernel
 // parameters (constant bank) with compile-time indices.
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
   using S = TS<DIM, N>;
-  using LY = KBLayout<DIM, N, T, MODE>;
+  using LY = KBLayout<DIM, N, T, MODE, TD>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
   constexpr int FS = LY::FS, NQ = NFLD / FS;  // fields per thread in the line passes
   constexpr int F0 = MODE == 0 ? 0 : 1;
@@ -910,14 +914,14 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
 
 // kb_tensor: one block per tile of ET elements (the body above with the
 // block's index; a group launch calls the same body, see k_group.cu)
-template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE>::THREADS, KBLayout<DIM, N, T, MODE>::MINB)
+template <int DIM, int N, typename T, int MODE, int TD = 1>
+__global__ void __launch_bounds__(KBLayout<DIM, N, T, MODE, TD>::THREADS, KBLayout<DIM, N, T, MODE, TD>::MINB)
     kb_tensor(const KArgs A) {
-  kb_tensor_body<DIM, N, T, MODE>(A, blockIdx.x);
+  kb_tensor_body<DIM, N, T, MODE, TD>(A, blockIdx.x);
 }
 
 // ============================================================================
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 struct KALayout {
   using S = TS<DIM, N>;
   static constexpr int NFLD = MODE == 0 ? 2 : 1;
@@ -932,7 +936,8 @@ struct KALayout {
                                   (PRE ? 2 * S::NU * 8 + 2 * S::NU * 4 + S::NU * 8 + 2 * S::NF * 4 + 16 : 0);
   static constexpr int ET_T = 256 / LN < 1 ? 1 : 256 / LN;
   static constexpr int ET_S = 45056 / BYTES_EL < 1 ? 1 : 45056 / BYTES_EL;
-  static constexpr int ET = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr int ET0 = warp_tile(ET_T < ET_S ? ET_T : ET_S, LN);
+  static constexpr int ET = TD == 1 ? ET0 : (ET0 / TD < 1 ? 1 : warp_tile(ET0 / TD, LN));
   static constexpr int FS = FRP_FIELD_SPLIT ? NFLD : 1;  // fields split across threads
   static constexpr int LINES = ET * LN;
   static constexpr int THREADS = (LINES * FS + 31) / 32 * 32;  // whole warps; idle lanes inactive
@@ -946,10 +951,10 @@ struct KALayout {
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
 // as in kb_tensor, the last of which also applies the update to its line.  stage -1 writes du/dt to A.out (fp64) and leaves the
 // state alone; stage 0 only recomputes the traces of ustg.
-template <int DIM, int N, typename T, int MODE>
+template <int DIM, int N, typename T, int MODE, int TD = 1>
 __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   using S = TS<DIM, N>;
-  using LY = KALayout<DIM, N, T, MODE>;
+  using LY = KALayout<DIM, N, T, MODE, TD>;
   constexpr int NU = S::NU, NF = S::NF, NG = S::NG, NFP = S::NFP, NFLD = LY::NFLD, ET = LY::ET, LN = LY::LN;
   constexpr int FS = LY::FS, NQ = NFLD / FS;
   constexpr int F0 = MODE == 0 ? 0 : 1;
@@ -1231,9 +1236,13 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
             if (!(w & 1) || pg == og) tr[((pg / NF) * 2 + F0 + fld) * NF + pg % NF] = sd ? t1 : t0;
           }
         } else {
+          // owner slots: only the traces a partner's kb gathers, at R ends
+          // (the partner is L there) and at walls (the own partner)
           T* trl = tr + ((e0 + lel) * 2 + F0 + fld) * NF;
-          trl[k0] = t0;
-          trl[k1] = t1;
+          const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
+          const int32_t g0 = (int32_t)((e0 + lel) * NF + k0), g1 = (int32_t)((e0 + lel) * NF + k1);
+          if (!(w0 & 1) || (w0 >> 1) == g0) trl[k0] = t0;
+          if (!(w1 & 1) || (w1 >> 1) == g1) trl[k1] = t1;
         }
       }
     }
@@ -1245,10 +1254,10 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
 }
 
-template <int DIM, int N, typename T, int MODE>
-__global__ void __launch_bounds__(KALayout<DIM, N, T, MODE>::THREADS, KALayout<DIM, N, T, MODE>::MINB)
+template <int DIM, int N, typename T, int MODE, int TD = 1>
+__global__ void __launch_bounds__(KALayout<DIM, N, T, MODE, TD>::THREADS, KALayout<DIM, N, T, MODE, TD>::MINB)
     ka_tensor(const KArgs A) {
-  ka_tensor_body<DIM, N, T, MODE>(A, blockIdx.x);
+  ka_tensor_body<DIM, N, T, MODE, TD>(A, blockIdx.x);
 }
 
 // Spatial velocity factor v(x) (g = 1) at the solution and flux points of

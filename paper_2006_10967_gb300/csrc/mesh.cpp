@@ -108,6 +108,18 @@ void geo_coeffs(const double* X /*nv x dim*/, int dim, double* c /*dim x NC*/) {
     for (int d = 0; d < dim; ++d)
       for (int k = 0; k < NC; ++k) c[d * NC + k] += B[k] * X[v * dim + d] / nv;
   }
+  // Round-off of the sums above leaves ~1e-17 h in coefficients that are
+  // zero for the element's shape (the cross terms of a parallelogram or
+  // parallelepiped, the off-diagonal terms of an axis-aligned box) when the
+  // node coordinates are not dyadic; set coefficients below 1e-13 of the
+  // element's largest linear coefficient to zero, so that such elements are
+  // recognised as affine (one metric per element) and axis-aligned.
+  double scale = 0.0;
+  for (int d = 0; d < dim; ++d)
+    for (int k = 1; k <= dim; ++k) scale = std::max(scale, std::fabs(c[d * NC + k]));
+  for (int d = 0; d < dim; ++d)
+    for (int k = 1; k < NC; ++k)
+      if (std::fabs(c[d * NC + k]) < 1e-13 * scale) c[d * NC + k] = 0.0;
 }
 
 void point_and_jac(const fr_mesh& m, int64_t e, const double* xi, double* x, double J[3][3]) {

@@ -74,12 +74,24 @@ def tune(workloads, precision="mixed", write=True, **kw):
     return table
 
 
+def _ensemble_probe(S, p, n=96, seed=3):
+    """A periodic n^2 quad instance of order p with a random-phase stream
+    velocity, the shape of the ensemble's instances."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    vel = S.workloads.random_phase_stream(rng)
+    h = 1.0 / n
+    w = S.Workload(f"ensemble_probe_quad{n}_p{p}", (lambda n=n: S.quad_grid(n)), p, vel,
+                   S.Circle((0.5, 0.5), 0.15, 3 * p / (4 * h)), t_end=4.0, h=h, precision="mixed")
+    return S.workloads._finish(w, 2)
+
+
 if __name__ == "__main__":
     import sys
     sys.path.insert(0, os.path.dirname(HERE))
     import synthetic as S
-    names = sys.argv[1:] or ["c2t", "c2s"]
+    names = sys.argv[1:] or ["c3", "c2q", "c2t", "ens2", "ens3", "ens4", "ens5"]
     ws = []
     for n in names:
-        ws.append(S.workload(n))
+        ws.append(_ensemble_probe(S, int(n[3:])) if n.startswith("ens") else S.workload(n))
     print(json.dumps(tune(ws), indent=1))
