@@ -156,9 +156,10 @@ typedef struct fr_params {
                             the count for a mesh and precision (FR_MIXED: triangles 0 scalar
                             dot products, 1 the operator applies on tensor cores, mma.sync
                             m16n8k8 in three-term TF32 with FP32 accumulation; quads and hexes
-                            0 the default element tiles of the physical-step kernels, 1 half
-                            tiles).  An autotuner picks among them by measurement.  Out of
-                            range: FR_EUNSUPPORTED from fr_field_init, negative: FR_EINVAL */
+                            the element tiles of the physical-step residual and update kernels:
+                            0 default/default, 1 half/half, 2 default/half, 3 half/default).
+                            An autotuner picks among them by measurement.  Out of range:
+                            FR_EUNSUPPORTED from fr_field_init, negative: FR_EINVAL */
 } fr_params;
 
 enum { FR_NORMAL_PSI = 0, FR_NORMAL_PHI = 1 };

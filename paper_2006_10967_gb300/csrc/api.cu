@@ -153,12 +153,12 @@ bool get_kernels(const fr_mesh& m, int precision, int variant, KernelSet* ks) {
   return kernels_tri(m.order, precision, m.E, variant, ks);
 }
 
-// FR_MIXED: two variants per element type (triangles: scalar / tensor-core
-// operator applies; quads and hexes: the default / half tiles of the
-// physical-step kernels); FR_FP64: one
+// FR_MIXED: triangles 2 (scalar / tensor-core operator applies), quads and
+// hexes 4 (default or half tiles of the physical-step residual and update
+// kernels); FR_FP64: 1
 int variant_count(const fr_mesh& m, int precision) {
-  (void)m;
-  return precision == FR_MIXED ? 2 : 1;
+  if (precision != FR_MIXED) return 1;
+  return m.etype == FR_TRI ? 2 : 4;
 }
 
 int check_params(const fr_params* p) {

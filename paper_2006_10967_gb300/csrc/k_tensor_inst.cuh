@@ -38,19 +38,21 @@ bool prepare_tensor() {
                               (int)KALayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess;
 }
 
-// TD: the physical-step kernels' tile divisor (the kernel variant; the
-// preconditioning kernels keep the default tile)
-template <int DIM, int N, typename T, int TD = 1>
+// TB, TA: the tile divisors of the physical-step residual and update
+// kernels (the kernel variant; the preconditioning kernels keep the default
+// tiles)
+template <int DIM, int N, typename T, int TB = 1, int TA = 1>
 void fill_tensor(int64_t E, KernelSet* ks) {
-  ks->prepared = prepare_tensor<DIM, N, T, 0, TD>() && prepare_tensor<DIM, N, T, 1>();
+  ks->prepared = prepare_tensor<DIM, N, T, 0, TB>() && prepare_tensor<DIM, N, T, 0, TA>() &&
+                 prepare_tensor<DIM, N, T, 1>();
   ks->vcache = launch_vcache<DIM, N, T>;
   ks->mconst = launch_mconst<DIM, N, T>;
-  ks->kb[0] = launch_kb_tensor<DIM, N, T, 0, TD>;
+  ks->kb[0] = launch_kb_tensor<DIM, N, T, 0, TB>;
   ks->kb[1] = launch_kb_tensor<DIM, N, T, 1>;
-  ks->ka[0] = launch_ka_tensor<DIM, N, T, 0, TD>;
+  ks->ka[0] = launch_ka_tensor<DIM, N, T, 0, TA>;
   ks->ka[1] = launch_ka_tensor<DIM, N, T, 1>;
-  const int et_min = KBLayout<DIM, N, T, 0, TD>::ET < KALayout<DIM, N, T, 0, TD>::ET ? KBLayout<DIM, N, T, 0, TD>::ET
-                                                                                      : KALayout<DIM, N, T, 0, TD>::ET;
+  const int et_min = KBLayout<DIM, N, T, 0, TB>::ET < KALayout<DIM, N, T, 0, TA>::ET ? KBLayout<DIM, N, T, 0, TB>::ET
+                                                                                      : KALayout<DIM, N, T, 0, TA>::ET;
   const int et_min1 = KBLayout<DIM, N, T, 1>::ET < KALayout<DIM, N, T, 1>::ET ? KBLayout<DIM, N, T, 1>::ET
                                                                                : KALayout<DIM, N, T, 1>::ET;
   const int et = et_min < et_min1 ? et_min : et_min1;

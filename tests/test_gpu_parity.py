@@ -473,7 +473,25 @@ def test_variant_counts_and_rejection(G):
         G.Field(M, G.make_params(w, "fp64", variant=1), ic=w.circle)
     wq = CASES["quad_periodic_jitter_p3"]()
     Mq = G.Mesh.from_synthetic(wq.mesh(), wq.order)
-    assert G.kernel_variants(Mq, "mixed") == 1
+    assert G.kernel_variants(Mq, "mixed") == 4 and G.kernel_variants(Mq, "fp64") == 1
+
+
+@pytest.mark.parametrize("case", ["quad_periodic_jitter_p3", "quad_walls_jitter_p4", "hex_periodic_jitter_p3",
+                                  "hex_rotated_walls_p3"])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_tile_variants_march_with_the_oracle(G, case, variant):
+    """The tile variants of the quad/hex physical-step kernels (half tiles
+    for the residual and/or the update kernel) march with the oracle like the
+    default tiles, and with the same bits as them."""
+    w = CASES[case]()
+    sol, F = _pair(G, w, precision="mixed", variant=variant)
+    _, F0 = _pair(G, w, precision="mixed", variant=0)
+    F.step(6)
+    F0.step(6)
+    sol.step(6)
+    assert F.sync() == 0
+    assert _rel(F.get(0), sol.phi.numpy()) < 1e-5
+    assert np.array_equal(F.get(0), F0.get(0)) and np.array_equal(F.get(1), F0.get(1))
 
 
 def test_autotuner_measures_every_variant(G):
