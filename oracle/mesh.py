@@ -82,7 +82,10 @@ def build_geometry(mesh, p):
         keys = np.round(cen / quantum).astype(np.int64)
         for a in range(d):
             if per[a] > 0:
-                keys[:, a] = np.mod(keys[:, a], int(round(per[a] / quantum)))
+                # on a periodic axis the quantum is rounded to divide the
+                # period, so a centroid and its periodic image share a key
+                K = int(round(per[a] / quantum))
+                keys[:, a] = np.mod(np.round(cen[:, a] * (K / per[a])).astype(np.int64), K)
         for e in range(E):
             table.setdefault(tuple(keys[e]), []).append((e, f))
     pe = np.tile(np.arange(E)[:, None], (1, el.nf))

@@ -221,10 +221,16 @@ int build(const fr_mesh_desc* d, fr_mesh& m) {
   m.h = et == FR_TRI ? std::sqrt(2.0 * vol / m.E) : std::pow(vol / m.E, 1.0 / dim);
 
   // ---- faces: sorted, wrapped, quantised vertex coordinates
+  // on a periodic axis the quantum is rounded to divide the period (inv[a]
+  // = P[a] / period), so a vertex and its periodic image share a key
   const double quantum = 1e-7 * m.h;
   int64_t P[3] = {0, 0, 0};
+  double inv[3] = {1.0 / quantum, 1.0 / quantum, 1.0 / quantum};
   for (int a = 0; a < dim; ++a)
-    if (d->periodic[a]) P[a] = std::llround(d->period[a] / quantum);
+    if (d->periodic[a]) {
+      P[a] = std::llround(d->period[a] / quantum);
+      inv[a] = (double)P[a] / d->period[a];
+    }
   std::vector<FaceKey> keys;
   keys.reserve(m.E * m.nfaces);
   std::vector<int> fv;
@@ -235,7 +241,7 @@ int build(const fr_mesh_desc* d, fr_mesh& m) {
       for (size_t q = 0; q < fv.size(); ++q) {
         const double* x = &d->nodes[d->conn[e * m.nverts + fv[q]] * dim];
         for (int a = 0; a < 3; ++a) {
-          int64_t v = a < dim ? std::llround(x[a] / quantum) : 0;
+          int64_t v = a < dim ? std::llround(x[a] * inv[a]) : 0;
           if (a < dim && P[a] > 0) v = ((v % P[a]) + P[a]) % P[a];
           vk[q][a] = v;
         }
@@ -250,7 +256,7 @@ int build(const fr_mesh_desc* d, fr_mesh& m) {
       for (int a = 0; a < dim; ++a) {
         double c = 0.0;
         for (size_t q = 0; q < fv.size(); ++q) c += d->nodes[d->conn[e * m.nverts + fv[q]] * dim + a];
-        int64_t v = std::llround(c / fv.size() / quantum);
+        int64_t v = std::llround(c / fv.size() * inv[a]);
         if (P[a] > 0) v = ((v % P[a]) + P[a]) % P[a];
         fk.k[12 + a] = v;
       }

@@ -1,0 +1,159 @@
+"""Element partitioning with two-layer ghost halos (paper_2006_10967_gb300.partition)
+on gloo ranks (CPU): each rank evaluates the FR residual on its local mesh
+(owned elements and ghosts) with the ghosts' states received from their
+owners, and marches RK4 with a ghost exchange before every stage; the owned
+elements' residuals and states equal the single-domain ones.  The residual
+here is the oracle's (CPU), which stands in for the per-rank kernels."""
+import json
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _case(name):
+    import synthetic as S
+    if name == "quad":
+        mesh = S.quad_grid(6, jitter=0.1, seed=3, shuffle_seed=4, rotate_seed=5)
+        return mesh, 2, S.Velocity("rider_kothe", T=8.0), S.Circle((0.45, 0.55), 0.25, 6.0)
+    if name == "hexp":
+        mesh = S.hex_grid(5, periodic=(True, False, True), jitter=0.1, seed=8, rotate_seed=2, shuffle_seed=6)
+    else:
+        mesh = S.hex_grid(4, jitter=0.1, seed=2, rotate_seed=7)
+    return mesh, 2, S.Velocity("leveque", T=3.0), S.Circle((0.45, 0.5, 0.4), 0.3, 6.0)
+
+
+def _rank_main(rank, world, port, out_dir, name):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import Params, Solver
+    from paper_2006_10967_gb300 import partition as PT
+    mesh, p, vel, circ = _case(name)
+    prm = Params(gamma=0.09, eps=0.01, tau=0.1, dt=2e-3)
+    full = Solver(mesh, p, prm, vel)
+    full.initialize(circ, precondition=False)
+    full.psi = full.psi + 0.05 * torch.sin(5.0 * full.xu[..., 0])
+    Rf = full.rhs(full.phi, full.psi, 0.3)
+    part = PT.partition(mesh, world)
+    plan = PT.plans(mesh, part)[rank]
+    loc = Solver(plan.mesh, p, prm, vel)
+    no = plan.n_owned
+    ol = torch.as_tensor(plan.owned_local)
+    gl = torch.as_tensor(np.searchsorted(plan.local, plan.ghosts))
+    phi = torch.zeros_like(loc.xu[..., 0])
+    psi = torch.zeros_like(phi)
+    phi[ol] = full.phi[plan.owned]           # owners know their own elements only
+    psi[ol] = full.psi[plan.owned]
+    PT.exchange(phi, plan)
+    PT.exchange(psi, plan)
+    ghosts_ok = bool(torch.equal(phi[gl], full.phi[plan.ghosts]) and torch.equal(psi[gl], full.psi[plan.ghosts]))
+    R = loc.rhs(phi, psi, 0.3)
+    res_err = max(float((R[f][ol] - Rf[f][plan.owned]).abs().max() / Rf[f].abs().max()) for f in (0, 1))
+    # RK4 with a ghost exchange before every stage, against the single domain
+    dt = prm.dt
+    u = torch.stack([phi, psi], 0)
+
+    def rate(U, t):
+        U = U.clone()
+        PT.exchange(U[0], plan)
+        PT.exchange(U[1], plan)
+        a, b = loc.rhs(U[0], U[1], t)
+        return torch.stack([a, b], 0)
+    t = 0.0
+    for _ in range(3):
+        k1 = rate(u, t)
+        k2 = rate(u + 0.5 * dt * k1, t + 0.5 * dt)
+        k3 = rate(u + 0.5 * dt * k2, t + 0.5 * dt)
+        k4 = rate(u + dt * k3, t + dt)
+        u = u + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        t += dt
+    full.prm.dt = dt
+    for _ in range(3):
+        full.rk4_step()
+    step_err = max(float((u[f][ol] - s[plan.owned]).abs().max() / s.abs().max())
+                   for f, s in ((0, full.phi), (1, full.psi)))
+    with open(os.path.join(out_dir, f"{name}{rank}.json"), "w") as f:
+        json.dump({"rank": rank, "owned": int(no), "ghosts": int(len(plan.ghosts)), "ghosts_ok": ghosts_ok,
+                   "res_err": res_err, "step_err": step_err, "peers": sorted(plan.recv)}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,world", [("quad", 2), ("quad", 3), ("hex", 2), ("hexp", 3)])
+def test_partitioned_residual_and_march_equal_single_domain(tmp_path, name, world):
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path), name), nprocs=world,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"{name}{r}.json")) for r in range(world)]
+    import synthetic  # noqa: F401
+    sys.path.insert(0, ROOT)
+    mesh = _case(name)[0]
+    assert sum(r["owned"] for r in res) == mesh.n_elems
+    for r in res:
+        assert r["ghosts_ok"] and r["ghosts"] > 0 and r["peers"]
+        assert r["res_err"] < 1e-13, r
+        assert r["step_err"] < 1e-13, r
+
+
+def test_partition_is_balanced_and_plans_are_consistent():
+    sys.path.insert(0, ROOT)
+    import synthetic as S
+    from paper_2006_10967_gb300 import partition as PT
+    mesh = S.hex_grid(6, periodic=(True, False, True), rotate_seed=3, shuffle_seed=2)
+    part = PT.partition(mesh, 4)
+    counts = np.bincount(part, minlength=4)
+    assert counts.min() >= mesh.n_elems // 4 - 1 and counts.max() <= mesh.n_elems // 4 + 1
+    P = PT.plans(mesh, part)
+    for p in P:
+        for q, idx in p.send.items():
+            # what p sends to q is, element for element, what q receives from p
+            sent = p.local[idx]
+            got = P[q].local[P[q].recv[p.rank]]
+            assert np.array_equal(sent, got)
+            assert np.all(part[sent] == p.rank)
+
+
+@pytest.mark.parametrize("name,world", [("quad", 3), ("hex", 3), ("hexp", 4)])
+def test_local_meshes_pair_faces_across_the_period(name, world):
+    """A rank's local mesh covers part of a periodic domain, so its cell size
+    no longer divides the period; faces that meet through the periodic
+    boundary still pair (in the oracle's geometry and in the library's mesh
+    builder), and the only boundary flux points are those whose neighbour in
+    the whole mesh is not on the rank."""
+    sys.path.insert(0, ROOT)
+    from libutil import ensure_built
+    from oracle.mesh import build_geometry
+    from paper_2006_10967_gb300 import partition as PT
+    ensure_built()
+    import paper_2006_10967_gb300 as G
+    mesh, p = _case(name)[:2]
+    gfull = build_geometry(mesh, p)
+    pe_full = gfull.pe
+    partial = 0
+    for plan in PT.plans(mesh, PT.partition(mesh, world)):
+        here = np.zeros(mesh.n_elems, dtype=bool)
+        here[plan.local] = True
+        cut = ~here[pe_full[plan.local]]
+        partial += int(cut.sum()) > 0
+        expected = int((cut | gfull.boundary[plan.local]).sum())
+        geo = build_geometry(plan.mesh, p)
+        assert int(geo.boundary.sum()) == expected
+        # partners map back to the whole mesh's partners
+        inner = ~geo.boundary
+        assert np.array_equal(plan.local[geo.pe][inner], pe_full[plan.local][inner])
+        M = G.Mesh.from_synthetic(plan.mesh, p)
+        assert M.info.n_boundary_fpts == expected
+    assert partial > 0
