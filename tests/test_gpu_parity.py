@@ -482,16 +482,22 @@ def test_variant_counts_and_rejection(G):
 def test_tile_variants_march_with_the_oracle(G, case, variant):
     """The tile variants of the quad/hex physical-step kernels (half tiles
     for the residual and/or the update kernel) march with the oracle like the
-    default tiles, and with the same bits as them."""
+    default tiles.  A variant is deterministic (two runs give the same bits);
+    against the default tiles it agrees to float round-off only: a different
+    tile is different compiled code, whose float operation order (for
+    instance which products fuse into an FMA) need not be the same."""
     w = CASES[case]()
     sol, F = _pair(G, w, precision="mixed", variant=variant)
+    _, F1 = _pair(G, w, precision="mixed", variant=variant)
     _, F0 = _pair(G, w, precision="mixed", variant=0)
-    F.step(6)
-    F0.step(6)
+    for f in (F, F1, F0):
+        f.step(6)
     sol.step(6)
     assert F.sync() == 0
     assert _rel(F.get(0), sol.phi.numpy()) < 1e-5
-    assert np.array_equal(F.get(0), F0.get(0)) and np.array_equal(F.get(1), F0.get(1))
+    assert np.array_equal(F.get(0), F1.get(0)) and np.array_equal(F.get(1), F1.get(1))
+    for fld in (0, 1):
+        assert _rel(F.get(fld), F0.get(fld)) < 1e-6
 
 
 def test_autotuner_measures_every_variant(G):
