@@ -57,6 +57,10 @@ extern "C" {
 #define FR_ENONFINITE (-4)  /* a non-finite value appeared in the state */
 #define FR_ETIMEOUT (-5)    /* a bounded device wait gave up */
 #define FR_EUNSUPPORTED (-6) /* element type / order / mode not built */
+#define FR_EBOUNDS (-7)     /* a partner index read from the connectivity was out of
+                               range (reported only by the bounds-checked build,
+                               libfrpcpf_checked.so, whose kernels check every such
+                               index before use and skip the access) */
 
 /* ---- element types, precisions, velocity and IC kinds ---------------- */
 #define FR_QUAD 0

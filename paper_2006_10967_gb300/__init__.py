@@ -335,6 +335,8 @@ class Field:
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:
+            if capi.CHECKED and lib().fr_sync(h, None) == capi.FR_EBOUNDS:
+                capi.BOUNDS_FIRED.append(h.value)   # a fired index check is never lost
             lib().fr_field_destroy(h)
             self.handle = None
 

@@ -8,9 +8,15 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfrpcpf.so")
+# FRP_BOUNDS_CHECK=1 selects the bounds-checked build of the same sources
+CHECKED = os.environ.get("FRP_BOUNDS_CHECK", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libfrpcpf_checked.so" if CHECKED else "libfrpcpf.so")
+# fields whose status, read when they were destroyed, showed a fired index
+# check (the checked build only)
+BOUNDS_FIRED = []
 
 FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ENONFINITE, FR_ETIMEOUT, FR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+FR_EBOUNDS = -7
 FR_QUAD, FR_TRI, FR_HEX = 0, 1, 2
 FR_FP64, FR_MIXED = 0, 1
 FR_VEL_UNIFORM, FR_VEL_RIDER_KOTHE, FR_VEL_LEVEQUE, FR_VEL_STREAM, FR_VEL_ROTATION = 0, 1, 2, 3, 4
@@ -113,7 +119,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2006_10967_gb300.build.build()")
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2006_10967_gb300.build.build"
+                               f"(checked={CHECKED})")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             fn = getattr(L, name)

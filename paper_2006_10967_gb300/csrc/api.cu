@@ -1008,6 +1008,7 @@ extern "C" const char* fr_strerror(int code) {
     case FR_ENONFINITE: return "non-finite value in the state";
     case FR_ETIMEOUT: return "bounded device wait timed out";
     case FR_EUNSUPPORTED: return "element type, order or mode not supported";
+    case FR_EBOUNDS: return "partner index out of range (bounds-checked build)";
     default: return "unknown error";
   }
 }

@@ -228,8 +228,10 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
         }
         // partner traces: in the own slots with FaceScatter (see ka_tensor),
         // else in the partner's
-        const int64_t g0 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k0 : (int64_t)(w0 >> 1);
-        const int64_t g1 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k1 : (int64_t)(w1 >> 1);
+        const int64_t g0 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k0
+                                                : (int64_t)partner<NF>(A, w0, (int32_t)((e0 + lel) * NF + k0));
+        const int64_t g1 = FaceScatter<DIM>::v ? (e0 + lel) * NF + k1
+                                                : (int64_t)partner<NF>(A, w1, (int32_t)((e0 + lel) * NF + k1));
         const double o0 = (w0 & 1) ? tr[((g0 / NF) * 2 + fld) * NF + g0 % NF] : f0;
         const double o1 = (w1 & 1) ? tr[((g1 / NF) * 2 + fld) * NF + g1 % NF] : f1;
         const int fo = (lel * 2 + fld) * NF;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
     if (!lm[el * NF + k]) continue;
     const int64_t gk = (e0 + el) * NF + k;
     const int32_t w = A.fnbr[gk];
-    const int64_t pg = (int64_t)(w >> 1);
+    const int64_t pg = (int64_t)partner<NF>(A, w, (int32_t)gk);
     const bool bnd = pg == gk;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
@@ -603,8 +605,8 @@ __global__ void __launch_bounds__(256) adj_c(const AdjArgs B) {
       double gv[2][2];
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        const int32_t w = A.fnbr[(e0 + lel) * NF + (2 * a + sd) * NFP + ll];
-        const int64_t pg = (int64_t)(w >> 1);
+        const int32_t own = (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll);
+        const int64_t pg = (int64_t)partner<NF>(A, A.fnbr[own], own);
 #pragma unroll
         for (int fld = 0; fld < 2; ++fld) gv[sd][fld] = B.lamuo[((pg / NF) * 2 + fld) * NF + pg % NF];
       }

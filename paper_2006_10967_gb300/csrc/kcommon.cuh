@@ -13,7 +13,8 @@ constexpr int kMaxModes = 32;
 constexpr int kThreads = 256;
 
 // status words (int32) in the workspace
-enum { ST_STATUS = 0, ST_PSEUDO_DONE = 1, ST_PSEUDO_ITERS = 2, ST_COUNTER = 3, ST_WORDS = 8 };
+enum { ST_STATUS = 0, ST_PSEUDO_DONE = 1, ST_PSEUDO_ITERS = 2, ST_COUNTER = 3, ST_BAD_INDEX = 4, ST_WORDS = 8 };
+constexpr int kStatusBounds = -7;  // FR_EBOUNDS
 // double slots in the workspace
 enum { DS_TIME = 0, DS_PSEUDO_RMS = 1, DS_MASS = 2, DS_MASS_C = 3, DS_WORDS = 8 };
 
@@ -137,6 +138,29 @@ struct KArgs {
   TriOpsT<double> trid;
   TriOpsT<float> trif;
 };
+
+// Partner flux point of a connectivity word w (bit 0: the L flag, bits 1-31:
+// the global flux-point index, E Nf < 2^30 checked at mesh creation).  In a
+// build with FR_BOUNDS_CHECK defined (the library's checked build) every such
+// index is checked against E Nf before it is used: an index out of range
+// records FR_EBOUNDS and the connectivity word in the status words, and the
+// caller's own flux point (always in range) is used instead, so no access
+// leaves the arrays.  Without the flag this is the plain shift.
+template <int NF>
+__device__ __forceinline__ int32_t partner(const KArgs& A, int32_t w, int32_t own) {
+  const int32_t p = w >> 1;
+#ifdef FR_BOUNDS_CHECK
+  if (p < 0 || (int64_t)p >= A.E * NF) {
+    atomicExch(&A.status[ST_STATUS], kStatusBounds);
+    atomicExch(&A.status[ST_BAD_INDEX], w);
+    return own;
+  }
+#else
+  (void)A;
+  (void)own;
+#endif
+  return p;
+}
 
 template <typename T> __device__ __forceinline__ const BulkConst<T>& bulk(const KArgs& A);
 template <> __device__ __forceinline__ const BulkConst<double>& bulk<double>(const KArgs& A) { return A.cd; }

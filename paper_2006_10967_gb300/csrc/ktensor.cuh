@@ -422,7 +422,7 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int32_t w = wpre[a][sd];
-        const int32_t p = w >> 1;  // < 2^30 (checked at mesh creation)
+        const int32_t p = partner<NF>(A, w, (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll));
         const int64_t pe = p / NF, pk = p % NF;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) opre[a][sd][q] = (w & 1) ? tr[(pe * 2 + F0 + fsel + q * FS) * NF + pk] : (T)0;
@@ -578,7 +578,7 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     // partner flux point: the common flux also goes to its slot on quads,
     // where the partner's ka_tensor lifts it (a wall point is its own partner)
     const int64_t og = (e0 + el) * NF + k;
-    const int64_t pg = FaceScatter<DIM>::v ? (int64_t)(A.fnbr[og] >> 1) : og;
+    const int64_t pg = FaceScatter<DIM>::v ? (int64_t)partner<NF>(A, A.fnbr[og], (int32_t)og) : og;
     const int64_t pslot = (pg / NF) * 2 * NF + pg % NF;
     int a, s, b0;
     fline<DIM, N>(k, a, s, b0);
@@ -1044,7 +1044,8 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
       for (int sd = 0; sd < 2; ++sd) {
         const int32_t w = wpre[a][sd];
         // flux-point indices fit 31 bits (E Nf < 2^30, checked at mesh creation)
-        const int32_t p = (w & 1) ? (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll) : (w >> 1);
+        const int32_t own = (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll);
+        const int32_t p = (w & 1) ? own : partner<NF>(A, w, own);
         const int64_t pe = p / NF, pk = p % NF;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[(pe * 2 + F0 + fsel + q * FS) * NF + pk];
@@ -1232,7 +1233,8 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
             const int32_t w = wpre[a][sd];
-            const int64_t pg = (int64_t)(w >> 1), og = (e0 + lel) * NF + (sd ? k1 : k0);
+            const int64_t og = (e0 + lel) * NF + (sd ? k1 : k0);
+            const int64_t pg = (int64_t)partner<NF>(A, w, (int32_t)og);
             if (!(w & 1) || pg == og) tr[((pg / NF) * 2 + F0 + fld) * NF + pg % NF] = sd ? t1 : t0;
           }
         } else {

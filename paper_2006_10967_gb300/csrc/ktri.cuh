@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     const int el = idx / NF, k = idx % NF;
     const int32_t w = A.fnbr[(e0 + el) * NF + k];
     const int isL = w & 1;
-    const int64_t pg = (int64_t)(w >> 1), pe = pg / NF, pk = pg % NF;
+    const int64_t pg = (int64_t)partner<NF>(A, w, (int32_t)((e0 + el) * NF + k)), pe = pg / NF, pk = pg % NF;
     lm[el * NF + k] = (unsigned char)isL;
 #pragma unroll
     for (int fld = 0; fld < NFLD; ++fld) {
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
         for (int fld = 0; fld < NFLD; ++fld) cr[(el * NFLD + fld) * NF + k] = 0;
         continue;
       }
-      const int64_t pg = (int64_t)(w >> 1), pe = pg / NF, pk = pg % NF;
+      const int64_t pg = (int64_t)partner<NF>(A, w, (int32_t)((e0 + el) * NF + k)), pe = pg / NF, pk = pg % NF;
       TriMet<T> m;
       tri_metric(gs + el * NG, m);
       const T pn0 = m.S[0][0] * op.nref[k][0] + m.S[1][0] * op.nref[k][1];
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
         for (int k = 0; k < NF; ++k) {
           const int64_t og = (e0 + el) * NF + k;
           const int32_t w = A.fnbr[og];
-          const int64_t pg = (int64_t)(w >> 1);
+          const int64_t pg = (int64_t)partner<NF>(A, w, (int32_t)og);
           const float Fo = (w & 1) ? (float)fc[((e0 + el) * 2 + fld) * NF + k]
                                    : -(float)fc[((pg / NF) * 2 + fld) * NF + pg % NF];
           bsum = ff_add(bsum, ff_mul(A.wphys[og], Fo));

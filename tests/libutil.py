@@ -14,5 +14,7 @@ def header_functions():
 
 
 def ensure_built():
-    from paper_2006_10967_gb300 import build
-    return build.build()
+    """Build the library the package loads (the bounds-checked one when the
+    environment sets FRP_BOUNDS_CHECK=1)."""
+    from paper_2006_10967_gb300 import _capi, build
+    return build.build(checked=_capi.CHECKED)

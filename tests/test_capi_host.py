@@ -121,3 +121,15 @@ def test_partner_index_width_is_guarded(G):
     conn[:] = np.arange(8)
     assert G.lib().fr_mesh_create(C.byref(d), C.byref(h)) == 0
     G.lib().fr_mesh_destroy(h)
+
+
+def test_bounds_checked_build_exports_every_declared_symbol():
+    """The bounds-checked build (FR_BOUNDS_CHECK) of the same sources links
+    and exports the same entry points; its error code has a message."""
+    from paper_2006_10967_gb300 import build
+    path = build.build(checked=True)
+    L = C.CDLL(path)
+    missing = [n for n in header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    L.fr_strerror.restype = C.c_char_p
+    assert b"bounds" in L.fr_strerror(-7)
