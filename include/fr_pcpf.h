@@ -325,6 +325,42 @@ int fr_group_create(fr_field* const* fields, int n, fr_group** out);
 int fr_group_step(fr_group* group, int n_steps, void* stream);
 void fr_group_destroy(fr_group* group);
 
+/* ---- element-partitioned runs (one rank per GPU) ------------------------
+ * A rank holds the elements it owns plus the ghost elements within two
+ * face-neighbour layers of them, all in one local mesh.  The residual of an
+ * owned element (Section 3.1, Steps 1-6) reads its neighbours' traces
+ * (Step 2) and, on faces where a neighbour is the L side, that neighbour's
+ * corrected gradient (Step 5), which reads the neighbour's neighbours; so
+ * with the ghosts' stage values taken from their owners before every RK
+ * stage, the owned elements march exactly as in the whole mesh.  A rank
+ * steps with fr_stage (one stage at a time) and, between stages, gathers the
+ * stage values its peers need (fr_halo_pack), exchanges them (the caller's
+ * transport: NCCL, or device copies), scatters the received ones into its
+ * ghosts (fr_halo_unpack) and recomputes the flux-point traces
+ * (fr_traces).  The ghosts' own updates are discarded by the next exchange.
+ * Preconditioning is not partitioned (its stop rule is a global RMS).
+ *
+ * fr_stage: stage s (1..4) of the physical RK4 step on `stream`, the
+ * residual and update kernels of that stage (asynchronous; no CUDA graph);
+ * stage 4 completes the step (the step count and time advance).  Errors:
+ * FR_EINVAL (null, s outside 1..4). */
+int fr_stage(fr_field* field, int stage, void* stream);
+/* Bytes of one element's stage values (2 fields x nu values in the field's
+ * bulk precision: 8-byte doubles for FR_FP64, 4-byte floats for FR_MIXED). */
+int fr_halo_row_bytes(const fr_field* field, size_t* bytes);
+/* Gather (pack) the stage values of the n elements listed in elems_dev
+ * (device, int64 local element indices) into buf_dev (device, n rows of
+ * fr_halo_row_bytes, in list order), or scatter (unpack) n rows of buf_dev
+ * into the listed elements.  Asynchronous on `stream`.  Every index is
+ * checked on the device: an index outside [0, E) is skipped and records
+ * FR_EINVAL in the status word (fr_sync reports it).  Errors: FR_EINVAL
+ * (null pointers with n > 0, n < 0), FR_ECUDA. */
+int fr_halo_pack(fr_field* field, const int64_t* elems_dev, int64_t n, void* buf_dev, void* stream);
+int fr_halo_unpack(fr_field* field, const int64_t* elems_dev, int64_t n, const void* buf_dev, void* stream);
+/* Recompute every element's flux-point traces from its stage values (Step 1,
+ * Eq. extrapolateSoln) after fr_halo_unpack.  Asynchronous. */
+int fr_traces(fr_field* field, void* stream);
+
 /* Number of kernel variants (fr_params.variant) built for the mesh's element
  * type and order in `precision` (FR_FP64 or FR_MIXED): *count >= 1. */
 int fr_kernel_variants(const fr_mesh* mesh, int precision, int32_t* count);

@@ -12,8 +12,8 @@ import ctypes as C
 import numpy as np
 
 from . import _capi as capi
-from ._capi import (FR_FP64, FR_MIXED, FR_QUAD, FR_TRI, FR_HEX, FR_IC_ARRAY, FR_IC_CIRCLE,
-                    FRError, check, lib)
+from ._capi import (FR_FP64, FR_MIXED, FR_QUAD, FR_TRI, FR_HEX, FR_IC_ARRAY, FR_IC_CIRCLE, FR_EINVAL,
+                    FR_EBOUNDS, FRError, check, lib)
 
 __all__ = ["Mesh", "Field", "make_params", "FRError", "FR_FP64", "FR_MIXED", "lib",
            "fr_mesh_create", "fr_field_init", "fr_step", "fr_adjoint_step", "fr_mass_integral"]
@@ -288,6 +288,35 @@ class Field:
         check(lib().fr_rhs_pseudo(self.handle, C.c_void_p(out.data_ptr()), self._stream(stream)),
               "fr_rhs_pseudo")
         return out
+
+    # ---- element-partitioned stepping (fr_stage, fr_halo_*, fr_traces) -----
+    def stage(self, s, stream=None):
+        """Stage s (1..4) of the physical RK4 step."""
+        check(lib().fr_stage(self.handle, int(s), self._stream(stream)), "fr_stage")
+
+    def halo_dtype(self):
+        nb = C.c_size_t()
+        check(lib().fr_halo_row_bytes(self.handle, C.byref(nb)), "fr_halo_row_bytes")
+        return self.torch.float64 if nb.value == 2 * self.mesh.info.nu * 8 else self.torch.float32
+
+    def halo_pack(self, elems, stream=None):
+        """Stage values of the listed local elements (int64 device tensor) as
+        an (n, 2, nu) device tensor of the bulk precision."""
+        out = self.torch.empty((len(elems), 2, self.mesh.info.nu), dtype=self.halo_dtype(), device="cuda")
+        check(lib().fr_halo_pack(self.handle, C.c_void_p(elems.data_ptr()), len(elems), C.c_void_p(out.data_ptr()),
+                                 self._stream(stream)), "fr_halo_pack")
+        return out
+
+    def halo_unpack(self, elems, rows, stream=None):
+        """Write rows (n, 2, nu; from halo_pack of the owners) into the listed
+        local elements' stage values."""
+        rows = rows.contiguous()
+        assert rows.dtype == self.halo_dtype() and rows.shape == (len(elems), 2, self.mesh.info.nu)
+        check(lib().fr_halo_unpack(self.handle, C.c_void_p(elems.data_ptr()), len(elems),
+                                   C.c_void_p(rows.data_ptr()), self._stream(stream)), "fr_halo_unpack")
+
+    def traces(self, stream=None):
+        check(lib().fr_traces(self.handle, self._stream(stream)), "fr_traces")
 
     # ---- discrete adjoint -------------------------------------------------
     def adjoint_record(self, n_steps, ckpt_every, stream=None):

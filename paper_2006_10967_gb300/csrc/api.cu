@@ -925,6 +925,80 @@ extern "C" int fr_rhs_pseudo(fr_field* f, double* dev_out, void* stream) {
   return FR_OK;
 }
 
+namespace {
+// Element rows of the stage values: gather (dst row r = src row elems[r]) or
+// scatter (dst row elems[r] = src row r); an index outside [0, E) is skipped
+// and recorded in the status word.
+template <typename T>
+__global__ void k_halo_rows(KArgs A, const int64_t* elems, int64_t n, int row, T* buf, int gather) {
+  T* stg = reinterpret_cast<T*>(A.ustg);
+  const int64_t total = n * row;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / row;
+    const int j = (int)(t - r * row);
+    const int64_t e = elems[r];
+    if (e < 0 || e >= A.E) {
+      atomicExch(&A.status[ST_STATUS], FR_EINVAL);
+      continue;
+    }
+    if (gather) buf[t] = stg[e * row + j];
+    else stg[e * row + j] = buf[t];
+  }
+}
+
+int halo_rows(fr_field* f, const int64_t* elems, int64_t n, void* buf, int gather, cudaStream_t s) {
+  if (!f || n < 0 || (n > 0 && (!elems || !buf))) return FR_EINVAL;
+  if (n == 0) return FR_OK;
+  const int row = 2 * f->nu;
+  int grid;
+  launch_elementwise_grid(n * row, &grid);
+  if (f->precision == FR_FP64)
+    k_halo_rows<double><<<grid, kThreads, 0, s>>>(f->args, elems, n, row, static_cast<double*>(buf), gather);
+  else
+    k_halo_rows<float><<<grid, kThreads, 0, s>>>(f->args, elems, n, row, static_cast<float*>(buf), gather);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+}  // namespace
+
+extern "C" int fr_stage(fr_field* f, int stage, void* stream) {
+  if (!f || stage < 1 || stage > 4) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KArgs a = f->args;
+  a.use_dev_time = 1;
+  a.dt = f->prm.dt;
+  a.rk = rk_const(a.dt);
+  a.stage = stage;
+  f->ks.kb[0](a, s);
+  f->ks.ka[0](a, s);
+  CK(cudaGetLastError());
+  if (stage == 4) f->nstep++;
+  return FR_OK;
+}
+
+extern "C" int fr_halo_row_bytes(const fr_field* f, size_t* bytes) {
+  if (!f || !bytes) return FR_EINVAL;
+  *bytes = (size_t)2 * f->nu * (f->precision == FR_FP64 ? 8 : 4);
+  return FR_OK;
+}
+
+extern "C" int fr_halo_pack(fr_field* f, const int64_t* elems, int64_t n, void* buf, void* stream) {
+  return halo_rows(f, elems, n, buf, 1, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fr_halo_unpack(fr_field* f, const int64_t* elems, int64_t n, const void* buf, void* stream) {
+  return halo_rows(f, elems, n, const_cast<void*>(buf), 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fr_traces(fr_field* f, void* stream) {
+  if (!f) return FR_EINVAL;
+  KArgs a = f->args;
+  a.stage = 0;
+  f->ks.ka[0](a, reinterpret_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
 extern "C" int fr_kernel_variants(const fr_mesh* m, int precision, int32_t* count) {
   if (!m || !count || (precision != FR_FP64 && precision != FR_MIXED)) return FR_EINVAL;
   *count = variant_count(*m, precision);

@@ -513,7 +513,22 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
           dst[base + j * st] = acc;
         }
       }
-      if (a == DIM - 1) {
+      if (a == DIM - 1 && DIM == 3 && mcs[lel * kKbRec + 11] == (T)2) {
+        // physical gradient, diagonal metric (axis-aligned affine element):
+        // q_b = S_bb q~_b / det J
+        const T* mcl = mcs + lel * kKbRec;
+        const T sd[3] = {mcl[0], mcl[4], mcl[8]}, rdj = mcl[10];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int i = base + j * st;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            T* qp = qt + (lel * NFLD + fsel + q * FS) * DIM * NU + i;
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) qp[b * NU] = (sd[b] * qp[b * NU]) * rdj;
+          }
+        }
+      } else if (a == DIM - 1) {
         // physical gradient at this line's points (all axes are done)
         LineMetric<DIM, T> em;
         em.load(gs + lel * NG, mcs + lel * kKbRec);
@@ -588,6 +603,79 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     // transformed face normal: row a of S = det J J^{-1} (from the record on
     // affine elements)
     const T* mcl = mcs + el * kKbRec;
+    const int st = ipow(N, a);
+    if (MODE == 0 && DIM == 3 && mcl[11] == (T)2) {
+      // diagonal metric (axis-aligned affine element): the transformed normal
+      // is sg S_aa e_a, so only the normal components of the fluxes enter,
+      // and the viscous flux needs q_phi along axis a and the full gradient
+      // that gives the interface normal (for |q|)
+      const T saa = mcl[a * 4];
+      const T nha = (sg * saa > (T)0) ? (T)1 : (T)-1;
+      const T pm = fabs(saa);
+      const int kn = P.nphi ? 0 : 1;
+      T qn[3];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const T* ql = qt + ((el * 2 + kn) * DIM + c) * NU + b0;
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
+        qn[c] = acc;
+      }
+      const T qna = a == 0 ? qn[0] : (a == 1 ? qn[1] : qn[2]);
+      T qpa = qna;
+      if (!P.nphi) {
+        const T* ql = qt + ((el * 2 + 0) * DIM + a) * NU + b0;
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
+        qpa = acc;
+      }
+      T v[3];
+      const T gel = A.ep ? gfe[el] : gfac;
+      const T epsel = A.ep ? epe[el] : P.eps;
+      if (tab_of(el)) {
+        int jj[3];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) jj[b] = b == a ? N + s : ucoord<N>(b0, b);
+        velocity_tab<DIM, NT, T>(BC.vel, vtab + el * DIM * NT * 2, jj, gel, v);
+      } else if (A.vsf) {
+        const T* vc = LY::VT ? vf + el * DIM * NF + k : vsf + (e0 + el) * DIM * NF + k;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) v[c] = gel * vc[c * NF];
+      } else {
+        T x[3];
+        map_point<S::ET_, T>(gs + el * NG, xi, x);
+        velocity<DIM, T>(BC.vel, x, gel, v);
+      }
+      const T va = a == 0 ? v[0] : (a == 1 ? v[1] : v[2]);
+      T v2 = 0, g2 = 0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        v2 += v[c] * v[c];
+        g2 += qn[c] * qn[c];
+      }
+      const T M = fmax(sqrt_(v2), P.gamma);
+      const T gm = fmax(sqrt_(g2), P.delta);
+      const T pL = cor[(el * 2 + 0) * NF + k], sL = cor[(el * 2 + 1) * NF + k];
+      const T pR = uo[(el * 2 + 0) * NF + k], sR = uo[(el * 2 + 1) * NF + k];
+      const T sharp = P.gamma * pL * ((T)1 - pL) / gm;
+      const T vn = nha * va;
+      const T fvn = nha * (epsel * qpa - sharp * qna);
+      const bool shut = P.noflux && wallp;
+      const T Fp = shut ? (T)0 : (T)0.5 * (pL + pR) * vn - M * fvn + P.tau * (pL - pR);
+      const T Fs = shut ? (T)0 : (T)0.5 * (sL + sR) * vn + P.tau_psi * (sL - sR);
+      const T Fp_t = pm * Fp, Fs_t = pm * Fs;
+      fc[((e0 + el) * 2 + 0) * NF + k] = Fp_t;
+      fc[((e0 + el) * 2 + 1) * NF + k] = Fs_t;
+      if (FaceScatter<DIM>::v && !wallp) {
+        fc[pslot] = Fp_t;
+        fc[pslot + NF] = Fs_t;
+      }
+      cor[(el * 2 + 0) * NF + k] = Fp_t;
+      cor[(el * 2 + 1) * NF + k] = Fs_t;
+      continue;
+    }
     T srow[3];
     if (mcl[11] != (T)0) {
 #pragma unroll
@@ -615,7 +703,6 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     T nh[3];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) nh[c] = pn[c] * rpm;
-    const int st = ipow(N, a);
     if (MODE == 0) {
       T qf[2][3];
 #pragma unroll
@@ -700,7 +787,16 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
     const int el = idx / NU, i = idx % NU;
     T xi[3], Sm[3][3];
     upt_xi<DIM, N>(i, O.x, xi);
-    const T dj = metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kKbRec);
+    // diagonal metric (axis-aligned affine hex): only S_aa enters below
+    const bool dg = MODE == 0 && DIM == 3 && mcs[el * kKbRec + 11] == (T)2;
+    T dj;
+    if (dg) {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) Sm[a][a] = mcs[el * kKbRec + a * 4];
+      dj = mcs[el * kKbRec + 9];
+    } else {
+      dj = metric_c<DIM>(gs + el * NG, xi, Sm, mcs + el * kKbRec);
+    }
     if (MODE == 0) {
       T v[3];
       const T gel = A.ep ? gfe[el] : gfac;
@@ -741,10 +837,15 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         T t0 = 0, t1 = 0;
+        if (dg) {
+          t0 = Sm[a][a] * f0[a];
+          t1 = Sm[a][a] * f1[a];
+        } else {
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-          t0 += Sm[a][c] * f0[c];
-          t1 += Sm[a][c] * f1[c];
+          for (int c = 0; c < DIM; ++c) {
+            t0 += Sm[a][c] * f0[c];
+            t1 += Sm[a][c] * f1[c];
+          }
         }
         qt[((el * 2 + 0) * DIM + a) * NU + i] = t0;
         qt[((el * 2 + 1) * DIM + a) * NU + i] = t1;
@@ -790,12 +891,21 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
         const int el = lel;
         LineMetric<DIM, T> em;
         em.load(gs + el * NG, mcs + el * kKbRec);
+        // diagonal metric (axis-aligned affine hex): only S_bb enters below
+        const bool dg = MODE == 0 && DIM == 3 && mcs[el * kKbRec + 11] == (T)2;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const int i = base + j;  // axis-0 lines are contiguous
           T xi[3], Sm[3][3];
           upt_xi<DIM, N>(i, O.x, xi);
-          const T dj = em.at(xi, Sm);
+          T dj;
+          if (dg) {
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) Sm[b][b] = mcs[el * kKbRec + b * 4];
+            dj = mcs[el * kKbRec + 9];
+          } else {
+            dj = em.at(xi, Sm);
+          }
           if (MODE == 0) {
             T v[3];
             const T gel = A.ep ? gfe[el] : gfac;
@@ -836,10 +946,15 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
 #pragma unroll
             for (int b = 0; b < DIM; ++b) {
               T t0 = 0, t1 = 0;
+              if (dg) {
+                t0 = Sm[b][b] * f0[b];
+                t1 = Sm[b][b] * f1[b];
+              } else {
 #pragma unroll
-              for (int c = 0; c < DIM; ++c) {
-                t0 += Sm[b][c] * f0[c];
-                t1 += Sm[b][c] * f1[c];
+                for (int c = 0; c < DIM; ++c) {
+                  t0 += Sm[b][c] * f0[c];
+                  t1 += Sm[b][c] * f1[c];
+                }
               }
               if (b == 0) {
                 fa[0][j] = t0;

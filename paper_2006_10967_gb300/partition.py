@@ -20,6 +20,14 @@ partition() splits the elements by recursive coordinate bisection of their
 centroids (balanced counts, deterministic); plans() builds every rank's local
 mesh and its send and receive lists; exchange() moves ghost values over
 torch.distributed point-to-point calls (gloo on the host, NCCL on the device).
+
+On the device a rank's field steps one RK stage at a time (Field.stage, the
+library's fr_stage) and exchanges its ghosts' stage values between stages:
+step() does that for one rank over torch.distributed, step_ranks() for
+several ranks' fields held by one process on one device (the exchange is
+then a device copy between the fields).  Preconditioning is not partitioned
+(its stop rule is an RMS over the whole mesh); a partitioned run takes a
+preconditioned state from the whole mesh or runs without it.
 """
 from dataclasses import dataclass, field
 
@@ -181,3 +189,60 @@ def exchange(values, plan, dist=None):
     for q, idx in plan.recv.items():
         values[torch.as_tensor(idx)] = bufs[q]
     return values
+
+
+def _device_lists(plan):
+    import torch
+    cache = getattr(plan, "_dev", None)
+    if cache is None:
+        cache = ({q: torch.as_tensor(ix, device="cuda") for q, ix in plan.send.items()},
+                 {q: torch.as_tensor(ix, device="cuda") for q, ix in plan.recv.items()})
+        plan._dev = cache
+    return cache
+
+
+def halo_exchange(field, plan, dist=None):
+    """Replace the ghost elements' stage values of a rank's field with their
+    owners' (packed on the device, moved with isend/irecv, unpacked), then
+    recompute the traces."""
+    import torch
+    import torch.distributed as td
+    d = dist or td
+    send, recv = _device_lists(plan)
+    packed = {q: field.halo_pack(ix) for q, ix in sorted(send.items())}
+    bufs = {q: torch.empty((len(ix), 2, field.mesh.info.nu), dtype=field.halo_dtype(), device="cuda")
+            for q, ix in sorted(recv.items())}
+    reqs = [d.irecv(bufs[q], src=q) for q in sorted(bufs)]
+    reqs += [d.isend(packed[q], dst=q) for q in sorted(packed)]
+    for r in reqs:
+        r.wait()
+    for q, ix in recv.items():
+        field.halo_unpack(ix, bufs[q])
+    field.traces()
+
+
+def step(field, plan, n_steps=1, dist=None):
+    """n physical RK4 steps of one rank's field with a ghost exchange after
+    every stage."""
+    for _ in range(int(n_steps)):
+        for s in (1, 2, 3, 4):
+            field.stage(s)
+            halo_exchange(field, plan, dist)
+
+
+def step_ranks(fields, plans, n_steps=1):
+    """n physical RK4 steps of several ranks' fields held by this process on
+    one device: per stage every rank's stage, then every rank's ghosts
+    refreshed from their owners by device copies, then the traces."""
+    lists = [_device_lists(p) for p in plans]
+    for _ in range(int(n_steps)):
+        for s in (1, 2, 3, 4):
+            for f in fields:
+                f.stage(s)
+            packed = {(p.rank, q): fields[p.rank].halo_pack(ix)
+                      for p, (send, _) in zip(plans, lists) for q, ix in sorted(send.items())}
+            for p, (_, recv) in zip(plans, lists):
+                for q, ix in sorted(recv.items()):
+                    fields[p.rank].halo_unpack(ix, packed[(q, p.rank)])
+            for f in fields:
+                f.traces()
