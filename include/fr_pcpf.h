@@ -378,27 +378,45 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  * The paper has no adjoint; these calls give the exact gradient of the FR
  * march's discrete map for a loss of the final state, with respect to the
  * initial fields and the stream-function coefficients (FR_VEL_STREAM).
- * Built for the FP64 path on quadrilaterals (p <= 6) and hexahedra (p <= 3);
- * other fields return FR_EUNSUPPORTED.  The recorded window must not contain
- * a preconditioning step (n > 0, n % n_precond == 0).
+ * Built for quadrilaterals (p <= 6) and hexahedra (p <= 3) in both
+ * precisions; triangles return FR_EUNSUPPORTED.  On an FR_MIXED field the
+ * recorded march is the field's own FP32 one (its float-float states are the
+ * checkpoints); the sweep recomputes each segment in FP64 from its widened
+ * checkpoint on FP64 shadow arrays in the workspace (a preconditioning in the
+ * window likewise from phi0) and applies the FP64 vector-Jacobian products
+ * along that recomputation (velocity evaluated analytically): the FP64
+ * scheme's gradient along trajectories restarted every ckpt_every steps from
+ * the FP32 march.  (Along the FP32 stage inputs themselves the linearisation
+ * is ill-conditioned: psi rounded to float has flat spots where phi is small,
+ * where the normal's derivative is 1/delta.)  The recorded window must not
+ * contain a preconditioning step (n > 0, n % n_precond == 0).
  *
+ * flags: 0, or FR_ADJ_PRECONDITION: the window starts with the
+ *   preconditioning of Section 2 from the current phi (psi0 = psi = phi -
+ *   1/2, then pseudo_kmax pseudo-time RK4 iterations of Eq. pseudotimesystem;
+ *   needs params.pseudo_fixed = 1), and dJ_du0 of fr_adjoint_step is then
+ *   dJ/dphi0 along both paths, phi0 itself and psi = P(phi0 - 1/2) with the
+ *   source's psi0 = phi0 - 1/2 (its psi half is zero: psi is no input).
  * fr_adjoint_workspace_bytes: device bytes for a window of n_steps with a
  *   checkpoint every ckpt_every steps ((n_steps/ckpt_every + 1) solution
- *   copies + 4 * ckpt_every stage inputs + adjoint work arrays).
+ *   copies + 4 * ckpt_every stage inputs + adjoint work arrays; with
+ *   FR_ADJ_PRECONDITION also 4 * pseudo_kmax pseudo stage inputs).
  * fr_adjoint_record: advance n_steps from the current state (as fr_step),
  *   keeping checkpoints in `workspace` (device, caller-owned, 256-byte
  *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
  *   FR_EUNSUPPORTED for a field whose normal is FR_NORMAL_PHI (the adjoint
- *   covers the preconditioned method).
+ *   covers the preconditioned method), and for FR_ADJ_PRECONDITION without
+ *   pseudo_fixed (the stop rule's iteration count is not differentiated).
  * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
  *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,
  *   2 * n_dof: phi then psi) and, for a stream-function velocity,
  *   dJ/d(A_1..A_M, B_1..B_M) to dJ_dcoef (device, 2M, or NULL).  Recomputes
  *   the forward stages segment by segment from the checkpoints; on return the
  *   field is back at the end of the window.  Synchronises `stream`. */
-int fr_adjoint_workspace_bytes(fr_field* field, int n_steps, int ckpt_every, size_t* bytes);
-int fr_adjoint_record(fr_field* field, int n_steps, int ckpt_every, void* workspace, size_t workspace_bytes,
-                      void* stream);
+#define FR_ADJ_PRECONDITION 1
+int fr_adjoint_workspace_bytes(fr_field* field, int n_steps, int ckpt_every, int flags, size_t* bytes);
+int fr_adjoint_record(fr_field* field, int n_steps, int ckpt_every, int flags, void* workspace,
+                      size_t workspace_bytes, void* stream);
 int fr_adjoint_step(fr_field* field, const double* dJ_dphiT, const double* dJ_dpsiT, double* dJ_du0,
                     double* dJ_dcoef, void* stream);
 

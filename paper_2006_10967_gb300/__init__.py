@@ -319,15 +319,18 @@ class Field:
         check(lib().fr_traces(self.handle, self._stream(stream)), "fr_traces")
 
     # ---- discrete adjoint -------------------------------------------------
-    def adjoint_record(self, n_steps, ckpt_every, stream=None):
-        """Advance n_steps keeping checkpoints for adjoint_step (fr_adjoint_record)."""
+    def adjoint_record(self, n_steps, ckpt_every, precondition=False, stream=None):
+        """Advance n_steps keeping checkpoints for adjoint_step (fr_adjoint_record);
+        with precondition, the window starts with the preconditioning of the
+        current phi (psi is reset to phi - 1/2 first; FR_ADJ_PRECONDITION)."""
+        flags = capi.FR_ADJ_PRECONDITION if precondition else 0
         nbytes = C.c_size_t()
-        check(lib().fr_adjoint_workspace_bytes(self.handle, int(n_steps), int(ckpt_every), C.byref(nbytes)),
-              "fr_adjoint_workspace_bytes")
+        check(lib().fr_adjoint_workspace_bytes(self.handle, int(n_steps), int(ckpt_every), flags,
+                                               C.byref(nbytes)), "fr_adjoint_workspace_bytes")
         self._adj_ws = self.torch.empty(nbytes.value + 256, dtype=self.torch.uint8, device="cuda")
         base = (self._adj_ws.data_ptr() + 255) // 256 * 256
-        check(lib().fr_adjoint_record(self.handle, int(n_steps), int(ckpt_every), C.c_void_p(base), nbytes.value,
-                                      self._stream(stream)), "fr_adjoint_record")
+        check(lib().fr_adjoint_record(self.handle, int(n_steps), int(ckpt_every), flags, C.c_void_p(base),
+                                      nbytes.value, self._stream(stream)), "fr_adjoint_record")
 
     def adjoint_step(self, dJ_dphiT, dJ_dpsiT=None, n_coef=0, stream=None):
         """(dJ/du0 as a (2, E, Nu) tensor, dJ/dcoef (2M,) or None) via fr_adjoint_step."""
@@ -402,10 +405,11 @@ class _PlaceholderIC:
 _PLACEHOLDER_IC = _PlaceholderIC()
 
 
-def flow_function(mesh, params_fn, n_steps, ckpt_every):
+def flow_function(mesh, params_fn, n_steps, ckpt_every, precondition=False):
     """A torch.autograd.Function for phi_T = Flow(phi0, coef): the FR march of
-    n_steps from phi0 (psi0 = phi0 - 1/2, no preconditioning) with a stream
-    velocity whose coefficients are coef = (A_1..A_M, B_1..B_M).
+    n_steps from phi0 (psi0 = phi0 - 1/2; with precondition, psi is then the
+    fixed-count preconditioning of phi0 - 1/2 and the gradient follows it too)
+    with a stream velocity whose coefficients are coef = (A_1..A_M, B_1..B_M).
     params_fn(coef) -> fr_params.  Backward is the hand-written adjoint
     (fr_adjoint_record / fr_adjoint_step).  phi0 (a CUDA float64 tensor of
     the mesh's shape) and phi_T stay on the device: the field is set up with a
@@ -421,7 +425,7 @@ def flow_function(mesh, params_fn, n_steps, ckpt_every):
             F.set_device(0, u0)
             F.set_device(1, u0 - 0.5)
             F.set_device(2, u0 - 0.5)
-            F.adjoint_record(n_steps, ckpt_every)
+            F.adjoint_record(n_steps, ckpt_every, precondition=precondition)
             ctx.field = F
             ctx.n_coef = coef.numel()
             out = torch.empty_like(u0)

@@ -17,6 +17,7 @@ BOUNDS_FIRED = []
 
 FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ENONFINITE, FR_ETIMEOUT, FR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FR_EBOUNDS = -7
+FR_ADJ_PRECONDITION = 1
 FR_QUAD, FR_TRI, FR_HEX = 0, 1, 2
 FR_FP64, FR_MIXED = 0, 1
 FR_VEL_UNIFORM, FR_VEL_RIDER_KOTHE, FR_VEL_LEVEQUE, FR_VEL_STREAM, FR_VEL_ROTATION = 0, 1, 2, 3, 4
@@ -96,8 +97,8 @@ _SIGS = {
     "fr_field_set_device": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "fr_rhs": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "fr_rhs_pseudo": (C.c_int, [_vp, _vp, _vp]),
-    "fr_adjoint_workspace_bytes": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
-    "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
+    "fr_adjoint_workspace_bytes": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
     "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fr_kernel_variants": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int32)]),
     "fr_stage": (C.c_int, [_vp, C.c_int, _vp]),

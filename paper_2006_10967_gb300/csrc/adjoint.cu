@@ -12,12 +12,33 @@
 //   lam = lam' + a4 + a3 + a2 + a1,
 // with the vector-Jacobian products of kadj.cuh, and accumulates the
 // gradient with respect to the stream-function coefficients.
+//
+// With FR_ADJ_PRECONDITION the window starts with the t = 0 preconditioning
+// (psi0 = psi = phi0 - 1/2, then the fixed count of pseudo-time RK4
+// iterations), recorded stage by stage; fr_adjoint_step then continues the
+// reverse sweep through the pseudo iterations (adj_b<.., 1>, the same RK4
+// recurrence with the pseudo step) and returns dJ/dphi0 along both paths:
+// phi0 itself and psi = P(phi0 - 1/2; psi0 = phi0 - 1/2).
+//
+// Mixed-precision fields: the recorded march is the field's own FP32 one
+// (its float-float states are the checkpoints); each segment is recomputed
+// from its checkpoint, widened to FP64, by the FP64 kernels on FP64 shadow
+// arrays in the workspace, and the sweep linearises along that recomputation
+// (velocity evaluated analytically).  Linearising along the FP32 stage inputs
+// themselves is ill-conditioned: where phi is small but not zero, psi = phi
+// - 1/2 rounded to float has an exactly flat gradient, and the derivative of
+// the normal q / max(|q|, delta) there is 1 / delta.  With a preconditioning
+// in the window its pseudo iterations are likewise re-run in FP64 from the
+// same phi0.  The result is the FP64 scheme's gradient along trajectories
+// restarted every ckpt_every steps from the FP32 march.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "field.cuh"
 #include "kadj.cuh"
+#include "kdispatch.hpp"
 
 using namespace frp;
 
@@ -33,7 +54,7 @@ size_t al(size_t x) { return (x + 255) / 256 * 256; }
 typedef void (*AdjFn)(const AdjArgs&, cudaStream_t);
 typedef void (*TabFn)(const KArgs&, double*, cudaStream_t);
 struct AdjSet {
-  AdjFn a = nullptr, b = nullptr, c = nullptr;
+  AdjFn a = nullptr, b = nullptr, c = nullptr, b1 = nullptr;  // b1: the preconditioning system
   TabFn tab = nullptr;  // cos/sin table of the stream-function modes at the points
   int et = 1;
 };
@@ -43,15 +64,15 @@ void la(const AdjArgs& B, cudaStream_t s) {
   using LY = AdjLayout<DIM, N>;
   adj_a<DIM, N><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, 0, s>>>(B);
 }
-template <int DIM, int N>
+template <int DIM, int N, int MODE>
 void lb(const AdjArgs& B, cudaStream_t s) {
   using LY = AdjLayout<DIM, N>;
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(adj_b<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+    cudaFuncSetAttribute(adj_b<DIM, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
     init = true;
   }
-  adj_b<DIM, N><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
+  adj_b<DIM, N, MODE><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
 }
 template <int DIM, int N>
 void lc(const AdjArgs& B, cudaStream_t s) {
@@ -68,7 +89,8 @@ template <int DIM, int N>
 AdjSet make_set() {
   AdjSet a;
   a.a = la<DIM, N>;
-  a.b = lb<DIM, N>;
+  a.b = lb<DIM, N, 0>;
+  a.b1 = lb<DIM, N, 1>;
   a.c = lc<DIM, N>;
   a.tab = ltab<DIM, N>;
   a.et = AdjLayout<DIM, N>::ET;
@@ -76,7 +98,6 @@ AdjSet make_set() {
 }
 
 bool adj_kernels(const fr_field* f, AdjSet* out) {
-  if (f->precision != FR_FP64) return false;
   if (f->etype == FR_QUAD) {
     switch (f->order) {
       case 1: *out = make_set<2, 2>(); return true;
@@ -115,6 +136,70 @@ __global__ void k_unpack_lam(const double* L, double* out, int64_t E, int NU) {
   }
 }
 
+// float-float states widened to FP64 (mixed fields)
+__global__ void k_ff_widen(const float2* in, double* out, int64_t n) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = (double)in[g].x + (double)in[g].y;
+}
+
+// psi0 = psi = phi - 1/2 on the FP64 shadow (the start of its preconditioning)
+__global__ void k_reset_psi64(KArgs A, int64_t NU) {
+  const int64_t n = A.E * NU;
+  double* st = reinterpret_cast<double*>(A.ustg);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / NU, i = g % NU;
+    const double p0 = A.u[(e * 2 + 0) * NU + i] - 0.5;
+    A.psi0[g] = p0;
+    A.u[(e * 2 + 1) * NU + i] = p0;
+    st[(e * 2 + 1) * NU + i] = p0;
+  }
+}
+
+// The FP64 shadow of a mixed field's arguments (workspace arrays; velocity
+// evaluated analytically)
+KArgs shadow_args(const fr_field* f, const AdjRecord& R) {
+  KArgs a = f->args;
+  a.u = reinterpret_cast<double*>(R.ws + R.off_u64);
+  a.ustg = R.ws + R.off_stg64;
+  a.acc = reinterpret_cast<double*>(R.ws + R.off_acc64);
+  a.rp = R.ws + R.off_rp64;
+  a.tr = R.ws + R.off_trd;
+  a.fc = R.ws + R.off_fc64;
+  a.mcg = R.ws + R.off_mc64;
+  a.vsu = a.vsf = nullptr;
+  a.tacc = nullptr;
+  a.ep = nullptr;
+  return a;
+}
+
+// The FP64 kernel set of the field's element type and order (the traces of
+// the widened stage inputs of a mixed field).
+bool fp64_kernels(const fr_field* f, KernelSet* ks) {
+  if (f->etype == FR_QUAD) return kernels_quad(f->order, FR_FP64, f->E, 0, ks);
+  if (f->etype == FR_HEX) return kernels_hex(f->order, FR_FP64, f->E, 0, ks);
+  return false;
+}
+
+// preconditioning sweep: keep phi's adjoint (out[0..n)) and zero it in L
+__global__ void k_zero_phi(double* L, int64_t E, int NU) {
+  const int64_t n = E * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / NU, i = g % NU;
+    L[(e * 2 + 0) * NU + i] = 0.0;
+  }
+}
+
+// dJ/dphi0 = lam_phi + lam_psi(start of the pseudo iterations) + lam_psi0;
+// psi is no independent input then (its slot of out is zeroed)
+__global__ void k_precond_out(double* out, const double* L, const double* lpsi0, int64_t E, int NU) {
+  const int64_t n = E * NU;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / NU, i = g % NU;
+    out[g] += L[(e * 2 + 1) * NU + i] + lpsi0[g];
+    out[n + g] = 0.0;
+  }
+}
+
 // out[m] = sum over blocks of coefp[b][m], in block order
 __global__ void k_coef_reduce(const double* coefp, int nblocks, int M2, double* out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,7 +214,7 @@ struct Sizes {
   int n_ckpt;
 };
 
-Sizes sizes(const fr_field* f, int n_steps, int ck, int adj_blocks) {
+Sizes sizes(const fr_field* f, int n_steps, int ck, int adj_blocks, int flags) {
   Sizes z;
   const size_t ndof = (size_t)f->E * f->nu;
   z.n_ckpt = (n_steps + ck - 1) / ck;
@@ -143,6 +228,12 @@ Sizes sizes(const fr_field* f, int n_steps, int ck, int adj_blocks) {
   t += 2 * al(nf2);
   t += 4 * al(2 * ndof * 8);
   t += al((size_t)adj_blocks * 2 * FR_MAX_MODES * 8);
+  if (f->precision == FR_MIXED)  // FP64 shadow: traces, common flux, state, stage, accumulator, divergence, records
+    t += 2 * al(nf2) + 4 * al(2 * ndof * 8) + al((size_t)f->E * kMetricRec * 8);
+  if (flags & FR_ADJ_PRECONDITION) {           // pseudo stage inputs, dR_p/dpsi0 adjoint
+    t += (size_t)f->prm.pseudo_kmax * 4 * z.stage_slot;
+    t += al(ndof * 8);
+  }
   if (f->prm.vel.kind == FR_VEL_STREAM) {  // phase table and per-point velocity adjoint
     const size_t np = (size_t)f->E * (f->nu + f->nf);
     t += al(np * (size_t)f->prm.vel.n_modes * 2 * 8);
@@ -154,25 +245,28 @@ Sizes sizes(const fr_field* f, int n_steps, int ck, int adj_blocks) {
 
 }  // namespace
 
-extern "C" int fr_adjoint_workspace_bytes(fr_field* f, int n_steps, int ckpt_every, size_t* bytes) {
-  if (!f || !bytes || n_steps < 1 || ckpt_every < 1) return FR_EINVAL;
+extern "C" int fr_adjoint_workspace_bytes(fr_field* f, int n_steps, int ckpt_every, int flags, size_t* bytes) {
+  if (!f || !bytes || n_steps < 1 || ckpt_every < 1 || (flags & ~FR_ADJ_PRECONDITION)) return FR_EINVAL;
   AdjSet as;
   if (!adj_kernels(f, &as)) return FR_EUNSUPPORTED;
   const int nb = (int)((f->E + as.et - 1) / as.et);
-  *bytes = sizes(f, n_steps, ckpt_every, nb).total;
+  *bytes = sizes(f, n_steps, ckpt_every, nb, flags).total;
   return FR_OK;
 }
 
-extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, void* ws, size_t ws_bytes,
+extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, int flags, void* ws, size_t ws_bytes,
                                  void* stream) {
-  if (!f || !ws || n_steps < 1 || ckpt_every < 1) return FR_EINVAL;
+  if (!f || !ws || n_steps < 1 || ckpt_every < 1 || (flags & ~FR_ADJ_PRECONDITION)) return FR_EINVAL;
+  const bool pre = (flags & FR_ADJ_PRECONDITION) != 0;
+  // the preconditioning is differentiated for its fixed iteration count
+  if (pre && !f->prm.pseudo_fixed) return FR_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return FR_EINVAL;
   if (f->prm.normal != FR_NORMAL_PSI) return FR_EUNSUPPORTED;  // adjoint of the preconditioned method only
   if (f->prm.wall != FR_WALL_COPY) return FR_EUNSUPPORTED;     // and of the paper's copy-ghost walls
   AdjSet as;
   if (!adj_kernels(f, &as)) return FR_EUNSUPPORTED;
   const int nb = (int)((f->E + as.et - 1) / as.et);
-  const Sizes z = sizes(f, n_steps, ckpt_every, nb);
+  const Sizes z = sizes(f, n_steps, ckpt_every, nb, flags);
   if (ws_bytes < z.total) return FR_ENOMEM;
   // the recorded window must not contain a preconditioning step
   for (int64_t n = f->nstep; n < f->nstep + n_steps; ++n)
@@ -209,6 +303,30 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, void*
   off += nd2;
   R.off_coefp = off;
   off += al((size_t)nb * 2 * FR_MAX_MODES * 8);
+  if (f->precision == FR_MIXED) {
+    R.off_trd = off;
+    off += nf2;
+    R.off_fc64 = off;
+    off += nf2;
+    R.off_u64 = off;
+    off += nd2;
+    R.off_stg64 = off;
+    off += nd2;
+    R.off_acc64 = off;
+    off += nd2;
+    R.off_rp64 = off;
+    off += nd2;
+    R.off_mc64 = off;
+    off += al((size_t)f->E * kMetricRec * 8);
+  }
+  if (pre) {
+    R.precond = 1;
+    R.n_pseudo = f->prm.pseudo_kmax;
+    R.off_pstage = off;
+    off += (size_t)R.n_pseudo * 4 * z.stage_slot;
+    R.off_lpsi0 = off;
+    off += al((size_t)f->E * f->nu * 8);
+  }
   if (f->prm.vel.kind == FR_VEL_STREAM) {
     const size_t np = (size_t)f->E * (f->nu + f->nf);
     R.off_cs = off;
@@ -216,6 +334,55 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, void*
     R.off_lv = off;
   }
   const size_t ubytes = 2 * (size_t)f->E * f->nu * 8;
+  const bool mixed = f->precision == FR_MIXED;
+  KernelSet ks64{};
+  if (mixed && !fp64_kernels(f, &ks64)) return FR_EUNSUPPORTED;
+  const int64_t nv = 2 * f->E * f->nu;
+  const int grid = (int)std::min<int64_t>((nv + 255) / 256, 152 * 16);
+  if (mixed) ks64.mconst(shadow_args(f, R), s);  // FP64 metric records of the shadow
+  if (pre) {
+    // the t = 0 preconditioning, keeping every pseudo stage input (a mixed
+    // field's FP32 preconditioning is re-run in FP64 from the same phi0)
+    if (mixed)
+      k_ff_widen<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(f->args.u), reinterpret_cast<double*>(R.ws + R.off_u64), nv);
+    int rc = field_precondition_begin(f, s);
+    if (rc) return rc;
+    KArgs a = f->args;
+    a.dt = f->prm.pseudo_dtau;
+    a.rk = rk_const(a.dt);
+    a.use_dev_time = 0;
+    for (int k = 0; k < R.n_pseudo; ++k)
+      for (int st = 1; st <= 4; ++st) {
+        if (!mixed) {
+          char* U = R.ws + R.off_pstage + ((size_t)k * 4 + (st - 1)) * z.stage_slot;
+          CK(cudaMemcpyAsync(U, f->args.ustg, ubytes, cudaMemcpyDeviceToDevice, s));
+        }
+        a.stage = st;
+        f->ks.kb[1](a, s);
+        f->ks.ka[1](a, s);
+      }
+    if (mixed) {
+      KArgs b = shadow_args(f, R);
+      b.dt = f->prm.pseudo_dtau;
+      b.rk = rk_const(b.dt);
+      b.use_dev_time = 0;
+      CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
+      k_reset_psi64<<<grid, 256, 0, s>>>(b, f->nu);
+      b.stage = 0;
+      ks64.ka[1](b, s);
+      for (int k = 0; k < R.n_pseudo; ++k)
+        for (int st = 1; st <= 4; ++st) {
+          char* U = R.ws + R.off_pstage + ((size_t)k * 4 + (st - 1)) * z.stage_slot;
+          CK(cudaMemcpyAsync(U, b.ustg, ubytes, cudaMemcpyDeviceToDevice, s));
+          b.stage = st;
+          ks64.kb[1](b, s);
+          ks64.ka[1](b, s);
+        }
+      CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
+    }
+    CK(cudaGetLastError());
+    f->n_precond_done++;
+  }
   for (int n = 0; n < n_steps; ++n) {
     if (n % ckpt_every == 0) {
       char* slot = R.ws + R.off_ckpt + (size_t)(n / ckpt_every) * z.ckpt_slot;
@@ -240,7 +407,10 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
   AdjSet as;
   if (!adj_kernels(f, &as)) return FR_EUNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const Sizes z = sizes(f, R.n_steps, R.ckpt_every, R.adj_blocks);
+  const bool mixed = f->precision == FR_MIXED;
+  KernelSet ks64{};
+  if (mixed && !fp64_kernels(f, &ks64)) return FR_EUNSUPPORTED;
+  const Sizes z = sizes(f, R.n_steps, R.ckpt_every, R.adj_blocks, R.precond ? FR_ADJ_PRECONDITION : 0);
   const int64_t E = f->E;
   const int NU = f->nu;
   const size_t ubytes = 2 * (size_t)E * NU * 8;
@@ -269,23 +439,33 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
     const int s1 = s0 + R.ckpt_every < R.n_steps ? s0 + R.ckpt_every : R.n_steps;
     // restore the checkpoint and recompute the segment, keeping the stage inputs
     char* slot = R.ws + R.off_ckpt + (size_t)seg * z.ckpt_slot;
-    CK(cudaMemcpyAsync(f->args.u, slot, ubytes, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(f->args.dstate + DS_TIME, slot + ubytes, 8, cudaMemcpyDeviceToDevice, s));
-    int rc = field_stage_and_traces(f, s);
-    if (rc) return rc;
+    KArgs a = mixed ? shadow_args(f, R) : f->args;
+    const KernelSet& ksr = mixed ? ks64 : f->ks;
+    if (mixed) {
+      // the FP64 shadow from the widened float-float checkpoint
+      k_ff_widen<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(slot), a.u, 2 * E * NU);
+      CK(cudaMemcpyAsync(a.ustg, a.u, ubytes, cudaMemcpyDeviceToDevice, s));
+      KArgs b = a;
+      b.stage = 0;
+      ks64.ka[0](b, s);
+    } else {
+      CK(cudaMemcpyAsync(f->args.u, slot, ubytes, cudaMemcpyDeviceToDevice, s));
+      int rc = field_stage_and_traces(f, s);
+      if (rc) return rc;
+    }
     f->nstep = R.step0 + s0;
     for (int n = s0; n < s1; ++n) {
       CK(cudaMemcpyAsync(times + (n - s0), f->args.dstate + DS_TIME, 8, cudaMemcpyDeviceToDevice, s));
-      KArgs a = f->args;
       a.use_dev_time = 1;
       a.dt = dt;
       a.rk = rk_const(dt);
       for (int st = 1; st <= 4; ++st) {
         char* U = R.ws + R.off_stage + ((size_t)(n - s0) * 4 + (st - 1)) * z.stage_slot;
-        CK(cudaMemcpyAsync(U, f->args.ustg, ubytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(U, a.ustg, ubytes, cudaMemcpyDeviceToDevice, s));
         a.stage = st;
-        f->ks.kb[0](a, s);
-        f->ks.ka[0](a, s);
+        ksr.kb[0](a, s);
+        ksr.ka[0](a, s);
       }
       f->nstep++;
     }
@@ -301,7 +481,18 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
         B.K.use_dev_time = 0;
         B.K.t = th[n - s0] + (st == 1 ? 0.0 : (st == 4 ? dt : 0.5 * dt));
         B.K.stage = 0;
-        f->ks.ka[0](B.K, s);  // traces of this stage input
+        if (mixed) {
+          // the FP64 shadow: traces into the workspace, analytic velocity
+          const char* U = static_cast<const char*>(B.K.ustg);
+          B.K = shadow_args(f, R);
+          B.K.ustg = const_cast<char*>(U);
+          B.K.use_dev_time = 0;
+          B.K.t = th[n - s0] + (st == 1 ? 0.0 : (st == 4 ? dt : 0.5 * dt));
+          B.K.stage = 0;
+          ks64.ka[0](B.K, s);
+        } else {
+          f->ks.ka[0](B.K, s);  // traces of this stage input
+        }
         B.lamk = st == 4 ? Lp : Lk;
         B.lam_scale = st == 4 ? dt / 6.0 : 1.0;
         B.Y = Y;
@@ -335,6 +526,60 @@ extern "C" int fr_adjoint_step(fr_field* f, const double* dJ_dphiT, const double
   }
   CK(cudaGetLastError());
   k_unpack_lam<<<grid, 256, 0, s>>>(Lp, dJ_du0, E, NU);
+  if (R.precond) {
+    // reverse sweep through the pseudo iterations of the t = 0
+    // preconditioning: phi is not changed by them (its adjoint, kept in
+    // dJ_du0, is carried with zero weight), psi's is propagated to psi(0) =
+    // phi0 - 1/2, and the dependence of the source on psi0 = phi0 - 1/2 is
+    // accumulated
+    double* lpsi0 = reinterpret_cast<double*>(R.ws + R.off_lpsi0);
+    k_zero_phi<<<grid, 256, 0, s>>>(Lp, E, NU);
+    CK(cudaMemsetAsync(lpsi0, 0, (size_t)E * NU * 8, s));
+    const double dtau = f->prm.pseudo_dtau;
+    for (int k = R.n_pseudo - 1; k >= 0; --k) {
+      for (int st = 4; st >= 1; --st) {
+        AdjArgs B;
+        std::memset(&B, 0, sizeof(B));
+        B.K = f->args;
+        B.K.ustg = R.ws + R.off_pstage + ((size_t)k * 4 + (st - 1)) * z.stage_slot;
+        B.K.use_dev_time = 0;
+        B.K.t = 0.0;
+        B.K.stage = 0;
+        if (mixed) {
+          const char* U = static_cast<const char*>(B.K.ustg);
+          B.K = shadow_args(f, R);
+          B.K.ustg = const_cast<char*>(U);
+          B.K.use_dev_time = 0;
+          B.K.t = 0.0;
+          B.K.stage = 0;
+          ks64.ka[0](B.K, s);
+        } else {
+          f->ks.ka[0](B.K, s);
+        }
+        B.lamk = st == 4 ? Lp : Lk;
+        B.lam_scale = st == 4 ? dtau / 6.0 : 1.0;
+        B.Y = Y;
+        B.lamU = lamU;
+        B.lamuo = lamuo;
+        B.Lp = Lp;
+        B.Lu = Lu;
+        B.first = st == 4;
+        B.lam_psi0 = lpsi0;
+        switch (st) {
+          case 4: B.Lk = Lk; B.c_lp = dtau / 3.0; B.c_a = dtau; break;
+          case 3: B.Lk = Lk; B.c_lp = dtau / 3.0; B.c_a = 0.5 * dtau; break;
+          case 2: B.Lk = Lk; B.c_lp = dtau / 6.0; B.c_a = 0.5 * dtau; break;
+          default: B.Lk = nullptr; B.c_lp = 0.0; B.c_a = 0.0;
+        }
+        as.a(B, s);
+        as.b1(B, s);
+        as.c(B, s);
+      }
+      std::swap(Lp, Lu);
+    }
+    CK(cudaGetLastError());
+    k_precond_out<<<grid, 256, 0, s>>>(dJ_du0, Lp, lpsi0, E, NU);
+  }
   if (M2 && dJ_dcoef) k_coef_reduce<<<1, 64, 0, s>>>(coefp, R.adj_blocks, M2, dJ_dcoef);
   // leave the field at the end of the recorded window
   char* last = R.ws + R.off_ckpt + (size_t)z.n_ckpt * z.ckpt_slot;

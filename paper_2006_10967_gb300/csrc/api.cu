@@ -468,6 +468,21 @@ int field_run_step(fr_field* f, cudaStream_t s, bool allow_precondition) {
   return run_step(f, s);
 }
 int field_stage_and_traces(fr_field* f, cudaStream_t s) { return stage_and_traces(f, s); }
+int field_precondition_begin(fr_field* f, cudaStream_t s) {
+  CK(cudaMemsetAsync(f->args.status + ST_PSEUDO_DONE, 0, 3 * sizeof(int32_t), s));
+  int grid;
+  launch_elementwise_grid(f->E * f->nu, &grid);
+  if (f->precision == FR_FP64) k_reset_psi<double><<<grid, kThreads, 0, s>>>(f->args, f->nu, 0);
+  else k_reset_psi<float><<<grid, kThreads, 0, s>>>(f->args, f->nu, 1);
+  KArgs a = f->args;
+  a.stage = 0;
+  a.dt = f->prm.pseudo_dtau;
+  a.rk = rk_const(a.dt);
+  a.use_dev_time = 0;
+  f->ks.ka[1](a, s);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
 }  // namespace frp
 
 namespace {

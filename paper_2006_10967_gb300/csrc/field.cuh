@@ -14,7 +14,12 @@ struct AdjRecord {
   char* ws = nullptr;      // caller workspace
   size_t bytes = 0;
   size_t off_ckpt = 0, off_stage = 0, off_times = 0, off_Y = 0, off_lamuo = 0, off_lamU = 0, off_Lp = 0,
-         off_Lu = 0, off_Lk = 0, off_coefp = 0, off_cs = 0, off_lv = 0;
+         off_Lu = 0, off_Lk = 0, off_coefp = 0, off_cs = 0, off_lv = 0,
+         off_trd = 0,   // mixed fields: FP64 shadow arrays (traces, state, stage input,
+         off_u64 = 0, off_stg64 = 0, off_acc64 = 0, off_rp64 = 0, off_fc64 = 0, off_mc64 = 0,  // RK accumulator,
+                        // partial divergence, common flux, metric records) of the FP64 recomputation
+         off_pstage = 0, off_lpsi0 = 0;  // preconditioning: pseudo stage inputs, dR_p/dpsi0 adjoint
+  int precond = 0, n_pseudo = 0;  // the window starts with the t = 0 preconditioning (n_pseudo iterations)
   int adj_blocks = 0;
 };
 
@@ -45,4 +50,6 @@ struct fr_field {
 namespace frp {
 int field_run_step(fr_field* f, cudaStream_t s, bool allow_precondition);
 int field_stage_and_traces(fr_field* f, cudaStream_t s);
+// psi0 = psi = phi - 1/2 and the traces of psi: the start of a preconditioning
+int field_precondition_begin(fr_field* f, cudaStream_t s);
 }  // namespace frp

@@ -17,6 +17,13 @@
 //           traces (lamuo, global)
 //   adj_c : gathers the partners' lamuo, adds L^T of it, and applies the
 //           RK4 adjoint recurrence.
+// adj_b<.., 1> is the same for the preconditioning system of psi (Eq.
+// pseudotimesystem): R_p = -J^{-1} div~ g~ + S with g = -nu_s(psi) q, the
+// common flux n.g_L + tau_p (psi_L - psi_R) and S = tanh(psi0 / max(|q|,
+// delta)) (1 - |q|); besides the gradient path it carries the element
+// viscosity's dependence on psi (through the resolution indicator, Eqs.
+// resolutionIndicator and nu_s) and accumulates dR_p/dpsi0 (lam_psi0).  The
+// phi slot of the stage arrays is carried with zero weight.
 // For a stream-function velocity adj_b also stores, per solution and flux
 // point, the adjoint of the velocity there (lv); k_coef_acc contracts it with
 // the derivative of the velocity with respect to each coefficient, from a
@@ -43,6 +50,7 @@ struct AdjArgs {
   double* Lk;
   double c_lp, c_a;
   int first;
+  double* lam_psi0;     // preconditioning sweep: E x NU, += (dR_p/dpsi0)^T lam (adj_b<.., 1>)
 };
 
 template <int DIM, int N>
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(256) adj_a(const AdjArgs B) {
 }
 
 // ---------------------------------------------------------------------------
-template <int DIM, int N>
+template <int DIM, int N, int MODE = 0>
 __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   using S = TS<DIM, N>;
   using LY = AdjLayout<DIM, N>;
@@ -200,7 +208,8 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   const TensorOpsT<double>& O = BC.ops;
   const PrmT<double> P = BC.prm;
   const double g = time_factor(A, A.t);
-  const bool coef = B.want_coef && BC.vel.kind == 3 && DIM == 2;
+  const bool coef = MODE == 0 && B.want_coef && BC.vel.kind == 3 && DIM == 2;
+  __shared__ double nu_e[ET], dnu_e[ET], lnu_e[ET];  // MODE 1: nu_s, d nu_s / d s, lam of nu_s
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) us[idx] = ustg[e0 * 2 * NU + idx];
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = A.geo[e0 * NG + idx];
   __syncthreads();
@@ -274,6 +283,44 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
     }
   }
   __syncthreads();
+  if constexpr (MODE == 1) {
+    // forward sensor of the element (as kb_tensor<.., 1>): modal coefficients
+    // chi = V^-1 psi (tensor product), s = log10(top / all), nu_s(s)
+    for (int el = tid; el < ne; el += blockDim.x) {
+      const double* ps = us + (el * 2 + 1) * NU;
+      double tot = 0.0, hi = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        double c = 0.0;
+        for (int i = 0; i < NU; ++i) {
+          double v = 1.0;
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) v *= O.Vinv[ucoord<N>(m, b)][ucoord<N>(i, b)];
+          c += v * ps[i];
+        }
+        tot += c * c;
+        bool top = false;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) top = top || (ucoord<N>(m, b) == N - 1);
+        if (top) hi += c * c;
+      }
+      double nu = 0.0, dnu = 0.0;
+      if (tot > 0.0 && hi > 0.0) {
+        const double se = log10(hi / tot);
+        const double lo = A.prm.s0 - A.prm.kappa, up = A.prm.s0 + A.prm.kappa;
+        const double nmax = A.prm.nu_max, w = M_PI / (2.0 * A.prm.kappa);
+        if (se > up) {
+          nu = nmax;
+        } else if (se >= lo) {
+          nu = 0.5 * nmax * (1.0 + sin(w * (se - A.prm.s0)));
+          dnu = 0.5 * nmax * w * cos(w * (se - A.prm.s0));
+        }
+      }
+      nu_e[el] = nu;
+      dnu_e[el] = dnu;
+      lnu_e[el] = 0.0;
+    }
+    __syncthreads();
+  }
 
   // ---- reverse of Step 6 by axis: lam_f~ from the derivative and the lifts
 #pragma unroll
@@ -303,6 +350,98 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
   }
   __syncthreads();
 
+  if constexpr (MODE == 1) {
+    // ---- reverse of Step 4 and of the source at solution points (psi slot)
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      double xi[3], Sm[3][3];
+      upt_xi<DIM, N>(i, O.x, xi);
+      metric<DIM>(gs + el * NG, xi, Sm);
+      double q[3], lg[3], q2 = 0.0, lnu = 0.0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        q[c] = qt[((el * 2 + 1) * DIM + c) * NU + i];
+        q2 += q[c] * q[c];
+      }
+      // lam_g = S^T lam_g~ with g~ = S g, g = -nu q
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        double sc = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sc += Sm[a][c] * lf[((el * 2 + 1) * DIM + a) * NU + i];
+        lg[c] = sc;
+        lnu -= sc * q[c];
+      }
+      // source S = tanh(psi0 / m)(1 - |q|), m = max(|q|, delta), weight lam_src
+      const double lsrc = B.lam_scale * B.lamk[((e0 + el) * 2 + 1) * NU + i];
+      const double qm = sqrt(q2), m = fmax(qm, P.delta);
+      const double p0 = A.psi0[(e0 + el) * NU + i];
+      const double t = tanh(p0 / m), sech2 = 1.0 - t * t;
+      const double dq = qm > 0.0 ? (-t - (qm > P.delta ? (1.0 - qm) * sech2 * p0 / (m * m) : 0.0)) / qm : 0.0;
+      const double nu = nu_e[el];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        lf[((el * 2 + 1) * DIM + c) * NU + i] = -nu * lg[c] + lsrc * dq * q[c];
+        lf[((el * 2 + 0) * DIM + c) * NU + i] = 0.0;
+      }
+      B.lam_psi0[(e0 + el) * NU + i] += lsrc * (1.0 - qm) * sech2 / m;
+      us[(el * 2 + 0) * NU + i] = 0.0;  // lam_U (direct part): none
+      us[(el * 2 + 1) * NU + i] = 0.0;
+      atomicAdd(&lnu_e[el], lnu);
+    }
+    // ---- reverse of Step 5 at L flux points (psi slot)
+    for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+      const int el = idx / NF, k = idx % NF;
+#pragma unroll
+      for (int fld = 0; fld < 2; ++fld) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) lqf[((el * 2 + fld) * DIM + c) * NF + k] = 0.0;
+        luf[(el * 2 + fld) * NF + k] = 0.0;
+        luo[(el * 2 + fld) * NF + k] = 0.0;
+      }
+      if (!lm[el * NF + k]) continue;
+      const int64_t gk = (e0 + el) * NF + k;
+      const int64_t pg = (int64_t)partner<NF>(A, A.fnbr[gk], (int32_t)gk);
+      const bool bnd = pg == gk;
+      int a, s, b0;
+      fline<DIM, N>(k, a, s, b0);
+      double xi[3], Sm[3][3];
+      fpt_xi<DIM, N>(k, O.x, xi);
+      metric<DIM>(gs + el * NG, xi, Sm);
+      double pn[3], pm = 0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        double sac = Sm[0][c];
+#pragma unroll
+        for (int b = 1; b < DIM; ++b)
+          if (b == a) sac = Sm[b][c];
+        pn[c] = (s ? 1.0 : -1.0) * sac;
+        pm += pn[c] * pn[c];
+      }
+      pm = sqrt(pm);
+      const int st = ipow(N, a);
+      double gn = 0.0, nh[3];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        nh[c] = pn[c] / pm;
+        const double* ql = qt + ((el * 2 + 1) * DIM + c) * NU + b0;
+        double acc = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc += (s ? O.lend[1][j] : O.lend[0][j]) * ql[j * st];
+        gn += nh[c] * acc;
+      }
+      // F~ = pm (-nu n.q_f + tau_p (psi_L - psi_R)) enters this side's lift
+      // and (negated) the partner's
+      const double y = B.Y[((e0 + el) * 2 + 1) * NF + k];
+      const double lF = pm * (bnd ? y : y - B.Y[((pg / NF) * 2 + 1) * NF + pg % NF]);
+      const double nu = nu_e[el];
+      luf[(el * 2 + 1) * NF + k] = lF * P.tau_pseudo;
+      luo[(el * 2 + 1) * NF + k] = -lF * P.tau_pseudo;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) lqf[((el * 2 + 1) * DIM + c) * NF + k] = -lF * nu * nh[c];
+      atomicAdd(&lnu_e[el], -lF * gn);
+    }
+  } else {
   // ---- reverse of Step 4 at solution points ---------------------------------
   for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
     const int el = idx / NU, i = idx % NU;
@@ -496,6 +635,7 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
       o[1] = lvv[1];
     }
   }
+  }
   __syncthreads();
 
   // ---- lam_q += L^T lam_qf, one pass per axis ------------------------------
@@ -576,6 +716,56 @@ __global__ void __launch_bounds__(256) adj_b(const AdjArgs B) {
           o[m * st] += acc;
         }
       }
+    }
+    __syncthreads();
+  }
+  if constexpr (MODE == 1) {
+    // the element viscosity's dependence on psi: lam_psi += lam_nu dnu/ds
+    // ds/dchi V^-1, with ds/dchi_m = 2 chi_m (top_m / hi - 1 / tot) / ln 10;
+    // chi (slot 0) and ds/dchi (slot 1) in the lam_div region, free by now
+    const double* psg = reinterpret_cast<const double*>(A.ustg);
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, m = idx % NU;
+      double c = 0.0;
+      for (int j = 0; j < NU; ++j) {
+        double v = 1.0;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) v *= O.Vinv[ucoord<N>(m, b)][ucoord<N>(j, b)];
+        c += v * psg[((e0 + el) * 2 + 1) * NU + j];
+      }
+      ld[(el * 2 + 0) * NU + m] = c;
+    }
+    __syncthreads();
+    for (int el = tid; el < ne; el += blockDim.x) {
+      double tot = 0.0, hi = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        const double c = ld[(el * 2 + 0) * NU + m];
+        bool top = false;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) top = top || (ucoord<N>(m, b) == N - 1);
+        tot += c * c;
+        if (top) hi += c * c;
+      }
+      const double w = lnu_e[el] * dnu_e[el];
+      for (int m = 0; m < NU; ++m) {
+        bool top = false;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) top = top || (ucoord<N>(m, b) == N - 1);
+        const double c = ld[(el * 2 + 0) * NU + m];
+        ld[(el * 2 + 1) * NU + m] = w == 0.0 ? 0.0 : w * 2.0 * c * ((top ? 1.0 / hi : 0.0) - 1.0 / tot) / M_LN10;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      double acc = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        double v = 1.0;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) v *= O.Vinv[ucoord<N>(m, b)][ucoord<N>(i, b)];
+        acc += ld[(el * 2 + 1) * NU + m] * v;
+      }
+      us[(el * 2 + 1) * NU + i] += acc;
     }
     __syncthreads();
   }
