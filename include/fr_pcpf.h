@@ -278,7 +278,8 @@ int fr_mass_integral(fr_field* field, int which, double* out_host, void* stream)
  * then the block partials in index order), so the result is deterministic
  * for a given n and agrees with fr_mass_integral to about 1e-13 relative
  * (the two summation orders differ).  The result is written to *out_host:
- * the call waits for the stream (cudaStreamSynchronize) before returning.
+ * the call waits for the stream (cudaStreamSynchronize) before returning,
+ * so it must not be called while that stream is being captured into a graph.
  * Pass u = one field from fr_field_get_device and w = fr_mesh_quadrature
  * copied to the device to compare with fr_mass_integral.
  *
@@ -378,8 +379,9 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  * The paper has no adjoint; these calls give the exact gradient of the FR
  * march's discrete map for a loss of the final state, with respect to the
  * initial fields and the stream-function coefficients (FR_VEL_STREAM).
- * Built for quadrilaterals (p <= 6) and hexahedra (p <= 3) in both
- * precisions; triangles return FR_EUNSUPPORTED.  On an FR_MIXED field the
+ * Built for quadrilaterals (p <= 6), hexahedra (p <= 3) and triangles
+ * (p <= 5) in both precisions (FR_ADJ_PRECONDITION: quadrilaterals and
+ * hexahedra).  On an FR_MIXED field the
  * recorded march is the field's own FP32 one (its float-float states are the
  * checkpoints); the sweep recomputes each segment in FP64 from its widened
  * checkpoint on FP64 shadow arrays in the workspace (a preconditioning in the
@@ -406,7 +408,8 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
  *   FR_EUNSUPPORTED for a field whose normal is FR_NORMAL_PHI (the adjoint
  *   covers the preconditioned method), and for FR_ADJ_PRECONDITION without
- *   pseudo_fixed (the stop rule's iteration count is not differentiated).
+ *   pseudo_fixed (the stop rule's iteration count is not differentiated) or
+ *   on triangles.
  * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
  *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,
  *   2 * n_dof: phi then psi) and, for a stream-function velocity,

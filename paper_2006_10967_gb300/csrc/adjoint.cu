@@ -38,6 +38,7 @@
 
 #include "field.cuh"
 #include "kadj.cuh"
+#include "kadj_tri.cuh"
 #include "kdispatch.hpp"
 
 using namespace frp;
@@ -97,7 +98,70 @@ AdjSet make_set() {
   return a;
 }
 
+// triangles (kadj_tri.cuh): no adjoint of the preconditioning (b1 null)
+template <typename K>
+void set_smem(K kern, size_t bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+template <int P>
+void la_tri(const AdjArgs& B, cudaStream_t s) {
+  using LY = AdjTriLayout<P>;
+  static bool init = false;
+  if (!init) {
+    set_smem(adj_a_tri<P>, LY::SMEM);
+    init = true;
+  }
+  adj_a_tri<P><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
+}
+template <int P>
+void lb_tri(const AdjArgs& B, cudaStream_t s) {
+  using LY = AdjTriLayout<P>;
+  static bool init = false;
+  if (!init) {
+    set_smem(adj_b_tri<P>, LY::SMEM);
+    init = true;
+  }
+  adj_b_tri<P><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
+}
+template <int P>
+void lc_tri(const AdjArgs& B, cudaStream_t s) {
+  using LY = AdjTriLayout<P>;
+  static bool init = false;
+  if (!init) {
+    set_smem(adj_c_tri<P>, LY::SMEM);
+    init = true;
+  }
+  adj_c_tri<P><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
+}
+template <int P>
+void ltab_tri(const KArgs& A, double* cs, cudaStream_t s) {
+  const int64_t n = A.E * (TriS<P>::NU + TriS<P>::NF);
+  const int64_t g = (n + 255) / 256;
+  k_coef_table_tri<P><<<(unsigned)(g < 152 * 16 ? g : 152 * 16), 256, 0, s>>>(A, cs);
+}
+template <int P>
+AdjSet make_set_tri() {
+  AdjSet a;
+  a.a = la_tri<P>;
+  a.b = lb_tri<P>;
+  a.c = lc_tri<P>;
+  a.b1 = nullptr;
+  a.tab = ltab_tri<P>;
+  a.et = AdjTriLayout<P>::ET;
+  return a;
+}
+
 bool adj_kernels(const fr_field* f, AdjSet* out) {
+  if (f->etype == FR_TRI) {
+    switch (f->order) {
+      case 1: *out = make_set_tri<1>(); return true;
+      case 2: *out = make_set_tri<2>(); return true;
+      case 3: *out = make_set_tri<3>(); return true;
+      case 4: *out = make_set_tri<4>(); return true;
+      case 5: *out = make_set_tri<5>(); return true;
+    }
+    return false;
+  }
   if (f->etype == FR_QUAD) {
     switch (f->order) {
       case 1: *out = make_set<2, 2>(); return true;
@@ -177,6 +241,7 @@ KArgs shadow_args(const fr_field* f, const AdjRecord& R) {
 bool fp64_kernels(const fr_field* f, KernelSet* ks) {
   if (f->etype == FR_QUAD) return kernels_quad(f->order, FR_FP64, f->E, 0, ks);
   if (f->etype == FR_HEX) return kernels_hex(f->order, FR_FP64, f->E, 0, ks);
+  if (f->etype == FR_TRI) return kernels_tri(f->order, FR_FP64, f->E, 0, ks);
   return false;
 }
 
@@ -258,8 +323,9 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, int f
                                  void* stream) {
   if (!f || !ws || n_steps < 1 || ckpt_every < 1 || (flags & ~FR_ADJ_PRECONDITION)) return FR_EINVAL;
   const bool pre = (flags & FR_ADJ_PRECONDITION) != 0;
-  // the preconditioning is differentiated for its fixed iteration count
-  if (pre && !f->prm.pseudo_fixed) return FR_EUNSUPPORTED;
+  // the preconditioning is differentiated for its fixed iteration count, on
+  // quads and hexes
+  if (pre && (!f->prm.pseudo_fixed || f->etype == FR_TRI)) return FR_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return FR_EINVAL;
   if (f->prm.normal != FR_NORMAL_PSI) return FR_EUNSUPPORTED;  // adjoint of the preconditioned method only
   if (f->prm.wall != FR_WALL_COPY) return FR_EUNSUPPORTED;     // and of the paper's copy-ghost walls
@@ -339,7 +405,7 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, int f
   if (mixed && !fp64_kernels(f, &ks64)) return FR_EUNSUPPORTED;
   const int64_t nv = 2 * f->E * f->nu;
   const int grid = (int)std::min<int64_t>((nv + 255) / 256, 152 * 16);
-  if (mixed) ks64.mconst(shadow_args(f, R), s);  // FP64 metric records of the shadow
+  if (mixed && ks64.mconst) ks64.mconst(shadow_args(f, R), s);  // FP64 metric records of the shadow
   if (pre) {
     // the t = 0 preconditioning, keeping every pseudo stage input (a mixed
     // field's FP32 preconditioning is re-run in FP64 from the same phi0)

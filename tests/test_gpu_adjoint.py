@@ -187,6 +187,42 @@ def test_preconditioned_mixed_adjoint_against_fp64(G):
     assert np.abs(c32 - c64).max() / np.abs(c64).max() < 1e-3
 
 
+@pytest.mark.parametrize("kind", ["delaunay_p3", "split_p2"])
+def test_triangle_adjoint_matches_oracle_adjoint(G, kind):
+    """Triangles (dense operators, one affine metric per element; the two
+    sides of an edge see different reference edges, so the adjoint of the
+    common flux weighs each side's lift adjoint by its own face scale):
+    gradient with respect to phi0 and the stream-function coefficients
+    against the oracle's reverse-mode adjoint, FP64 to round-off; the mixed
+    field (FP32 march, FP64 recomputation) against the FP64 gradient."""
+    if kind == "delaunay_p3":
+        w = _wl(lambda: S.tri_delaunay(5, seed=2, shuffle_seed=3), 3, 0.2, 4)
+    else:
+        w = _wl(lambda: S.tri_split(4, shuffle_seed=1), 2, 0.25, 4)
+    mesh = w.mesh()
+    prm = Params.from_workload(w)
+    sol = Solver(mesh, w.order, prm, w.velocity)
+    phi0 = circle_ic(sol.xu, w.circle).numpy()
+    phis = circle_ic(sol.xu, S.Circle((0.55, 0.45), 0.3, 6.0)).numpy()
+    n, ck = 5, 2
+    J, gphi, gc, F = _gpu_grad(G, w, mesh, phi0, phis, n, ck)
+    assert F.sync() == 0
+    Jo, gphio, gAo, gBo = loss_and_gradients(mesh, w.order, prm, w.velocity, phi0, phis, n)
+    assert J == pytest.approx(Jo, rel=1e-12)
+    assert np.abs(gphi - gphio.numpy()).max() / np.abs(gphio.numpy()).max() < 1e-9
+    go = np.concatenate([gAo.numpy(), gBo.numpy()])
+    assert np.abs(gc - go).max() / np.abs(go).max() < 1e-9
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    Fm = G.Field(M, G.make_params(w, "mixed"), phi0=phi0, precondition=False)
+    Fm.adjoint_record(n, ck)
+    wq = M.quadrature()
+    du0, dc = Fm.adjoint_step(torch.from_numpy(wq * (Fm.get(0) - phis)).cuda(), None, len(go))
+    assert Fm.sync() == 0
+    g32 = (du0[0] + du0[1]).cpu().numpy()
+    assert np.abs(g32 - gphi).max() / np.abs(gphi).max() < 1e-4
+    assert np.abs(dc.cpu().numpy() - gc).max() / np.abs(gc).max() < 1e-4
+
+
 def test_adjoint_c5_against_central_differences(G):
     """The adjoint workload: 64^2 periodic quads, p = 4, 400 RK4 steps, velocity
     from 32 stream-function coefficients, checkpoints every 20 steps."""
