@@ -380,8 +380,7 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  * march's discrete map for a loss of the final state, with respect to the
  * initial fields and the stream-function coefficients (FR_VEL_STREAM).
  * Built for quadrilaterals (p <= 6), hexahedra (p <= 3) and triangles
- * (p <= 5) in both precisions (FR_ADJ_PRECONDITION: quadrilaterals and
- * hexahedra).  On an FR_MIXED field the
+ * (p <= 5) in both precisions.  On an FR_MIXED field the
  * recorded march is the field's own FP32 one (its float-float states are the
  * checkpoints); the sweep recomputes each segment in FP64 from its widened
  * checkpoint on FP64 shadow arrays in the workspace (a preconditioning in the
@@ -408,8 +407,7 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
  *   FR_EUNSUPPORTED for a field whose normal is FR_NORMAL_PHI (the adjoint
  *   covers the preconditioned method), and for FR_ADJ_PRECONDITION without
- *   pseudo_fixed (the stop rule's iteration count is not differentiated) or
- *   on triangles.
+ *   pseudo_fixed (the stop rule's iteration count is not differentiated).
  * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
  *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,
  *   2 * n_dof: phi then psi) and, for a stream-function velocity,

@@ -98,7 +98,7 @@ AdjSet make_set() {
   return a;
 }
 
-// triangles (kadj_tri.cuh): no adjoint of the preconditioning (b1 null)
+// triangles (kadj_tri.cuh)
 template <typename K>
 void set_smem(K kern, size_t bytes) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -113,15 +113,15 @@ void la_tri(const AdjArgs& B, cudaStream_t s) {
   }
   adj_a_tri<P><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
 }
-template <int P>
+template <int P, int MODE>
 void lb_tri(const AdjArgs& B, cudaStream_t s) {
   using LY = AdjTriLayout<P>;
   static bool init = false;
   if (!init) {
-    set_smem(adj_b_tri<P>, LY::SMEM);
+    set_smem(adj_b_tri<P, MODE>, LY::SMEM);
     init = true;
   }
-  adj_b_tri<P><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
+  adj_b_tri<P, MODE><<<(unsigned)((B.K.E + LY::ET - 1) / LY::ET), LY::THREADS, LY::SMEM, s>>>(B);
 }
 template <int P>
 void lc_tri(const AdjArgs& B, cudaStream_t s) {
@@ -143,9 +143,9 @@ template <int P>
 AdjSet make_set_tri() {
   AdjSet a;
   a.a = la_tri<P>;
-  a.b = lb_tri<P>;
+  a.b = lb_tri<P, 0>;
   a.c = lc_tri<P>;
-  a.b1 = nullptr;
+  a.b1 = lb_tri<P, 1>;
   a.tab = ltab_tri<P>;
   a.et = AdjTriLayout<P>::ET;
   return a;
@@ -323,9 +323,8 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, int f
                                  void* stream) {
   if (!f || !ws || n_steps < 1 || ckpt_every < 1 || (flags & ~FR_ADJ_PRECONDITION)) return FR_EINVAL;
   const bool pre = (flags & FR_ADJ_PRECONDITION) != 0;
-  // the preconditioning is differentiated for its fixed iteration count, on
-  // quads and hexes
-  if (pre && (!f->prm.pseudo_fixed || f->etype == FR_TRI)) return FR_EUNSUPPORTED;
+  // the preconditioning is differentiated for its fixed iteration count
+  if (pre && !f->prm.pseudo_fixed) return FR_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return FR_EINVAL;
   if (f->prm.normal != FR_NORMAL_PSI) return FR_EUNSUPPORTED;  // adjoint of the preconditioned method only
   if (f->prm.wall != FR_WALL_COPY) return FR_EUNSUPPORTED;     // and of the paper's copy-ghost walls

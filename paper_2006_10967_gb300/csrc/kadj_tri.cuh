@@ -14,7 +14,10 @@
 //   adj_c_tri : gathers the partners' lamuo, adds L^T of it, and applies the
 //               RK4 adjoint recurrence.
 // FP64 only; the velocity is evaluated analytically, as in the forward
-// triangle kernels.
+// triangle kernels.  adj_b_tri<P, 1> is the preconditioning system's
+// (Eq. pseudotimesystem), as adj_b<.., 1> of kadj.cuh: the flux -nu_s q, the
+// penalty, the source tanh(psi0 / |q|)(1 - |q|) and the element viscosity's
+// dependence on psi through the resolution indicator.
 #pragma once
 #include "kadj.cuh"
 #include "ktri.cuh"
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(256) adj_a_tri(const AdjArgs B) {
   }
 }
 
-template <int P>
+template <int P, int MODE = 0>
 __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
   using S = TriS<P>;
   using LY = AdjTriLayout<P>;
@@ -105,7 +108,8 @@ __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
   const BulkConst<double>& BC = A.cd;
   const PrmT<double> Pm = BC.prm;
   const double g = time_factor(A, A.t);
-  const bool coef = B.want_coef && BC.vel.kind == 3;
+  const bool coef = MODE == 0 && B.want_coef && BC.vel.kind == 3;
+  __shared__ double nu_e[ET], dnu_e[ET], lnu_e[ET];  // MODE 1: nu_s, d nu_s / d s, lam of nu_s
   load_tri_ops<P, double>(A.trid, op);
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) us[idx] = ustg[e0 * 2 * NU + idx];
   for (int idx = tid; idx < ne * NG; idx += blockDim.x) gs[idx] = A.geo[e0 * NG + idx];
@@ -158,6 +162,34 @@ __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
     }
   }
   __syncthreads();
+  if constexpr (MODE == 1) {
+    // forward sensor (as kb_tri<.., 1>): chi = V^-1 psi, s = log10(top / all)
+    for (int el = tid; el < ne; el += blockDim.x) {
+      double tot = 0.0, hi = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        double c = 0.0;
+        for (int j = 0; j < NU; ++j) c += op.Vinv[m][j] * us[(el * 2 + 1) * NU + j];
+        tot += c * c;
+        if (op.high[m]) hi += c * c;
+      }
+      double nu = 0.0, dnu = 0.0;
+      if (tot > 0.0 && hi > 0.0) {
+        const double se = log10(hi / tot);
+        const double lo = A.prm.s0 - A.prm.kappa, up = A.prm.s0 + A.prm.kappa;
+        const double w = M_PI / (2.0 * A.prm.kappa);
+        if (se > up) {
+          nu = A.prm.nu_max;
+        } else if (se >= lo) {
+          nu = 0.5 * A.prm.nu_max * (1.0 + sin(w * (se - A.prm.s0)));
+          dnu = 0.5 * A.prm.nu_max * w * cos(w * (se - A.prm.s0));
+        }
+      }
+      nu_e[el] = nu;
+      dnu_e[el] = dnu;
+      lnu_e[el] = 0.0;
+    }
+    __syncthreads();
+  }
   // ---- reverse of Step 6: lam_f~_a = D_a^T lam_div - L^T (n~_a Y)
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) {
     const int c = idx / NU, j = idx % NU;  // c = element-field column
@@ -176,6 +208,70 @@ __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
     lf[(c * 2 + 1) * NU + j] = a1;
   }
   __syncthreads();
+  if constexpr (MODE == 1) {
+    // ---- reverse of Step 4 and of the source (psi slot)
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, i = idx % NU;
+      const double* mt = met + el * 5;
+      double q1[2], lg[2], lnu = 0.0;
+      for (int c = 0; c < 2; ++c) q1[c] = q[((el * 2 + 1) * 2 + c) * NU + i];
+      // lam_g = S^T lam_g~ with g~_a = sum_c S[a][c] g_c, g = -nu q
+      for (int c = 0; c < 2; ++c) {
+        lg[c] = mt[0 * 2 + c] * lf[((el * 2 + 1) * 2 + 0) * NU + i] + mt[1 * 2 + c] * lf[((el * 2 + 1) * 2 + 1) * NU + i];
+        lnu -= lg[c] * q1[c];
+      }
+      const double lsrc = B.lam_scale * B.lamk[((e0 + el) * 2 + 1) * NU + i];
+      const double qm = sqrt(q1[0] * q1[0] + q1[1] * q1[1]), m = fmax(qm, Pm.delta);
+      const double p0 = A.psi0[(e0 + el) * NU + i];
+      const double t = tanh(p0 / m), sech2 = 1.0 - t * t;
+      const double dq = qm > 0.0 ? (-t - (qm > Pm.delta ? (1.0 - qm) * sech2 * p0 / (m * m) : 0.0)) / qm : 0.0;
+      const double nu = nu_e[el];
+      for (int c = 0; c < 2; ++c) {
+        lf[((el * 2 + 1) * 2 + c) * NU + i] = -nu * lg[c] + lsrc * dq * q1[c];
+        lf[((el * 2 + 0) * 2 + c) * NU + i] = 0.0;
+      }
+      B.lam_psi0[(e0 + el) * NU + i] += lsrc * (1.0 - qm) * sech2 / m;
+      us[(el * 2 + 0) * NU + i] = 0.0;
+      us[(el * 2 + 1) * NU + i] = 0.0;
+      atomicAdd(&lnu_e[el], lnu);
+    }
+    // ---- reverse of Step 5 at L flux points (psi slot)
+    for (int idx = tid; idx < ne * NF; idx += blockDim.x) {
+      const int el = idx / NF, k = idx % NF;
+      for (int fld = 0; fld < 2; ++fld) {
+        for (int c = 0; c < 2; ++c) lqf[((el * 2 + fld) * 2 + c) * NF + k] = 0.0;
+        luf[(el * 2 + fld) * NF + k] = 0.0;
+        luo[(el * 2 + fld) * NF + k] = 0.0;
+      }
+      if (!lm[el * NF + k]) continue;
+      const int32_t own = (int32_t)((e0 + el) * NF + k);
+      const int64_t pg = (int64_t)partner<NF>(A, A.fnbr[own], own);
+      const bool bnd = pg == own;
+      double nh[2];
+      const double pm = tri_normal(met + el * 5, op.nref[k], nh);
+      double pmR = pm;
+      if (!bnd) {
+        TriMet<double> mp;
+        tri_metric(A.geo + (pg / NF) * NG, mp);
+        const double mpv[4] = {mp.S[0][0], mp.S[0][1], mp.S[1][0], mp.S[1][1]};
+        double nr[2];
+        pmR = tri_normal(mpv, op.nref[pg % NF], nr);
+      }
+      double gn = 0.0;
+      for (int c = 0; c < 2; ++c) {
+        double a = 0.0;
+        for (int j = 0; j < NU; ++j) a += op.L[k][j] * q[((el * 2 + 1) * 2 + c) * NU + j];
+        gn += nh[c] * a;
+      }
+      const double y = B.Y[((e0 + el) * 2 + 1) * NF + k];
+      const double lF = bnd ? pm * y : pm * y - pmR * B.Y[((pg / NF) * 2 + 1) * NF + pg % NF];
+      const double nu = nu_e[el];
+      luf[(el * 2 + 1) * NF + k] = lF * Pm.tau_pseudo;
+      luo[(el * 2 + 1) * NF + k] = -lF * Pm.tau_pseudo;
+      for (int c = 0; c < 2; ++c) lqf[((el * 2 + 1) * 2 + c) * NF + k] = -lF * nu * nh[c];
+      atomicAdd(&lnu_e[el], -lF * gn);
+    }
+  } else {
   // ---- reverse of Step 4 at solution points
   for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
     const int el = idx / NU, i = idx % NU;
@@ -313,6 +409,7 @@ __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
         o[c] = lF[0] * (0.5 * (pL + pR) * nh[c] - fvn * v[c] * dM) + lF[1] * 0.5 * (sL + sR) * nh[c];
     }
   }
+  }
   __syncthreads();
   // ---- lam_q += L^T lam_qf, then lam_q~_a = sum_b S[a][b] lam_q_b / det J
   for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
@@ -341,6 +438,39 @@ __global__ void __launch_bounds__(256) adj_b_tri(const AdjArgs B) {
     luf[c * NF + k] -= lj;
   }
   __syncthreads();
+  if constexpr (MODE == 1) {
+    // the element viscosity's dependence on psi: lam_psi += lam_nu dnu/ds
+    // ds/dchi V^-1, ds/dchi_m = 2 chi_m (top_m / hi - 1 / tot) / ln 10; chi
+    // (slot 0) and the weights (slot 1) in the lam_div region, free by now
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, m = idx % NU;
+      double c = 0.0;
+      for (int j = 0; j < NU; ++j) c += op.Vinv[m][j] * ustg[((e0 + el) * 2 + 1) * NU + j];
+      ld[(el * 2 + 0) * NU + m] = c;
+    }
+    __syncthreads();
+    for (int el = tid; el < ne; el += blockDim.x) {
+      double tot = 0.0, hi = 0.0;
+      for (int m = 0; m < NU; ++m) {
+        const double c = ld[(el * 2 + 0) * NU + m];
+        tot += c * c;
+        if (op.high[m]) hi += c * c;
+      }
+      const double w = lnu_e[el] * dnu_e[el];
+      for (int m = 0; m < NU; ++m) {
+        const double c = ld[(el * 2 + 0) * NU + m];
+        ld[(el * 2 + 1) * NU + m] = w == 0.0 ? 0.0 : w * 2.0 * c * ((op.high[m] ? 1.0 / hi : 0.0) - 1.0 / tot) / M_LN10;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
+      const int el = idx / NU, j = idx % NU;
+      double a = 0.0;
+      for (int m = 0; m < NU; ++m) a += op.Vinv[m][j] * ld[(el * 2 + 1) * NU + m];
+      us[(el * 2 + 1) * NU + j] += a;
+    }
+    __syncthreads();
+  }
   // ---- reverse of Step 3's derivative and of Step 1: lam_U += D^T lam_q~ + L^T lam_uf
   for (int idx = tid; idx < ne * 2 * NU; idx += blockDim.x) {
     const int c = idx / NU, j = idx % NU;

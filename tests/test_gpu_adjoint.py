@@ -97,6 +97,8 @@ def test_adjoint_matches_oracle_adjoint(G, kind):
 def _small_case(kind):
     if kind == "quad":
         w = _wl(lambda: S.quad_grid(4, jitter=0.1, seed=3, shuffle_seed=1, rotate_seed=2), 3, 0.25, 4)
+    elif kind == "tri":
+        w = _wl(lambda: S.tri_delaunay(5, seed=2, shuffle_seed=3), 3, 0.2, 4)
     else:
         w = _wl(lambda: S.hex_grid(2, periodic=(True, True, True), jitter=0.05, seed=3), 2, 0.5, 4)
         w.velocity = S.Velocity("leveque", T=3.0)
@@ -104,7 +106,7 @@ def _small_case(kind):
     return w
 
 
-@pytest.mark.parametrize("kind", ["quad", "hex"])
+@pytest.mark.parametrize("kind", ["quad", "tri", "hex"])
 def test_preconditioned_adjoint_matches_oracle_adjoint(G, kind):
     """With the t = 0 preconditioning inside the window (psi0 = psi =
     phi0 - 1/2, then a fixed count of pseudo-time RK4 iterations): the
@@ -139,7 +141,8 @@ def test_preconditioned_adjoint_matches_oracle_adjoint(G, kind):
     assert float(nu.max()) > 0.0
     phi0t = torch.tensor(phi0, requires_grad=True)
     s2 = Solver(mesh, w.order, prm, w.velocity)
-    if kind == "quad":
+    stream = w.velocity.kind == "stream"
+    if stream:
         A = torch.as_tensor(w.velocity.A, dtype=torch.float64).clone().requires_grad_(True)
         B = torch.as_tensor(w.velocity.B, dtype=torch.float64).clone().requires_grad_(True)
     else:
@@ -149,7 +152,7 @@ def test_preconditioned_adjoint_matches_oracle_adjoint(G, kind):
         s2.rk4_step(A, B)
     Jt = 0.5 * s2.integral((s2.phi - torch.tensor(phis)) ** 2)
     assert J == pytest.approx(float(Jt.detach()), rel=1e-12)
-    if kind == "quad":
+    if stream:
         go, gA, gB = torch.autograd.grad(Jt, (phi0t, A, B))
         gco = np.concatenate([gA.numpy(), gB.numpy()])
         assert np.abs(dc.cpu().numpy() - gco).max() / np.abs(gco).max() < 1e-9
