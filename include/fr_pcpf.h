@@ -137,9 +137,9 @@ typedef struct fr_params {
   double delta;          /* guard: |grad psi| -> max(|grad psi|, delta) */
   fr_velocity vel;
   int32_t vel_cache;     /* 1: store the time-independent factor v(x) of u(x,t) = g(t) v(x)
-                            at every solution and flux point at init (quad/hex; dim x (nu+nf)
-                            values per element in the stage precision) instead of evaluating
-                            v(x) every stage; 0: evaluate in the kernels */
+                            at every solution and flux point at init (evaluated in FP64;
+                            dim x (nu+nf) values per element in the stage precision) instead
+                            of evaluating v(x) every stage; 0: evaluate in the kernels */
   int32_t normal;        /* interface normal of the sharpening term: FR_NORMAL_PSI (the
                             preconditioned method, n = grad psi/|grad psi|, Section 2) or
                             FR_NORMAL_PHI (the unpreconditioned conservative phase field,

@@ -129,7 +129,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   L.fc = take(E * 2 * NF * tb);
   L.psi0 = take(E * NU * sizeof(double));
   L.xfer = take(E * NU * sizeof(double));
-  const bool vc = vel_cache && m.etype != FR_TRI;
+  const bool vc = vel_cache;
   L.vsu = vc ? take(E * m.dim * NU * tb) : 0;
   L.vsf = vc ? take(E * m.dim * NF * tb) : 0;
   L.tacc = take(E * 2 * sizeof(double));

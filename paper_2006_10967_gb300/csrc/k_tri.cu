@@ -24,9 +24,15 @@ bool prepare_tri() {
                               (int)KATriLayout<P, T, MODE, TC>::SMEM) == cudaSuccess;
 }
 
+template <int P, typename T>
+void launch_vcache_tri(const KArgs& A, cudaStream_t s) {
+  k_vel_cache_tri<P, T><<<152 * 8, kThreads, 0, s>>>(A);
+}
+
 template <int P, typename T, bool TC>
 void fill_tri(int64_t E, KernelSet* ks) {
   ks->prepared = prepare_tri<P, T, 0, TC>() && prepare_tri<P, T, 1, TC>();
+  ks->vcache = launch_vcache_tri<P, T>;
   ks->kb[0] = launch_kb_tri<P, T, 0, TC>;
   ks->kb[1] = launch_kb_tri<P, T, 1, TC>;
   ks->ka[0] = launch_ka_tri<P, T, 0, TC>;

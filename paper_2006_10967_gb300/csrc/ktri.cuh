@@ -289,9 +289,16 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
             qfv[fld][c] = acc;
           }
         }
-      T x[3], v[3];
-      map_point<ET_TRI, T>(gs + el * NG, op.xf[k], x);
-      velocity<2, T>(BC.vel, x, gfac, v);
+      T v[3];
+      if (A.vsf) {  // the velocity cache: v(x) at the flux point, evaluated in FP64
+        const T* vc = reinterpret_cast<const T*>(A.vsf) + (e0 + el) * 2 * NF + k;
+        v[0] = gfac * vc[0];
+        v[1] = gfac * vc[NF];
+      } else {
+        T x[3];
+        map_point<ET_TRI, T>(gs + el * NG, op.xf[k], x);
+        velocity<2, T>(BC.vel, x, gfac, v);
+      }
       const T vn = v[0] * nh[0] + v[1] * nh[1];
       const T M = fmax(sqrt_(v[0] * v[0] + v[1] * v[1]), Pm.gamma);
       const int kn = Pm.nphi ? 0 : 1;  // field whose gradient gives the interface normal
@@ -335,12 +342,19 @@ __global__ void __launch_bounds__(kThreads) kb_tri(const KArgs A) {
     const int el = idx / NU, i = idx % NU;
     const T* mt = met + el * 5;
     if (MODE == 0) {
-      T xi[2], x[3], v[3];
-      const T* xr = tri_of<T>(A).xu + 2 * i;  // solution point i in the reference triangle
-      xi[0] = xr[0];
-      xi[1] = xr[1];
-      map_point<ET_TRI, T>(gs + el * NG, xi, x);
-      velocity<2, T>(BC.vel, x, gfac, v);
+      T v[3];
+      if (A.vsu) {  // the velocity cache: v(x) at the solution point, evaluated in FP64
+        const T* vc = reinterpret_cast<const T*>(A.vsu) + (e0 + el) * 2 * NU + i;
+        v[0] = gfac * vc[0];
+        v[1] = gfac * vc[NU];
+      } else {
+        T xi[2], x[3];
+        const T* xr = tri_of<T>(A).xu + 2 * i;  // solution point i in the reference triangle
+        xi[0] = xr[0];
+        xi[1] = xr[1];
+        map_point<ET_TRI, T>(gs + el * NG, xi, x);
+        velocity<2, T>(BC.vel, x, gfac, v);
+      }
       const T qp0 = q[((el * 2 + 0) * 2 + 0) * NU + i], qp1 = q[((el * 2 + 0) * 2 + 1) * NU + i];
       const int kn = Pm.nphi ? 0 : 1;  // field whose gradient gives the interface normal
       const T qs0 = q[((el * 2 + kn) * 2 + 0) * NU + i], qs1 = q[((el * 2 + kn) * 2 + 1) * NU + i];
@@ -630,6 +644,35 @@ __global__ void __launch_bounds__(kThreads) ka_tri(const KArgs A) {
   if (MODE == 0 && stage == 4 && A.use_dev_time && blockIdx.x == 0 && tid == 0)
     A.dstate[DS_TIME] = A.dstate[DS_TIME] + A.dt;
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
+}
+
+// Spatial velocity factor v(x) (g = 1) at the solution and flux points of
+// every triangle, evaluated once in double (exact zeros where the analytic
+// field vanishes, as on the walls of the benchmark flows) and stored in the
+// bulk type: vsu [E][2][NU], vsf [E][2][NF].
+template <int P, typename T>
+__global__ void k_vel_cache_tri(const KArgs A) {
+  using S = TriS<P>;
+  constexpr int NU = S::NU, NF = S::NF, NG = S::NG;
+  const int64_t n = A.E * (NU + NF);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / (NU + NF);
+    const int r = (int)(g % (NU + NF));
+    const double* xr = r < NU ? A.trid.xu + 2 * r : A.trid.xf + 2 * (r - NU);
+    const double xi[2] = {xr[0], xr[1]};
+    double x[3], v[3];
+    map_point<ET_TRI, double>(A.geo + e * NG, xi, x);
+    velocity<2, double>(A.cd.vel, x, 1.0, v);
+    if (r < NU) {
+      T* o = reinterpret_cast<T*>(const_cast<void*>(A.vsu)) + e * 2 * NU + r;
+      o[0] = (T)v[0];
+      o[NU] = (T)v[1];
+    } else {
+      T* o = reinterpret_cast<T*>(const_cast<void*>(A.vsf)) + e * 2 * NF + (r - NU);
+      o[0] = (T)v[0];
+      o[NF] = (T)v[1];
+    }
+  }
 }
 
 }  // namespace frp

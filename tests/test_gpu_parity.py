@@ -124,8 +124,8 @@ def test_rhs_parity_fp64(G, case):
         assert _rel(R[1], Ro[1].numpy()) < TOL64, case
 
 
-@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_stream_p5", "hex_periodic_jitter_p2",
-                                  "hex_periodic_jitter_p3"])
+@pytest.mark.parametrize("case", ["quad_walls_jitter_p4", "quad_stream_p5", "tri_delaunay_p3", "tri_split_periodic_p2",
+                                  "hex_periodic_jitter_p2", "hex_periodic_jitter_p3"])
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
 def test_rhs_parity_velocity_evaluated_in_kernel(G, case, precision, tol):
     """The same residual with the velocity evaluated in the kernels instead of
