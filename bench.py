@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-vel-cache", action="store_true", help="evaluate the velocity in the kernels")
     ap.add_argument("--normal", default="psi", choices=["psi", "phi"],
                     help="interface normal: psi (preconditioned method) or phi (unpreconditioned CPF)")
+    ap.add_argument("--wall", default=None, choices=["copy", "noflux"],
+                    help="wall faces: the workload's own (copy ghost, Section 3.3) or zero normal flux")
     ap.add_argument("--order", type=int, default=None,
                     help="zalesak/rudman: polynomial order (default 4); c2s: (default 3)")
     ap.add_argument("--workload", default="c3", choices=["c2q", "c2t", "c2s", "c3", "c4", "zalesak", "rudman"],
@@ -592,6 +594,10 @@ def main():
     w.normal = args.normal
     if args.normal == "phi":
         wname += "_unpreconditioned"
+    if args.wall:
+        w.wall = args.wall
+        if args.wall == "noflux":
+            wname += "_noflux_walls"
     mesh = w.mesh()
     workload_cfg = workload_config(w, wname, mesh, args.normal, world)
     workload_cfg["rk_steps_per_step"] = args.rk_steps
@@ -602,6 +608,8 @@ def main():
     if cpu_n is not None:
         w_cpu, cpu_name = select_workload(S, args.workload, cpu_n, args.order)
         w_cpu.normal = args.normal
+        if args.wall:
+            w_cpu.wall = args.wall
         cpu_note = f"the same problem on a {cpu_n}^3 sub-grid ({cpu_name}, {cpu_n ** 3} elements)"
     else:
         w_cpu, cpu_note = w, f"the full workload ({wname})"
