@@ -406,7 +406,8 @@ int fr_rhs_pseudo(fr_field* field, double* dev_out, void* stream);
  *   keeping checkpoints in `workspace` (device, caller-owned, 256-byte
  *   aligned, >= the bytes above; it must live until fr_adjoint_step returns).
  *   FR_EUNSUPPORTED for a field whose normal is FR_NORMAL_PHI (the adjoint
- *   covers the preconditioned method), and for FR_ADJ_PRECONDITION without
+ *   covers the preconditioned method), for no-flux walls, for batch fields
+ *   (fr_field_init_batch: per-instance time steps), and for FR_ADJ_PRECONDITION without
  *   pseudo_fixed (the stop rule's iteration count is not differentiated).
  * fr_adjoint_step: given dJ/dphi(T) (device, n_dof) and optionally dJ/dpsi(T)
  *   (device, n_dof, or NULL for zero), write dJ/du(t0) to dJ_du0 (device,

@@ -328,6 +328,7 @@ extern "C" int fr_adjoint_record(fr_field* f, int n_steps, int ckpt_every, int f
   if (reinterpret_cast<uintptr_t>(ws) % 256) return FR_EINVAL;
   if (f->prm.normal != FR_NORMAL_PSI) return FR_EUNSUPPORTED;  // adjoint of the preconditioned method only
   if (f->prm.wall != FR_WALL_COPY) return FR_EUNSUPPORTED;     // and of the paper's copy-ghost walls
+  if (f->args.ep) return FR_EUNSUPPORTED;                       // one uniform time step (no batch fields)
   AdjSet as;
   if (!adj_kernels(f, &as)) return FR_EUNSUPPORTED;
   const int nb = (int)((f->E + as.et - 1) / as.et);

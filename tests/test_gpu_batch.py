@@ -59,6 +59,18 @@ def test_batch_matches_independent_oracle_runs(G, precision, tol):
         assert np.abs(psi[b:e] - refp).max() / np.abs(refp).max() < tol
 
 
+def test_batch_fields_have_no_adjoint(G):
+    """The adjoint assumes one uniform time step: a batch field (per-instance
+    steps) is rejected with FR_EUNSUPPORTED, before any work."""
+    ws = _instances(2, [3, 4], seed=5)
+    (p, F, ranges), = G.batch_from_workloads(ws, precision="fp64", pseudo_fixed=True)
+    with pytest.raises(G.FRError) as e:
+        F.adjoint_record(2, 1)
+    assert e.value.code == -6
+    F.step(1)
+    assert F.sync() == 0
+
+
 def test_ensemble_workload_builds_and_steps(G):
     """The 256-instance ensemble recipe, subsampled: one batch per order."""
     ws = S.ensemble_instances(16, seed=3)
