@@ -2,10 +2,10 @@
 from the connectivity is checked on the device before use, and an index out
 of range ends the run with FR_EBOUNDS instead of an access outside the
 arrays) runs the GPU parity suites with no check firing: the residual, RK4,
-preconditioning, tile-variant, batch and adjoint parity tests pass on it, and
-every field they create is destroyed with a status free of FR_EBOUNDS (the
-package reads it at destruction under FRP_BOUNDS_CHECK=1; the tests'
-conftest fails the test otherwise)."""
+preconditioning, tile-variant, batch, partitioned-march and adjoint parity
+tests pass on it, and every field they create is destroyed with a status
+free of FR_EBOUNDS (the package reads it at destruction under
+FRP_BOUNDS_CHECK=1; the tests' conftest fails the test otherwise)."""
 import os
 import subprocess
 import sys
@@ -20,6 +20,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     ("tests/test_gpu_parity.py", "rhs_parity or march or pseudo or tile_variants or noflux"),
     ("tests/test_gpu_adjoint.py", ""),
     ("tests/test_gpu_batch.py", ""),
+    ("tests/test_gpu_partition.py", ""),
 ])
 def test_parity_suites_pass_on_the_bounds_checked_build(suite, select):
     from paper_2006_10967_gb300 import build
