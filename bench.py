@@ -184,7 +184,9 @@ def alg_bytes_per_dof(etype, p, precision):
 
 def source_sha():
     h = hashlib.sha256()
-    for fn in ("ktensor.cuh", "kcommon.cuh", "geom.cuh"):
+    # the tensor kernels, their launch table and the field set-up that lays
+    # out the arrays they read
+    for fn in ("ktensor.cuh", "kcommon.cuh", "geom.cuh", "k_tensor_inst.cuh", "api.cu"):
         h.update(open(os.path.join(ROOT, "paper_2006_10967_gb300", "csrc", fn), "rb").read())
     return h.hexdigest()[:16]
 

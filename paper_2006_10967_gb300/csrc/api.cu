@@ -21,6 +21,7 @@ struct Layout {
   size_t status, dstate, red, geo, geof, fnbr, wdet, ustg, u, acc, rp, tr, fc, psi0, xfer, vsu, vsf, tacc, wdetf, ep, mcg;
   size_t tri_d, tri_f, tri_high;  // dense triangle operators (double, float), mode mask
   size_t wphys;                   // triangles: physical edge quadrature weight per flux point (float-float)
+  size_t ffw;                     // hexahedra: face words (KArgs.ffw)
   size_t total;
 };
 
@@ -136,6 +137,7 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   L.wdetf = take(E * NU * 2 * sizeof(float));
   L.ep = take(E * sizeof(ElemPar));
   L.mcg = m.etype != FR_TRI ? take(E * kMetricRec * tb) : 0;  // per-element metric records
+  L.ffw = m.etype == FR_HEX ? take(E * 6 * sizeof(int2)) : 0;
   if (m.etype == FR_TRI) {
     const size_t nops = tri_op_count(m);
     L.tri_d = take(nops * sizeof(double));
@@ -145,6 +147,42 @@ Layout make_layout(const fr_mesh& m, int precision, int max_blocks, int vel_cach
   }
   L.total = off;
   return L;
+}
+
+// Hexahedra: the face words of KArgs.ffw (see face_link), derived from the
+// per-point connectivity.  FR_EINVAL if the points of a face do not all meet
+// one face of one partner, or meet it in an order that is not one of the
+// eight symmetries of the face's point grid (face_perm).
+int hex_face_words(const fr_mesh& m, std::vector<int32_t>& w) {
+  const int N = m.n, NFP = m.nfp, NF = m.nf, NFC = m.nfaces;
+  w.assign((size_t)m.E * NFC * 2, 0);
+  for (int64_t e = 0; e < m.E; ++e)
+    for (int f = 0; f < NFC; ++f) {
+      const int64_t base = e * NF + (int64_t)f * NFP;
+      const int32_t w0 = m.fnbr[base];
+      const int64_t p0 = w0 >> 1;
+      const int64_t pe = p0 / NF;
+      const int pf = (int)((p0 % NF) / NFP);
+      const int32_t isL = w0 & 1;
+      const bool wall = p0 == base;
+      int found = -1;
+      for (int o = 0; o < 8 && found < 0; ++o) {
+        bool ok = true;
+        for (int q = 0; q < NFP && ok; ++q) {
+          const int64_t p = pe * NF + (int64_t)pf * NFP + face_perm(o, q % N, q / N, N);
+          ok = m.fnbr[base + q] == (int32_t)((p << 1) | isL);
+        }
+        if (ok) found = o;
+      }
+      if (found < 0 || (wall && found != 0)) return FR_EINVAL;
+      const int c0 = face_perm(found, 0, 0, N);
+      const int ci = face_perm(found, 1, 0, N) - c0, cj = face_perm(found, 0, 1, N) - c0;
+      for (int q = 0; q < NFP; ++q)  // face_perm is affine in (i, j) for a fixed o
+        if (c0 + ci * (q % N) + cj * (q / N) != face_perm(found, q % N, q / N, N)) return FR_EINVAL;
+      w[(e * NFC + f) * 2] = (int32_t)(pe * 2 * NF + (int64_t)pf * NFP + c0);
+      w[(e * NFC + f) * 2 + 1] = (isL ? kFwL : 0) | (wall ? kFwWall : 0) | ((ci & 0x3FF) << 2) | ((cj & 0x3FF) << 12);
+    }
+  return FR_OK;
 }
 
 bool get_kernels(const fr_mesh& m, int precision, int variant, KernelSet* ks) {
@@ -547,6 +585,11 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   }
   for (int64_t g = 0; g < ndof; ++g)
     if (!std::isfinite(phi[g])) return FR_ENONFINITE;
+  std::vector<int32_t> ffw;
+  if (L.ffw) {
+    rc = hex_face_words(*m, ffw);
+    if (rc != FR_OK) return rc;
+  }
 
   fr_field* f = new (std::nothrow) fr_field();
   if (!f) return FR_ENOMEM;
@@ -570,6 +613,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   A.geo = reinterpret_cast<const double*>(b + L.geo);
   A.geof = reinterpret_cast<const float*>(b + L.geof);
   A.fnbr = reinterpret_cast<const int32_t*>(b + L.fnbr);
+  A.ffw = L.ffw ? reinterpret_cast<const int2*>(b + L.ffw) : nullptr;
   A.wdet = reinterpret_cast<const double*>(b + L.wdet);
   A.ustg = b + L.ustg;
   A.u = reinterpret_cast<double*>(b + L.u);
@@ -617,6 +661,7 @@ extern "C" int fr_field_init(const fr_mesh* m, const fr_params* prm, const fr_ic
   };
   up(L.geo, m->geo.data(), m->geo.size() * sizeof(double));
   up(L.fnbr, m->fnbr.data(), m->fnbr.size() * sizeof(int32_t));
+  if (L.ffw) up(L.ffw, ffw.data(), ffw.size() * sizeof(int32_t));
   up(L.wdet, m->wdet.data(), m->wdet.size() * sizeof(double));
   std::vector<float> wdetf(m->wdet.size() * 2);
   for (size_t g = 0; g < m->wdet.size(); ++g) {

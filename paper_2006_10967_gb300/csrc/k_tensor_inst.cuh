@@ -14,7 +14,22 @@ void launch_kb_tensor(const KArgs& A, cudaStream_t s) {
 template <int DIM, int N, typename T, int MODE, int TD = 1>
 void launch_ka_tensor(const KArgs& A, cudaStream_t s) {
   using LY = KALayout<DIM, N, T, MODE, TD>;
+  if constexpr (StageKA<DIM, T, MODE>::v) {
+    switch (A.stage) {
+      case 1: launch_kernel(ka_tensor<DIM, N, T, MODE, TD, 1>, LY::SMEM, LY::ET, A, s, LY::THREADS); return;
+      case 2: launch_kernel(ka_tensor<DIM, N, T, MODE, TD, 2>, LY::SMEM, LY::ET, A, s, LY::THREADS); return;
+      case 3: launch_kernel(ka_tensor<DIM, N, T, MODE, TD, 3>, LY::SMEM, LY::ET, A, s, LY::THREADS); return;
+      case 4: launch_kernel(ka_tensor<DIM, N, T, MODE, TD, 4>, LY::SMEM, LY::ET, A, s, LY::THREADS); return;
+      default: break;
+    }
+  }
   launch_kernel(ka_tensor<DIM, N, T, MODE, TD>, LY::SMEM, LY::ET, A, s, LY::THREADS);
+}
+
+template <int DIM, int N, typename T, int MODE, int TD, int SF>
+bool prepare_ka() {
+  return cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE, TD, SF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)KALayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess;
 }
 
 template <int DIM, int N, typename T>
@@ -32,10 +47,13 @@ void launch_vcache(const KArgs& A, cudaStream_t s) {
 // filled, so that no launch (and no graph capture) has to do it.
 template <int DIM, int N, typename T, int MODE, int TD = 1>
 bool prepare_tensor() {
-  return cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)KBLayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(ka_tensor<DIM, N, T, MODE, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)KALayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess;
+  bool ok = cudaFuncSetAttribute(kb_tensor<DIM, N, T, MODE, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)KBLayout<DIM, N, T, MODE, TD>::SMEM) == cudaSuccess &&
+            prepare_ka<DIM, N, T, MODE, TD, -2>();
+  if constexpr (StageKA<DIM, T, MODE>::v)
+    ok = ok && prepare_ka<DIM, N, T, MODE, TD, 1>() && prepare_ka<DIM, N, T, MODE, TD, 2>() &&
+         prepare_ka<DIM, N, T, MODE, TD, 3>() && prepare_ka<DIM, N, T, MODE, TD, 4>();
+  return ok;
 }
 
 // TB, TA: the tile divisors of the physical-step residual and update

@@ -108,6 +108,7 @@ struct KArgs {
   const double* geo;     // E x dim x ncoef (fp64)
   const float* geof;     // E x dim x ncoef (fp32 copy for the mixed path)
   const int32_t* fnbr;   // E x nf
+  const int2* ffw;       // hexahedra: E x 6 face words (face_link), or nullptr
   void* ustg;            // T   E x 2 x nu  stage input
   double* u;             // E x 2 x nu     solution (RK base)
   double* acc;           // E x 2 x nu     RK accumulator
@@ -160,6 +161,52 @@ __device__ __forceinline__ int32_t partner(const KArgs& A, int32_t w, int32_t ow
   (void)own;
 #endif
   return p;
+}
+
+// Hexahedra carry one word pair per face (KArgs.ffw) in place of one
+// connectivity word per flux point.  Face point (i, j) (the line index
+// i + N j of the two other axes, lowest fastest) meets the partner's face
+// point face_perm(o, i, j) for one orientation o of the shared face: o & 4
+// exchanges i and j, then o & 1 reverses the first index and o & 2 the
+// second; the eight values of o are the eight symmetries of the N x N point
+// grid of a face.  That index is affine in (i, j), c0 + ci i + cj j with
+// ci, cj in {+-1, +-N}, so the word pair stores x = the offset of the
+// partner's point (0, 0)-image in an E x 2 x NF array (field 0), plus c0,
+// and y = bit 0 L side, bit 1 wall (the face is its own partner), bits 2-11
+// ci and bits 12-21 cj as signed 10-bit fields.  The host derives the words
+// from the per-point connectivity with face_perm.
+constexpr int kFwL = 1, kFwWall = 2;
+
+__host__ __device__ __forceinline__ int face_perm(int o, int i, int j, int N) {
+  const int a = (o & 4) ? j : i, b = (o & 4) ? i : j;
+  return ((o & 1) ? N - 1 - a : a) + N * ((o & 2) ? N - 1 - b : b);
+}
+
+// Decodes the face word pair w of face f of element e for face point
+// (i, j): returns the offset of the partner flux point's slot in an
+// E x 2 x NF array (field 0; E 2 NF < 2^31 since E NF < 2^30) and sets
+// flags (bit 0 L side, bit 1 wall).  With FR_BOUNDS_CHECK an offset outside
+// the array or off the field-0 rows records FR_EBOUNDS and the word, and the
+// face is treated as a wall (its own partner).
+template <int N, int NF>
+__device__ __forceinline__ int32_t face_link(const KArgs& A, int2 w, int64_t e, int f, int i, int j,
+                                             int32_t& flags) {
+  const int32_t ci = (int32_t)((uint32_t)w.y << 20) >> 22, cj = (int32_t)((uint32_t)w.y << 10) >> 22;
+  const int32_t off = w.x + ci * i + cj * j;
+  flags = w.y & 3;
+#ifdef FR_BOUNDS_CHECK
+  if (off < 0 || (int64_t)off >= A.E * 2 * NF || off % (2 * NF) >= NF) {
+    atomicExch(&A.status[ST_STATUS], kStatusBounds);
+    atomicExch(&A.status[ST_BAD_INDEX], w.x);
+    flags = kFwL | kFwWall;
+    return (int32_t)(e * 2 * NF + f * N * N + i + N * j);
+  }
+#else
+  (void)A;
+  (void)e;
+  (void)f;
+#endif
+  return off;
 }
 
 template <typename T> __device__ __forceinline__ const BulkConst<T>& bulk(const KArgs& A);
@@ -435,6 +482,32 @@ __device__ __forceinline__ void tile_async(void* sdst, const void* gsrc, int nby
     done = n16 << 4;
   }
   for (int i = (done >> 2) + threadIdx.x; i < (nbytes >> 2); i += blockDim.x) cp_async_4(d + 4 * i, s + 4 * i);
+}
+
+// tile_async for a tile of ne elements of ELB bytes each, with ET elements in
+// a full tile, copied by the first TH threads of the block (a block may have
+// more, as in a group launch): a full tile of rows that are whole 16-byte
+// granules (every workspace region starts on a 256-byte boundary and every
+// shared region on a 16-byte one) is copied in a loop of compile-time length
+// without the alignment test; other tiles take tile_async.
+template <int ELB, int ET, int TH>
+__device__ __forceinline__ void tile_rows_async(void* sdst, const void* gsrc, int ne) {
+  if constexpr (ELB % 16 == 0) {
+    if (ne == ET) {
+      constexpr int n16 = ELB * ET / 16;
+      const char* s = static_cast<const char*>(gsrc);
+      char* d = static_cast<char*>(sdst);
+      if ((int)threadIdx.x < TH) {
+#pragma unroll
+        for (int r = 0; r < (n16 + TH - 1) / TH; ++r) {
+          const int i = r * TH + (int)threadIdx.x;
+          if (i < n16) cp_async_16(d + 16 * i, s + 16 * i);
+        }
+      }
+      return;
+    }
+  }
+  tile_async(sdst, gsrc, ne * ELB);
 }
 
 // Carves 16-byte aligned regions out of dynamic shared memory.

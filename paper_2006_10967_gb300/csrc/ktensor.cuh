@@ -386,18 +386,26 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
   // axis passes.  With FaceScatter the trace array holds the partner's trace
   // at each L flux point and both loads are independent; otherwise the
   // partner traces are gathered below, after the tile copies are issued.
+  // Hexahedra read one face word per line end (face_link) instead of the
+  // per-point connectivity, decoded below once the tile copies are issued;
+  // wpre then holds the flags (bit 0 L side, bit 1 wall).
   int32_t wpre[DIM][2];
   T opre[DIM][2][NQ];
+  [[maybe_unused]] int2 fwr[DIM][2];
   if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int k = (2 * a + sd) * NFP + ll;
-        wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
-        if constexpr (FaceScatter<DIM>::v)
+        if constexpr (DIM == 3) {
+          fwr[a][sd] = __ldg(A.ffw + (e0 + lel) * 6 + 2 * a + sd);
+        } else {
+          wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
+          if constexpr (FaceScatter<DIM>::v)
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) opre[a][sd][q] = tr[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+            for (int q = 0; q < NQ; ++q) opre[a][sd][q] = tr[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+        }
       }
   }
   // contiguous tiles: state (both fields), geometry, velocity cache; all in
@@ -416,17 +424,20 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
   const T* vsf = reinterpret_cast<const T*>(A.vsf);
   if (LY::VT && A.vsu) tile_async(vu, vsu + e0 * DIM * NU, ne * DIM * NU * (int)sizeof(T));
   if (LY::VT && A.vsf) tile_async(vf, vsf + e0 * DIM * NF, ne * DIM * NF * (int)sizeof(T));
-  if (!FaceScatter<DIM>::v && lact) {
+  if constexpr (DIM == 3) {
+    if (lact) {
+      const int fi = ll % N, fj = ll / N;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
+      for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int32_t w = wpre[a][sd];
-        const int32_t p = partner<NF>(A, w, (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll));
-        const int64_t pe = p / NF, pk = p % NF;
+        for (int sd = 0; sd < 2; ++sd) {
+          int32_t fl;
+          const int32_t po = face_link<N, NF>(A, fwr[a][sd], e0 + lel, 2 * a + sd, fi, fj, fl);
+          wpre[a][sd] = fl;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) opre[a][sd][q] = (w & 1) ? tr[(pe * 2 + F0 + fsel + q * FS) * NF + pk] : (T)0;
-      }
+          for (int q = 0; q < NQ; ++q) opre[a][sd][q] = (fl & 1) ? tr[po + (F0 + fsel + q * FS) * NF] : (T)0;
+        }
+    }
   }
   if (MODE == 1)
     for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
@@ -463,8 +474,10 @@ __device__ __forceinline__ void kb_tensor_body(const KArgs& A, const int blk) {
         // L points go to the compacted list of Step 5; R points get no flux here
         // entry: tile flux point, bit 15 set at walls (own partner)
         const int64_t g0 = (e0 + lel) * NF + k0, g1 = (e0 + lel) * NF + k1;
-        if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k0) | ((w0 >> 1) == g0 ? 0x8000 : 0));
-        if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k1) | ((w1 >> 1) == g1 ? 0x8000 : 0));
+        const bool wl0 = DIM == 3 ? (w0 & 2) != 0 : (w0 >> 1) == g0;
+        const bool wl1 = DIM == 3 ? (w1 & 2) != 0 : (w1 >> 1) == g1;
+        if (w0 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k0) | (wl0 ? 0x8000 : 0));
+        if (w1 & 1) llist[atomicAdd(&nL, 1)] = (uint16_t)((lel * NF + k1) | (wl1 ? 0x8000 : 0));
       }
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
@@ -1066,7 +1079,10 @@ struct KALayout {
 // ka_tensor: R-side lift, du/dt, RK4 update, next-stage traces; line passes
 // as in kb_tensor, the last of which also applies the update to its line.  stage -1 writes du/dt to A.out (fp64) and leaves the
 // state alone; stage 0 only recomputes the traces of ustg.
-template <int DIM, int N, typename T, int MODE, int TD = 1>
+// SF: the RK stage as a compile-time constant (1..4), or -2 to read it
+// from A.stage; a fixed stage removes the per-point stage switch and the
+// code of the other stages.
+template <int DIM, int N, typename T, int MODE, int TD = 1, int SF = -2>
 __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   using S = TS<DIM, N>;
   using LY = KALayout<DIM, N, T, MODE, TD>;
@@ -1098,7 +1114,7 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   const T* fc = reinterpret_cast<const T*>(A.fc);
   const T* rp = reinterpret_cast<const T*>(A.rp);
   const int tid = threadIdx.x;
-  const int stage = A.stage;
+  const int stage = SF >= -1 ? SF : A.stage;
   const TensorOpsT<T>& O = bulk<T>(A).ops;
   // line-pass role: line (lel, ll) of the fields fsel + q FS, q < NQ
   const int fsel = tid / LY::LINES, lin = tid % LY::LINES;
@@ -1113,25 +1129,33 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   // partner's at its R points: with FluxScatter both sit in the own slots
   // (one independent load per line end), else the R value is gathered from
   // the partner's slot.
+  // Hexahedra read one face word per line end (face_link), decoded below
+  // once the tile copies are issued; wpre then holds the flags (bit 0 L
+  // side, bit 1 wall).
   T fpre[DIM][2][NQ];
   int32_t wpre[DIM][2];
+  [[maybe_unused]] int2 fwr[DIM][2];
   if (lact) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int k = (2 * a + sd) * NFP + ll;
-        wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
-        // with FaceScatter both values sit in the own slot; otherwise only
-        // the L ends' own fluxes do (the R ends gather below)
-        if (stage != 0 && FaceScatter<DIM>::v)
+        if constexpr (DIM == 3) {
+          fwr[a][sd] = __ldg(A.ffw + (e0 + lel) * 6 + 2 * a + sd);
+        } else {
+          wpre[a][sd] = A.fnbr[(e0 + lel) * NF + k];
+          // with FaceScatter both values sit in the own slot
+          if (stage != 0 && FaceScatter<DIM>::v)
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+            for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[((e0 + lel) * 2 + F0 + fsel + q * FS) * NF + k];
+        }
       }
   }
   // contiguous tiles, all in flight together with the connectivity loads
+  constexpr int TH = LY::THREADS;
   if (MODE == 0) {
-    tile_async(ys, (stage == 0 ? ustg : rp) + e0 * 2 * NU, ne * 2 * NU * (int)sizeof(T));
+    tile_rows_async<2 * NU * (int)sizeof(T), ET, TH>(ys, (stage == 0 ? ustg : rp) + e0 * 2 * NU, ne);
   } else {
     for (int idx = tid; idx < ne * NU; idx += blockDim.x) {
       const int el = idx / NU, i = idx % NU;
@@ -1140,31 +1164,37 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
     }
   }
   if (stage != 0) {
-    tile_async(gs, geo_of<T>(A) + e0 * NG, ne * NG * (int)sizeof(T));
-    tile_async(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne * kMetricRec * (int)sizeof(T));
+    tile_rows_async<NG * (int)sizeof(T), ET, TH>(gs, geo_of<T>(A) + e0 * NG, ne);
+    tile_rows_async<kMetricRec * (int)sizeof(T), ET, TH>(mcs, reinterpret_cast<const T*>(A.mcg) + e0 * kMetricRec, ne);
   }
   if (PRE && stage >= 1) {
-    tile_async(u2s, reinterpret_cast<const float2*>(A.u) + e0 * 2 * NU, ne * 2 * NU * 8);
-    if (stage >= 2) tile_async(acs, reinterpret_cast<const float*>(A.acc) + e0 * 2 * NU, ne * 2 * NU * 4);
+    tile_rows_async<2 * NU * 8, ET, TH>(u2s, reinterpret_cast<const float2*>(A.u) + e0 * 2 * NU, ne);
+    if (stage >= 2) tile_rows_async<2 * NU * 4, ET, TH>(acs, reinterpret_cast<const float*>(A.acc) + e0 * 2 * NU, ne);
     if (cons) {
-      if (stage >= 2) tile_async(tas, A.tacc + e0 * 2, ne * 2 * 8);
-      if (stage == 4) tile_async(wds, A.wdetf + e0 * NU, ne * NU * 8);
+      if (stage >= 2) tile_rows_async<2 * 8, ET, TH>(tas, A.tacc + e0 * 2, ne);
+      if (stage == 4) tile_rows_async<NU * 8, ET, TH>(wds, A.wdetf + e0 * NU, ne);
     }
   }
-  if (!FaceScatter<DIM>::v && stage != 0 && lact) {
-    // one load per line end: the own slot at L ends, the partner's at R ends
+  if constexpr (DIM == 3) {
+    if (lact) {
+      // one load per line end: the own slot at L ends, the partner's at R ends
+      const int fi = ll % N, fj = ll / N;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
+      for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int32_t w = wpre[a][sd];
-        // flux-point indices fit 31 bits (E Nf < 2^30, checked at mesh creation)
-        const int32_t own = (int32_t)((e0 + lel) * NF + (2 * a + sd) * NFP + ll);
-        const int32_t p = (w & 1) ? own : partner<NF>(A, w, own);
-        const int64_t pe = p / NF, pk = p % NF;
+        for (int sd = 0; sd < 2; ++sd) {
+          int32_t fl;
+          const int32_t po = face_link<N, NF>(A, fwr[a][sd], e0 + lel, 2 * a + sd, fi, fj, fl);
+          wpre[a][sd] = fl;
+          if (stage != 0) {
+            // slot offsets fit 31 bits (E 2 Nf < 2^31, checked at mesh creation)
+            const int32_t own = (int32_t)((e0 + lel) * 2 * NF + (2 * a + sd) * NFP + ll);
+            const int32_t o = (fl & 1) ? own : po;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[(pe * 2 + F0 + fsel + q * FS) * NF + pk];
-      }
+            for (int q = 0; q < NQ; ++q) fpre[a][sd][q] = fc[o + (F0 + fsel + q * FS) * NF];
+          }
+        }
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -1357,9 +1387,8 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
           // (the partner is L there) and at walls (the own partner)
           T* trl = tr + ((e0 + lel) * 2 + F0 + fld) * NF;
           const int32_t w0 = wpre[a][0], w1 = wpre[a][1];
-          const int32_t g0 = (int32_t)((e0 + lel) * NF + k0), g1 = (int32_t)((e0 + lel) * NF + k1);
-          if (!(w0 & 1) || (w0 >> 1) == g0) trl[k0] = t0;
-          if (!(w1 & 1) || (w1 >> 1) == g1) trl[k1] = t1;
+          if (!(w0 & 1) || (w0 & 2)) trl[k0] = t0;
+          if (!(w1 & 1) || (w1 & 2)) trl[k1] = t1;
         }
       }
     }
@@ -1371,11 +1400,19 @@ __device__ __forceinline__ void ka_tensor_body(const KArgs& A, const int blk) {
   if (MODE == 1 && stage == 4) pseudo_rms_finish(A, block_sum(sq, red_sh), red_sh, A.E * NU);
 }
 
-template <int DIM, int N, typename T, int MODE, int TD = 1>
+template <int DIM, int N, typename T, int MODE, int TD = 1, int SF = -2>
 __global__ void __launch_bounds__(KALayout<DIM, N, T, MODE, TD>::THREADS, KALayout<DIM, N, T, MODE, TD>::MINB)
     ka_tensor(const KArgs A) {
-  ka_tensor_body<DIM, N, T, MODE, TD>(A, blockIdx.x);
+  ka_tensor_body<DIM, N, T, MODE, TD, SF>(A, blockIdx.x);
 }
+
+// Update kernels compiled once per RK stage: the physical step of mixed
+// hexahedral fields (the large 3D workloads); other fields read the stage
+// from their arguments.
+template <int DIM, typename T, int MODE>
+struct StageKA {
+  static constexpr bool v = DIM == 3 && sizeof(T) == 4 && MODE == 0;
+};
 
 // Spatial velocity factor v(x) (g = 1) at the solution and flux points of
 // every element, evaluated once in double and stored in the bulk type.
