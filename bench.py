@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--ensemble-launch", default="streams", choices=["group", "streams"],
                     help="c4: one field per order on its own stream (faster, measured), or one launch per RK "
                          "stage over all orders (fr_group_step)")
+    ap.add_argument("--probe", default=None, choices=["dense-hex"],
+                    help="time the two forms of the hex p = 3 operator applies (fr_probe_hex_apply) and exit")
     ap.add_argument("--rk-steps", type=int, default=STEPS_PER_BENCH_STEP,
                     help="RK4 steps per benchmark step (profiling captures use fewer launches)")
     return ap.parse_args()
@@ -562,8 +564,72 @@ def accuracy(G, S, w, mesh, precisions=("fp64", "mixed")):
     return res
 
 
+def probe_dense_hex(args):
+    """Steps 1 and 3's operator applies on 64^3 hexahedra of order 3 (traces
+    and reference derivatives of both fields, no corrections), sum-factorised
+    (form 0) against the dense 288 x 64 operator on the tensor cores (form 1),
+    through fr_probe_hex_apply in its reducing mode (one sum per element and
+    field written, so the output traffic is negligible).  Each launch is
+    timed alone with CUDA events after an L2 flush; the median is reported."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10967_gb300 as G
+    from paper_2006_10967_gb300 import _capi
+    L = G.lib()
+    n = args.mesh_n or 64
+    E = n ** 3
+    u = torch.randn(E, 2, 64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+    out = {f: torch.empty(E * 2, device="cuda") for f in (0, 1)}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+
+    def call(form):
+        _capi.check(L.fr_probe_hex_apply(3, form, 1, C.c_void_p(u.data_ptr()), E, C.c_void_p(out[form].data_ptr()),
+                                         E * 2, sp), "fr_probe_hex_apply")
+
+    res = {}
+    for form in (0, 1):
+        for _ in range(max(args.warmup, 3)):
+            call(form)
+        ts = []
+        for _ in range(max(args.steps, 5)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call(form)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        res[form] = statistics.median(ts)
+    agree = float((out[0] - out[1]).abs().max() / out[0].abs().max())
+    cols = 2 * E
+    useful = 2 * (96 * 4 + 192 * 4)          # FMAs x 2 per column, both forms' useful work
+    dense_tc = 3 * 2 * 288 * 64              # three TF32 products of the dense operator per column
+    pk = peaks()
+    tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+    line = {"probe": "hex p=3 operator applies: flux-point traces and reference derivatives of both fields "
+                     "(Steps 1 and 3 without corrections), reducing mode",
+            "elements": E, "columns": cols, "input_bytes": u.numel() * 4,
+            "sum_factorised_us": res[0], "dense_tensor_core_us": res[1], "dense_over_sf": res[1] / res[0],
+            "sum_factorised": {"useful_tflops": useful * cols / (res[0] * 1e-6) / 1e12,
+                               "input_gbs": u.numel() * 4 / (res[0] * 1e-6) / 1e9},
+            "dense_tensor_core": {"tensor_tflops": dense_tc * cols / (res[1] * 1e-6) / 1e12,
+                                  "tf32_peak_tflops": tf32_peak,
+                                  "tf32_peak_source": "MEASURED_PEAKS bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
+                                  "useful_tflops": useful * cols / (res[1] * 1e-6) / 1e12},
+            "forms_agree_rel": agree,
+            "timing": "median of per-launch CUDA events, L2 flushed (512 MiB write) before each launch"}
+    line["dense_tensor_core"]["frac_of_tf32_peak"] = line["dense_tensor_core"]["tensor_tflops"] / tf32_peak
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.probe == "dense-hex":
+        probe_dense_hex(args)
+        return
     rank, world = dist_init()
     import synthetic as S
     if args.workload == "c4" and args.impl == "ours":

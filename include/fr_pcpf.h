@@ -366,6 +366,28 @@ int fr_traces(fr_field* field, void* stream);
  * type and order in `precision` (FR_FP64 or FR_MIXED): *count >= 1. */
 int fr_kernel_variants(const fr_mesh* mesh, int precision, int32_t* count);
 
+/* Measurement entry point: the element-local operator applies of Steps 1 and
+ * 3 on hexahedra of order 3 (Section 3.1, Eq. extrapolateSoln: the flux-point
+ * traces u^f = L u; Eq. continuousGrad: the reference derivatives D_a u,
+ * without the correction terms) in one of two forms, so that they can be
+ * timed against each other:
+ *   form 0: the 1D operators along solution-point lines (sum factorisation,
+ *           the form of the residual kernel), FP32 FMAs;
+ *   form 1: the dense 288 x 64 operator [L; D_0; D_1; D_2] on the tensor
+ *           cores (mma.sync m16n8k8, three-term TF32, FP32 accumulation).
+ * u_dev: device, n_elems x 2 x 64 floats (element, field, solution point;
+ * the stage-value layout), 16-byte aligned.  out_dev: device, out_len
+ * floats.  reduce == 0: n_elems x 2 x 288 values per (element, field): the
+ * 96 traces (face 2a + sd, face point l: line l along axis a, the other two
+ * point indices with the lower axis fastest), then the derivatives along
+ * axes 0, 1, 2 at the 64 points.  reduce != 0: n_elems x 2 values, the sum of
+ * each (element, field)'s 288 values (for timing without the output
+ * traffic).  Asynchronous on `stream`.  Errors: FR_EUNSUPPORTED (order != 3),
+ * FR_EINVAL (form not 0 or 1, negative n_elems, null or misaligned pointers,
+ * out_len too small), FR_ECUDA. */
+int fr_probe_hex_apply(int order, int form, int reduce, const float* u_dev, int64_t n_elems,
+                       float* out_dev, int64_t out_len, void* stream);
+
 /* Evaluate the semi-discrete right-hand side du/dt = -J^{-1} div~ f~ (Step 6)
  * of the physical system at the current state and time t into dev_out
  * (device, 2 * n_dof doubles: phi rates then psi rates).  Does not change the

@@ -101,6 +101,7 @@ _SIGS = {
     "fr_adjoint_record": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp]),
     "fr_adjoint_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fr_kernel_variants": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int32)]),
+    "fr_probe_hex_apply": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_int64, _vp, C.c_int64, _vp]),
     "fr_stage": (C.c_int, [_vp, C.c_int, _vp]),
     "fr_halo_row_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "fr_halo_pack": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),

@@ -27,12 +27,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"] + ARCH
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC"]
 
-CU = ["api.cu", "k_quad.cu", "k_hex.cu", "k_tri.cu", "k_group.cu", "noalloc.cu", "adjoint.cu"]
+CU = ["api.cu", "k_quad.cu", "k_hex.cu", "k_tri.cu", "k_group.cu", "noalloc.cu", "adjoint.cu", "probe_dense.cu"]
 # The residual/update kernels' float arithmetic (the mixed path) uses the
 # approximate reciprocal, division and square root (2 ulp) and flushes
 # denormals; FP64 arithmetic is unaffected by these flags.
 FAST_FLOAT = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-FAST_FLOAT_TU = {"k_quad.cu", "k_hex.cu", "k_tri.cu", "k_group.cu"}
+FAST_FLOAT_TU = {"k_quad.cu", "k_hex.cu", "k_tri.cu", "k_group.cu", "probe_dense.cu"}
 CPP = ["mesh.cpp", "refel.cpp"]
 
 

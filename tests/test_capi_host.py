@@ -123,6 +123,22 @@ def test_partner_index_width_is_guarded(G):
     G.lib().fr_mesh_destroy(h)
 
 
+def test_probe_rejects_bad_arguments_before_any_launch(G):
+    """fr_probe_hex_apply validates its arguments on the host: unsupported
+    order, unknown form, negative count, null or misaligned input, short
+    output (none of these reaches the device)."""
+    f = G.lib().fr_probe_hex_apply
+    ok = C.c_void_p(256)                             # aligned, never dereferenced: every call below fails first
+    assert f(2, 0, 0, ok, 1, ok, 576, None) == -6    # order 2: FR_EUNSUPPORTED
+    assert f(3, 2, 0, ok, 1, ok, 576, None) == -1    # form 2
+    assert f(3, 0, 0, ok, -1, ok, 576, None) == -1   # negative count
+    assert f(3, 0, 0, None, 1, ok, 576, None) == -1  # null input
+    assert f(3, 1, 0, C.c_void_p(260), 1, ok, 576, None) == -1  # input not on a 16-byte boundary
+    assert f(3, 0, 0, ok, 1, ok, 575, None) == -1    # 1 x 2 x 288 values needed
+    assert f(3, 1, 1, ok, 2, ok, 3, None) == -1      # reduce: 2 x 2 values needed
+    assert f(3, 0, 0, None, 0, None, 0, None) == 0   # nothing to do
+
+
 def test_bounds_checked_build_exports_every_declared_symbol():
     """The bounds-checked build (FR_BOUNDS_CHECK) of the same sources links
     and exports the same entry points; its error code has a message."""
