@@ -339,7 +339,8 @@ void fr_group_destroy(fr_group* group);
  * transport: NCCL, or device copies), scatters the received ones into its
  * ghosts (fr_halo_unpack) and recomputes the flux-point traces
  * (fr_traces).  The ghosts' own updates are discarded by the next exchange.
- * Preconditioning is not partitioned (its stop rule is a global RMS).
+ * The preconditioning runs the same way with fr_pseudo_begin and
+ * fr_pseudo_stage in place of fr_stage (fixed iteration count only).
  *
  * fr_stage: stage s (1..4) of the physical RK4 step on `stream`, the
  * residual and update kernels of that stage (asynchronous; no CUDA graph);
@@ -361,6 +362,23 @@ int fr_halo_unpack(fr_field* field, const int64_t* elems_dev, int64_t n, const v
 /* Recompute every element's flux-point traces from its stage values (Step 1,
  * Eq. extrapolateSoln) after fr_halo_unpack.  Asynchronous. */
 int fr_traces(fr_field* field, void* stream);
+/* The preconditioning of an element-partitioned run, one pseudo stage at a
+ * time (Section 2, Eq. lsequation and the reset psi_0 = phi - 1/2; Section
+ * 3.2, Eq. pseudotimesystem marched by RK4 in pseudo time).  fr_pseudo_begin
+ * resets psi_0 and psi from phi on every local element and computes psi's
+ * traces; fr_pseudo_stage(s) runs stage s (1..4) of one pseudo-time
+ * iteration with the step params.pseudo_dtau.  A rank calls fr_pseudo_begin,
+ * exchanges its ghosts (fr_halo_pack / fr_halo_unpack / fr_traces, as after
+ * fr_stage), then for each of params.pseudo_kmax iterations the four
+ * fr_pseudo_stage calls, each followed by the same exchange; the owned
+ * elements then hold what fr_precondition gives on the whole mesh.  Only
+ * fields with params.pseudo_fixed = 1 (the stop rule's RMS over the local
+ * points would count the ghosts) and the preconditioned normal
+ * (FR_NORMAL_PSI): FR_EUNSUPPORTED otherwise.  Asynchronous on `stream`; no
+ * CUDA graph.  Errors: FR_EINVAL (null field, stage outside 1..4),
+ * FR_EUNSUPPORTED, FR_ECUDA. */
+int fr_pseudo_begin(fr_field* field, void* stream);
+int fr_pseudo_stage(fr_field* field, int stage, void* stream);
 
 /* Number of kernel variants (fr_params.variant) built for the mesh's element
  * type and order in `precision` (FR_FP64 or FR_MIXED): *count >= 1. */

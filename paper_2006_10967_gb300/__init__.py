@@ -318,6 +318,15 @@ class Field:
     def traces(self, stream=None):
         check(lib().fr_traces(self.handle, self._stream(stream)), "fr_traces")
 
+    def pseudo_begin(self, stream=None):
+        """psi_0 = psi = phi - 1/2 and psi's traces: the start of a
+        preconditioning run one pseudo stage at a time (fr_pseudo_begin)."""
+        check(lib().fr_pseudo_begin(self.handle, self._stream(stream)), "fr_pseudo_begin")
+
+    def pseudo_stage(self, s, stream=None):
+        """Stage s (1..4) of one pseudo-time RK4 iteration (fr_pseudo_stage)."""
+        check(lib().fr_pseudo_stage(self.handle, int(s), self._stream(stream)), "fr_pseudo_stage")
+
     # ---- discrete adjoint -------------------------------------------------
     def adjoint_record(self, n_steps, ckpt_every, precondition=False, stream=None):
         """Advance n_steps keeping checkpoints for adjoint_step (fr_adjoint_record);

@@ -107,6 +107,8 @@ _SIGS = {
     "fr_halo_pack": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "fr_halo_unpack": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "fr_traces": (C.c_int, [_vp, _vp]),
+    "fr_pseudo_begin": (C.c_int, [_vp, _vp]),
+    "fr_pseudo_stage": (C.c_int, [_vp, C.c_int, _vp]),
     "fr_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
     "fr_group_step": (C.c_int, [_vp, C.c_int, _vp]),
     "fr_group_destroy": (None, [_vp]),

@@ -1059,6 +1059,43 @@ extern "C" int fr_traces(fr_field* f, void* stream) {
   return FR_OK;
 }
 
+// The preconditioning one pseudo stage at a time, for element-partitioned
+// runs: the same launches as launch_precondition, with the caller's ghost
+// exchange between them.  Only the fixed iteration count: the stop rule's RMS
+// would be taken over the rank's local points, ghosts included.
+namespace {
+int pseudo_check(const fr_field* f) {
+  if (!f) return FR_EINVAL;
+  if (f->prm.normal != FR_NORMAL_PSI || !f->prm.pseudo_fixed) return FR_EUNSUPPORTED;
+  return FR_OK;
+}
+}  // namespace
+
+extern "C" int fr_pseudo_begin(fr_field* f, void* stream) {
+  int rc = pseudo_check(f);
+  if (rc) return rc;
+  rc = field_precondition_begin(f, reinterpret_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  f->n_precond_done++;
+  return FR_OK;
+}
+
+extern "C" int fr_pseudo_stage(fr_field* f, int stage, void* stream) {
+  const int rc = pseudo_check(f);
+  if (rc) return rc;
+  if (stage < 1 || stage > 4) return FR_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KArgs a = f->args;
+  a.stage = stage;
+  a.dt = f->prm.pseudo_dtau;
+  a.rk = rk_const(a.dt);
+  a.use_dev_time = 0;
+  f->ks.kb[1](a, s);
+  f->ks.ka[1](a, s);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
 extern "C" int fr_kernel_variants(const fr_mesh* m, int precision, int32_t* count) {
   if (!m || !count || (precision != FR_FP64 && precision != FR_MIXED)) return FR_EINVAL;
   *count = variant_count(*m, precision);

@@ -25,9 +25,14 @@ On the device a rank's field steps one RK stage at a time (Field.stage, the
 library's fr_stage) and exchanges its ghosts' stage values between stages:
 step() does that for one rank over torch.distributed, step_ranks() for
 several ranks' fields held by one process on one device (the exchange is
-then a device copy between the fields).  Preconditioning is not partitioned
-(its stop rule is an RMS over the whole mesh); a partitioned run takes a
-preconditioned state from the whole mesh or runs without it.
+then a device copy between the fields).  The preconditioning runs the same
+way, one pseudo stage at a time (Field.pseudo_begin / pseudo_stage, the
+library's fr_pseudo_begin / fr_pseudo_stage) with the ghost exchange after
+the reset and after every pseudo stage: precondition() and
+precondition_ranks(), called by step() and step_ranks() before every step
+whose index is a positive multiple of params.n_precond, as fr_step does.
+Only the fixed iteration count (params.pseudo_fixed): the stop rule's RMS is
+taken over the whole mesh.
 """
 from dataclasses import dataclass, field
 
@@ -221,28 +226,75 @@ def halo_exchange(field, plan, dist=None):
     field.traces()
 
 
+def _precondition_due(field, n):
+    """fr_step's schedule: a preconditioning before step n (the field's step
+    count) when n is a positive multiple of params.n_precond and the normal
+    comes from psi."""
+    P = field.params
+    return P.normal == 0 and n > 0 and n % P.n_precond == 0
+
+
+def precondition(field, plan, dist=None):
+    """The preconditioning of one rank's field: psi reset, then
+    params.pseudo_kmax pseudo-time RK4 iterations, with a ghost exchange
+    after the reset and after every pseudo stage."""
+    field.pseudo_begin()
+    halo_exchange(field, plan, dist)
+    for _ in range(int(field.params.pseudo_kmax)):
+        for s in (1, 2, 3, 4):
+            field.pseudo_stage(s)
+            halo_exchange(field, plan, dist)
+
+
 def step(field, plan, n_steps=1, dist=None):
     """n physical RK4 steps of one rank's field with a ghost exchange after
-    every stage."""
-    for _ in range(int(n_steps)):
+    every stage, preconditioning on fr_step's schedule."""
+    n0 = field.stats()["n_steps"]
+    for i in range(int(n_steps)):
+        if _precondition_due(field, n0 + i):
+            precondition(field, plan, dist)
         for s in (1, 2, 3, 4):
             field.stage(s)
             halo_exchange(field, plan, dist)
 
 
+def _exchange_ranks(fields, plans, lists):
+    """Every rank's ghosts refreshed from their owners (device copies), then
+    every rank's traces."""
+    packed = {(p.rank, q): fields[p.rank].halo_pack(ix)
+              for p, (send, _) in zip(plans, lists) for q, ix in sorted(send.items())}
+    for p, (_, recv) in zip(plans, lists):
+        for q, ix in sorted(recv.items()):
+            fields[p.rank].halo_unpack(ix, packed[(q, p.rank)])
+    for f in fields:
+        f.traces()
+
+
+def precondition_ranks(fields, plans):
+    """precondition() for several ranks' fields held by this process on one
+    device."""
+    lists = [_device_lists(p) for p in plans]
+    for f in fields:
+        f.pseudo_begin()
+    _exchange_ranks(fields, plans, lists)
+    for _ in range(int(fields[0].params.pseudo_kmax)):
+        for s in (1, 2, 3, 4):
+            for f in fields:
+                f.pseudo_stage(s)
+            _exchange_ranks(fields, plans, lists)
+
+
 def step_ranks(fields, plans, n_steps=1):
     """n physical RK4 steps of several ranks' fields held by this process on
     one device: per stage every rank's stage, then every rank's ghosts
-    refreshed from their owners by device copies, then the traces."""
+    refreshed from their owners by device copies, then the traces;
+    preconditioning on fr_step's schedule."""
     lists = [_device_lists(p) for p in plans]
-    for _ in range(int(n_steps)):
+    n0 = fields[0].stats()["n_steps"]
+    for i in range(int(n_steps)):
+        if _precondition_due(fields[0], n0 + i):
+            precondition_ranks(fields, plans)
         for s in (1, 2, 3, 4):
             for f in fields:
                 f.stage(s)
-            packed = {(p.rank, q): fields[p.rank].halo_pack(ix)
-                      for p, (send, _) in zip(plans, lists) for q, ix in sorted(send.items())}
-            for p, (_, recv) in zip(plans, lists):
-                for q, ix in sorted(recv.items()):
-                    fields[p.rank].halo_unpack(ix, packed[(q, p.rank)])
-            for f in fields:
-                f.traces()
+            _exchange_ranks(fields, plans, lists)

@@ -8,7 +8,8 @@ values between the fields (device copies; the same pack/unpack calls a rank
 makes around its NCCL send/receive).  The owned elements' state after
 several RK4 steps equals the whole-mesh field's, bit for bit: every owned
 element reads exactly the values it reads in the whole mesh, through the
-same kernels."""
+same kernels.  The preconditioning, run one pseudo stage at a time with the
+same exchange, does the same."""
 import numpy as np
 import pytest
 import torch
@@ -116,6 +117,81 @@ def test_partitioned_march_equals_whole_mesh(G, case, world, precision):
     Fs.set(1, psi[pl.local])
     Fs.step(n)
     assert not np.array_equal(Fs.get(0)[pl.owned_local], ref[0][pl.owned])
+
+
+@pytest.mark.parametrize("case,world", [
+    ("quad_walls_jitter_p4", 3),
+    ("tri_delaunay_p3", 2),
+    ("hex_rotated_walls_p3", 3),
+])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_partitioned_preconditioning_equals_whole_mesh(G, case, world, precision):
+    """The preconditioning run one pseudo stage at a time with the ghost
+    exchange after the reset and after every pseudo stage (fr_pseudo_begin,
+    fr_pseudo_stage): at t = 0 and on fr_step's schedule (before steps 3 and
+    6 of 7 here), the owned elements equal the whole-mesh field's, bit for
+    bit; a rank preconditioned alone on its local mesh differs."""
+    from paper_2006_10967_gb300 import partition as PT
+    w = CASES[case]()
+    mesh = w.mesh()
+    M = G.Mesh.from_synthetic(mesh, w.order)
+    P = G.make_params(w, precision, variant=0, n_precond=3, pseudo_kmax=4, pseudo_fixed=True)
+    F = G.Field(M, P, ic=w.circle, precondition=False)
+    phi = F.get(0)
+    F.set(0, phi)                                    # the same set-up path as the ranks' fields
+    F.precondition()
+    psi_pre = F.get(1)
+    part = PT.partition(mesh, world)
+    plans = PT.plans(mesh, part)
+    fields = []
+    for pl in plans:
+        Fl = G.Field(G.Mesh.from_synthetic(pl.mesh, w.order), P, ic=w.circle, precondition=False)
+        Fl.set(0, phi[pl.local])
+        fields.append(Fl)
+    PT.precondition_ranks(fields, plans)
+    for pl, Fl in zip(plans, fields):
+        got = Fl.get(1)[pl.owned_local]
+        assert np.array_equal(got, psi_pre[pl.owned]), (pl.rank, np.abs(got - psi_pre[pl.owned]).max())
+    assert not np.array_equal(psi_pre, phi - 0.5)    # the iterations moved psi
+    n = 7
+    F.step(n)
+    PT.step_ranks(fields, plans, n)
+    assert F.sync() == 0
+    ref = [F.get(0), F.get(1)]
+    assert F.stats()["n_preconditions"] == 3
+    for pl, Fl in zip(plans, fields):
+        assert Fl.sync() == 0
+        st = Fl.stats()
+        assert st["n_steps"] == n and st["n_preconditions"] == 3
+        for fld in (0, 1):
+            got = Fl.get(fld)[pl.owned_local]
+            assert np.array_equal(got, ref[fld][pl.owned]), (pl.rank, fld, np.abs(got - ref[fld][pl.owned]).max())
+    pl = plans[0]
+    Fs = G.Field(G.Mesh.from_synthetic(pl.mesh, w.order), P, ic=w.circle, precondition=False)
+    Fs.set(0, phi[pl.local])
+    Fs.precondition()
+    assert not np.array_equal(Fs.get(1)[pl.owned_local], psi_pre[pl.owned])
+
+
+def test_pseudo_stage_calls_need_the_fixed_iteration_count(G):
+    """fr_pseudo_begin / fr_pseudo_stage refuse fields whose preconditioning
+    stops on the RMS rule or that take the normal from phi
+    (FR_EUNSUPPORTED), and stages outside 1..4 (FR_EINVAL)."""
+    from paper_2006_10967_gb300 import _capi
+    w = CASES["quad_periodic_jitter_p3"]()
+    M = G.Mesh.from_synthetic(w.mesh(), w.order)
+    for kw in ({}, {"pseudo_fixed": True, "normal": "phi"}):
+        F = G.Field(M, G.make_params(w, "fp64", variant=0, **kw), ic=w.circle, precondition=False)
+        with pytest.raises(_capi.FRError) as e:
+            F.pseudo_begin()
+        assert e.value.code == _capi.FR_EUNSUPPORTED
+    F = G.Field(M, G.make_params(w, "fp64", variant=0, pseudo_fixed=True), ic=w.circle, precondition=False)
+    with pytest.raises(_capi.FRError) as e:
+        F.pseudo_stage(5)
+    assert e.value.code == G.FR_EINVAL
+    F.pseudo_begin()
+    F.pseudo_stage(1)
+    assert F.sync() == 0
 
 
 def test_halo_rows_round_trip_and_index_check(G):

@@ -157,3 +157,45 @@ def test_local_meshes_pair_faces_across_the_period(name, world):
         M = G.Mesh.from_synthetic(plan.mesh, p)
         assert M.info.n_boundary_fpts == expected
     assert partial > 0
+
+
+def test_step_runs_the_preconditioning_on_fr_steps_schedule(monkeypatch):
+    """partition.step on the host: before every step whose index is a
+    positive multiple of n_precond, the preconditioning (the reset, then
+    pseudo_kmax iterations of four pseudo stages), with a ghost exchange after
+    the reset, after every pseudo stage and after every physical stage; none
+    when the normal comes from phi."""
+    from paper_2006_10967_gb300 import partition as PT
+    calls = []
+
+    class Params:
+        normal, n_precond, pseudo_kmax = 0, 3, 2
+
+    class FakeField:
+        params = Params
+
+        def stats(self):
+            return {"n_steps": 0}
+
+        def stage(self, s):
+            calls.append(("stage", s))
+
+        def pseudo_begin(self):
+            calls.append(("begin",))
+
+        def pseudo_stage(self, s):
+            calls.append(("pseudo", s))
+
+    monkeypatch.setattr(PT, "halo_exchange", lambda field, plan, dist=None: calls.append(("exchange",)))
+    one_step = [c for s in (1, 2, 3, 4) for c in (("stage", s), ("exchange",))]
+    pre = [("begin",), ("exchange",)] + [c for _ in range(2) for s in (1, 2, 3, 4)
+                                         for c in (("pseudo", s), ("exchange",))]
+    PT.step(FakeField(), None, 7)
+    expect = []
+    for i in range(7):
+        expect += (pre if i in (3, 6) else []) + one_step
+    assert calls == expect
+    calls.clear()
+    Params.normal = 1
+    PT.step(FakeField(), None, 7)
+    assert calls == one_step * 7
