@@ -108,6 +108,95 @@ def test_partitioned_residual_and_march_equal_single_domain(tmp_path, name, worl
         assert r["step_err"] < 1e-13, r
 
 
+def _precond_rank_main(rank, world, port, out_dir, name):
+    """The preconditioning (psi0 = phi - 1/2, RK4 in pseudo time) on a
+    rank's local mesh with the stage values' ghosts exchanged before every
+    pseudo residual, in the fixed-count form and with the stop rule's RMS
+    over the owned points all-reduced across the ranks."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import Params, Solver
+    from paper_2006_10967_gb300 import partition as PT
+    mesh, p, vel, circ = _case(name)
+    h = 1.0 / (6 if name == "quad" else 4)
+    prm = Params(gamma=0.09, eps=0.01, tau=0.1, dt=2e-3, pseudo_kmax=6, pseudo_dtau=0.1 * h / (p + 1),
+                 nu_max=0.02)
+    full = Solver(mesh, p, prm, vel)
+    full.initialize(circ, precondition=False)
+    # the whole mesh's RMS after k iterations, k = 1..kmax; the adaptive
+    # tolerance sits midway between iterations 2 and 3
+    hist = []
+    for k in range(1, prm.pseudo_kmax + 1):
+        full.prm.pseudo_kmax = k
+        hist.append(full.precondition(fixed=True)[1])
+    full.prm.pseudo_kmax = 6
+    tol = 0.5 * (hist[1] + hist[2])
+    part = PT.partition(mesh, world)
+    plan = PT.plans(mesh, part)[rank]
+    loc = Solver(plan.mesh, p, prm, vel)
+    ol = torch.as_tensor(plan.owned_local)
+    phi = torch.zeros_like(loc.xu[..., 0])
+    phi[ol] = full.phi[plan.owned]
+    PT.exchange(phi, plan)
+    psi0 = phi - 0.5
+    dtau = prm.pseudo_dtau
+
+    def rate(y):
+        y = y.clone()
+        PT.exchange(y, plan)
+        return loc.rhs_pseudo(y, psi0)
+
+    out = {"rank": rank, "hist": hist, "tol": tol}
+    for fixed in (True, False):
+        full.prm.pseudo_tol = tol
+        it_f, rms_f = full.precondition(fixed=fixed)
+        psi = psi0.clone()
+        it, rms = 0, float("nan")
+        for it in range(1, prm.pseudo_kmax + 1):
+            k1 = rate(psi)
+            k2 = rate(psi + 0.5 * dtau * k1)
+            k3 = rate(psi + 0.5 * dtau * k2)
+            k4 = rate(psi + dtau * k3)
+            new = psi + dtau / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+            R = ((new - psi) / dtau)[ol]
+            acc = torch.tensor([float((R * R).sum()), float(R.numel())], dtype=torch.float64)
+            dist.all_reduce(acc)
+            rms = float(torch.sqrt(acc[0] / acc[1]))
+            psi = new
+            if not fixed and rms <= tol:
+                break
+        key = "fixed" if fixed else "adaptive"
+        out[key] = {"iters": it, "iters_full": it_f, "rms_rel": abs(rms - rms_f) / rms_f,
+                    "err": float((psi[ol] - full.psi[plan.owned]).abs().max() / full.psi.abs().max())}
+    with open(os.path.join(out_dir, f"pre{name}{rank}.json"), "w") as f:
+        json.dump(out, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,world", [("quad", 3), ("hexp", 2)])
+def test_partitioned_preconditioning_equals_single_domain(tmp_path, name, world):
+    """The partitioned preconditioning (the pattern of partition.precondition:
+    an exchange of the ghosts' stage values before every pseudo residual)
+    gives the owned elements the single-domain psi, with the fixed count and
+    with the stop rule, whose RMS over all points is an all-reduce of the
+    ranks' sums over their owned points; the stop comes at the same
+    iteration."""
+    mp.start_processes(_precond_rank_main, args=(world, _free_port(), str(tmp_path), name), nprocs=world,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"pre{name}{r}.json")) for r in range(world)]
+    h = res[0]["hist"]
+    assert h[0] > res[0]["tol"] and h[1] > res[0]["tol"] > h[2]   # the rule stops after iteration 3
+    for r in res:
+        assert r["fixed"]["iters"] == r["fixed"]["iters_full"] == 6
+        assert r["adaptive"]["iters"] == r["adaptive"]["iters_full"] == 3
+        for key in ("fixed", "adaptive"):
+            assert r[key]["err"] < 1e-13, r
+            assert r[key]["rms_rel"] < 1e-12, r
+
+
 def test_partition_is_balanced_and_plans_are_consistent():
     sys.path.insert(0, ROOT)
     import synthetic as S
