@@ -290,6 +290,8 @@ class Field:
         return out
 
     # ---- element-partitioned stepping (fr_stage, fr_halo_*, fr_traces) -----
+    device = "cuda"  # where halo rows live (partition.halo_exchange allocates its buffers there)
+
     def stage(self, s, stream=None):
         """Stage s (1..4) of the physical RK4 step."""
         check(lib().fr_stage(self.handle, int(s), self._stream(stream)), "fr_stage")

@@ -196,26 +196,29 @@ def exchange(values, plan, dist=None):
     return values
 
 
-def _device_lists(plan):
+def _device_lists(plan, device="cuda"):
+    """The plan's send and receive lists as int64 tensors on `device`."""
     import torch
     cache = getattr(plan, "_dev", None)
     if cache is None:
-        cache = ({q: torch.as_tensor(ix, device="cuda") for q, ix in plan.send.items()},
-                 {q: torch.as_tensor(ix, device="cuda") for q, ix in plan.recv.items()})
-        plan._dev = cache
-    return cache
+        cache = plan._dev = {}
+    if device not in cache:
+        cache[device] = ({q: torch.as_tensor(ix, device=device) for q, ix in plan.send.items()},
+                         {q: torch.as_tensor(ix, device=device) for q, ix in plan.recv.items()})
+    return cache[device]
 
 
 def halo_exchange(field, plan, dist=None):
     """Replace the ghost elements' stage values of a rank's field with their
-    owners' (packed on the device, moved with isend/irecv, unpacked), then
-    recompute the traces."""
+    owners' (packed on the field's device, moved with isend/irecv,
+    unpacked), then recompute the traces."""
     import torch
     import torch.distributed as td
     d = dist or td
-    send, recv = _device_lists(plan)
+    dev = field.device
+    send, recv = _device_lists(plan, dev)
     packed = {q: field.halo_pack(ix) for q, ix in sorted(send.items())}
-    bufs = {q: torch.empty((len(ix), 2, field.mesh.info.nu), dtype=field.halo_dtype(), device="cuda")
+    bufs = {q: torch.empty((len(ix), 2, field.mesh.info.nu), dtype=field.halo_dtype(), device=dev)
             for q, ix in sorted(recv.items())}
     reqs = [d.irecv(bufs[q], src=q) for q in sorted(bufs)]
     reqs += [d.isend(packed[q], dst=q) for q in sorted(packed)]
@@ -273,7 +276,7 @@ def _exchange_ranks(fields, plans, lists):
 def precondition_ranks(fields, plans):
     """precondition() for several ranks' fields held by this process on one
     device."""
-    lists = [_device_lists(p) for p in plans]
+    lists = [_device_lists(p, f.device) for p, f in zip(plans, fields)]
     for f in fields:
         f.pseudo_begin()
     _exchange_ranks(fields, plans, lists)
@@ -289,7 +292,7 @@ def step_ranks(fields, plans, n_steps=1):
     one device: per stage every rank's stage, then every rank's ghosts
     refreshed from their owners by device copies, then the traces;
     preconditioning on fr_step's schedule."""
-    lists = [_device_lists(p) for p in plans]
+    lists = [_device_lists(p, f.device) for p, f in zip(plans, fields)]
     n0 = fields[0].stats()["n_steps"]
     for i in range(int(n_steps)):
         if _precondition_due(fields[0], n0 + i):

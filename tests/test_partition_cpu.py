@@ -288,3 +288,139 @@ def test_step_runs_the_preconditioning_on_fr_steps_schedule(monkeypatch):
     Params.normal = 1
     PT.step(FakeField(), None, 7)
     assert calls == one_step * 7
+
+
+class _StencilField:
+    """A stand-in for a rank's Field on the host: element rows of two
+    fields, each stage (and pseudo stage) an explicit update that reads the
+    face neighbours' rows, so a stale ghost changes the owned result.  It has
+    the calls partition.step makes (stage, pseudo_begin, pseudo_stage,
+    halo_pack, halo_unpack, traces, stats, params) with CPU tensors."""
+    device = "cpu"
+
+    class _Params:
+        normal, n_precond, pseudo_kmax = 0, 2, 2
+
+    params = _Params
+
+    def __init__(self, rows, adj, glob):
+        import types
+        self.u = rows.clone()
+        # neighbours in ascending global order, so that every rank sums them
+        # in the same order as the whole mesh
+        self.nbr = [sorted(a, key=lambda j: glob[j]) for a in adj]
+        self.n = 0
+        self.mesh = types.SimpleNamespace(info=types.SimpleNamespace(nu=rows.shape[2]))
+
+    def _mix(self, fld, c):
+        old = self.u[:, fld].clone()
+        for e, nb in enumerate(self.nbr):
+            if nb:
+                m = sum(old[j] for j in nb) / len(nb)
+                self.u[e, fld] = old[e] + c * (m - old[e])
+
+    def stage(self, s):
+        self._mix(0, 0.1 * s)
+        self._mix(1, 0.05 * s)
+        if s == 4:
+            self.n += 1
+
+    def pseudo_begin(self):
+        self.u[:, 1] = self.u[:, 0] - 0.5
+
+    def pseudo_stage(self, s):
+        self._mix(1, 0.2)
+
+    def stats(self):
+        return {"n_steps": self.n}
+
+    def halo_dtype(self):
+        return self.u.dtype
+
+    def halo_pack(self, ix):
+        return self.u[ix].clone()
+
+    def halo_unpack(self, ix, rows):
+        self.u[ix] = rows
+
+    def traces(self):
+        pass
+
+
+def _halo_rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2006_10967_gb300 import partition as PT
+    mesh = _case("hexp")[0]
+    g = torch.Generator().manual_seed(21)
+    u0 = torch.rand(mesh.n_elems, 2, 5, generator=g, dtype=torch.float64)
+    whole = _StencilField(u0, PT.face_adjacency(mesh), np.arange(mesh.n_elems))
+    plan = PT.plans(mesh, PT.partition(mesh, world))[rank]
+    mine = _StencilField(u0[torch.as_tensor(plan.local)], PT.face_adjacency(plan.mesh), plan.local)
+    n = 5
+    # the whole mesh on fr_step's schedule, no exchange
+    for i in range(n):
+        if i > 0 and i % whole.params.n_precond == 0:
+            whole.pseudo_begin()
+            for _ in range(whole.params.pseudo_kmax):
+                for s in (1, 2, 3, 4):
+                    whole.pseudo_stage(s)
+        for s in (1, 2, 3, 4):
+            whole.stage(s)
+    PT.step(mine, plan, n, dist=dist)      # isend / irecv over gloo
+    ol = torch.as_tensor(plan.owned_local)
+    err = float((mine.u[ol] - whole.u[torch.as_tensor(plan.owned)]).abs().max())
+    lone = _StencilField(u0[torch.as_tensor(plan.local)], PT.face_adjacency(plan.mesh), plan.local)
+    for _ in range(n):
+        for s in (1, 2, 3, 4):
+            lone.stage(s)
+    lone_err = float((lone.u[ol] - whole.u[torch.as_tensor(plan.owned)]).abs().max())
+    with open(os.path.join(out_dir, f"halo{rank}.json"), "w") as f:
+        json.dump({"err": err, "lone_err": lone_err, "steps": mine.n, "owned": int(plan.n_owned)}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_step_and_halo_exchange_over_gloo(tmp_path, world):
+    """partition.step and partition.halo_exchange, the calls a rank makes
+    with one GPU per process, run with real point-to-point transport (gloo,
+    one process per rank) on host stand-ins of the fields: after 5 steps
+    with two scheduled preconditionings the owned rows equal the whole
+    mesh's bit for bit, and a rank marched without the exchange differs."""
+    mp.start_processes(_halo_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"halo{r}.json")) for r in range(world)]
+    sys.path.insert(0, ROOT)
+    assert sum(r["owned"] for r in res) == _case("hexp")[0].n_elems
+    for r in res:
+        assert r["steps"] == 5
+        assert r["err"] == 0.0, r
+        assert r["lone_err"] > 1e-6, r
+
+
+def test_step_ranks_on_host_stand_ins():
+    """partition.step_ranks (all ranks' fields in one process, the exchange
+    a copy between them) on the host stand-ins: the owned rows after 5 steps
+    with two scheduled preconditionings equal the whole mesh's bit for bit."""
+    sys.path.insert(0, ROOT)
+    from paper_2006_10967_gb300 import partition as PT
+    mesh = _case("quad")[0]
+    u0 = torch.rand(mesh.n_elems, 2, 4, generator=torch.Generator().manual_seed(5), dtype=torch.float64)
+    whole = _StencilField(u0, PT.face_adjacency(mesh), np.arange(mesh.n_elems))
+    for i in range(5):
+        if i > 0 and i % 2 == 0:
+            whole.pseudo_begin()
+            for _ in range(2):
+                for s in (1, 2, 3, 4):
+                    whole.pseudo_stage(s)
+        for s in (1, 2, 3, 4):
+            whole.stage(s)
+    plans = PT.plans(mesh, PT.partition(mesh, 3))
+    fields = [_StencilField(u0[torch.as_tensor(p.local)], PT.face_adjacency(p.mesh), p.local) for p in plans]
+    PT.step_ranks(fields, plans, 5)
+    for p, f in zip(plans, fields):
+        assert f.n == 5
+        assert torch.equal(f.u[torch.as_tensor(p.owned_local)], whole.u[torch.as_tensor(p.owned)])
