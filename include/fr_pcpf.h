@@ -367,10 +367,11 @@ int fr_traces(fr_field* field, void* stream);
  * 3.2, Eq. pseudotimesystem marched by RK4 in pseudo time).  fr_pseudo_begin
  * resets psi_0 and psi from phi on every local element and computes psi's
  * traces; fr_pseudo_stage(s) runs stage s (1..4) of one pseudo-time
- * iteration with the step params.pseudo_dtau.  A rank calls fr_pseudo_begin,
- * exchanges its ghosts (fr_halo_pack / fr_halo_unpack / fr_traces, as after
- * fr_stage), then for each of params.pseudo_kmax iterations the four
- * fr_pseudo_stage calls, each followed by the same exchange; the owned
+ * iteration with the pseudo time step params.pseudo_dtau.  A rank calls
+ * fr_pseudo_begin, exchanges its ghosts (fr_halo_pack / fr_halo_unpack /
+ * fr_traces, as after fr_stage), then for each of params.pseudo_kmax
+ * iterations makes the four fr_pseudo_stage calls, each followed by the
+ * same exchange; the owned
  * elements then hold what fr_precondition gives on the whole mesh.  Only
  * fields with params.pseudo_fixed = 1 (the stop rule's RMS over the local
  * points would count the ghosts) and the preconditioned normal
@@ -395,7 +396,7 @@ int fr_kernel_variants(const fr_mesh* mesh, int precision, int32_t* count);
  *           cores (mma.sync m16n8k8, three-term TF32, FP32 accumulation).
  * u_dev: device, n_elems x 2 x 64 floats (element, field, solution point;
  * the stage-value layout), 16-byte aligned.  out_dev: device, out_len
- * floats.  reduce == 0: n_elems x 2 x 288 values per (element, field): the
+ * floats.  reduce == 0: n_elems x 2 x 288 values; per (element, field) the
  * 96 traces (face 2a + sd, face point l: line l along axis a, the other two
  * point indices with the lower axis fastest), then the derivatives along
  * axes 0, 1, 2 at the 64 points.  reduce != 0: n_elems x 2 values, the sum of
