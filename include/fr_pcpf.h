@@ -371,8 +371,8 @@ int fr_traces(fr_field* field, void* stream);
  * fr_pseudo_begin, exchanges its ghosts (fr_halo_pack / fr_halo_unpack /
  * fr_traces, as after fr_stage), then for each of params.pseudo_kmax
  * iterations makes the four fr_pseudo_stage calls, each followed by the
- * same exchange; the owned
- * elements then hold what fr_precondition gives on the whole mesh.  Only
+ * same exchange; the owned elements then hold what fr_precondition gives
+ * on the whole mesh.  Only
  * fields with params.pseudo_fixed = 1 (the stop rule's RMS over the local
  * points would count the ghosts) and the preconditioned normal
  * (FR_NORMAL_PSI): FR_EUNSUPPORTED otherwise.  Asynchronous on `stream`; no
