@@ -52,7 +52,11 @@ def centroids(mesh):
 
 def partition(mesh, nparts):
     """Part id per element: recursive bisection of the centroids along the
-    axis of largest extent, with sizes proportional to the part counts."""
+    axis of largest extent, with sizes proportional to the part counts.
+    1 <= nparts <= the element count (no part is empty)."""
+    nparts = int(nparts)
+    if not 1 <= nparts <= mesh.n_elems:
+        raise ValueError(f"nparts must lie in 1..{mesh.n_elems} (the element count), not {nparts}")
     cen = centroids(mesh)
     part = np.zeros(mesh.n_elems, dtype=np.int64)
 
@@ -68,7 +72,7 @@ def partition(mesh, nparts):
         split(order[:n1], k1, first)
         split(order[n1:], k - k1, first + k1)
 
-    split(np.arange(mesh.n_elems), int(nparts), 0)
+    split(np.arange(mesh.n_elems), nparts, 0)
     return part
 
 

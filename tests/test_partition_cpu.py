@@ -424,3 +424,21 @@ def test_step_ranks_on_host_stand_ins():
     for p, f in zip(plans, fields):
         assert f.n == 5
         assert torch.equal(f.u[torch.as_tensor(p.owned_local)], whole.u[torch.as_tensor(p.owned)])
+
+
+def test_partition_counts_edge_cases():
+    """One part owns everything and has no ghosts or peers; as many parts as
+    elements gives one element each; zero parts or more parts than elements
+    are refused."""
+    sys.path.insert(0, ROOT)
+    import synthetic as S
+    from paper_2006_10967_gb300 import partition as PT
+    mesh = S.quad_grid(3, jitter=0.1, seed=1)
+    one = PT.plans(mesh, PT.partition(mesh, 1))
+    assert len(one) == 1 and len(one[0].ghosts) == 0 and not one[0].send and not one[0].recv
+    assert np.array_equal(one[0].local, np.arange(mesh.n_elems))
+    part = PT.partition(mesh, mesh.n_elems)
+    assert np.array_equal(np.sort(part), np.arange(mesh.n_elems))
+    for bad in (0, mesh.n_elems + 1):
+        with pytest.raises(ValueError):
+            PT.partition(mesh, bad)
