@@ -139,6 +139,21 @@ def test_probe_rejects_bad_arguments_before_any_launch(G):
     assert f(3, 0, 0, None, 0, None, 0, None) == 0   # nothing to do
 
 
+def test_partitioned_run_calls_reject_a_null_field(G):
+    """The element-partitioned calls (fr_stage, fr_halo_*, fr_traces,
+    fr_pseudo_begin, fr_pseudo_stage) return FR_EINVAL for a null field
+    before touching the device."""
+    L = G.lib()
+    nb = C.c_size_t()
+    assert L.fr_stage(None, 1, None) == -1
+    assert L.fr_halo_row_bytes(None, C.byref(nb)) == -1
+    assert L.fr_halo_pack(None, None, 0, None, None) == -1
+    assert L.fr_halo_unpack(None, None, 0, None, None) == -1
+    assert L.fr_traces(None, None) == -1
+    assert L.fr_pseudo_begin(None, None) == -1
+    assert L.fr_pseudo_stage(None, 1, None) == -1
+
+
 def test_bounds_checked_build_exports_every_declared_symbol():
     """The bounds-checked build (FR_BOUNDS_CHECK) of the same sources links
     and exports the same entry points; its error code has a message."""
